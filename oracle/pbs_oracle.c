@@ -1,0 +1,665 @@
+/*
+ * pbs_oracle.c -- plain FP64 CPU oracle of the depth-marching proton-beam
+ * solver of Zhang, Bai & Tang, "A deterministic solver for the linear
+ * Boltzmann model of a single mono-directional proton beam"
+ * (arXiv 2504.00340).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header or table generator
+ * with the CUDA library; both are written separately from the paper.
+ *
+ * Everything here is double precision, written as straightforward loops in
+ * the paper's order and notation.  OpenMP (when compiled with -fopenmp) only
+ * runs the independent index sets that Remark 2 names in parallel; each
+ * output element is still computed by exactly the same sequence of
+ * operations as in a serial run.
+ *
+ * Readings of the paper that the paper leaves open are marked "Reading:".
+ *
+ * Data layout of one component psi_k (logical, row-major):
+ *     psi[g][c][j][i][p][q]
+ *   g = energy group 0..G-1 (0 = lowest energy; the paper's g = G is the top)
+ *   c = DG coefficient 0 (psi^1, group mean) or 1 (psi^2, slope)
+ *   j,i = angle indices in v and u (u fastest of the two)
+ *   p,q = lateral cell indices in y and z (z fastest)
+ *
+ * Parity status: every function below is pinned by a CPU test against a
+ * closed form, an invariant, a special case that reduces to a library
+ * routine, or brute force (see tests/test_oracle_*.py).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "pbs_oracle.h"
+
+#define IDX5(ctx, g, c, a, p, q) \
+  (((((size_t)(g) * 2 + (c)) * (size_t)(ctx)->na + (a)) * (size_t)(ctx)->ny + (p)) * (size_t)(ctx)->nz + (q))
+
+struct orc_ctx {
+  int ny, nz, ng, nu, nv, na;
+  double dy, dz, du, dv, u_max, v_max;
+  orc_phys ph;
+  double *e_faces;  /* ng+1 */
+  double *e_c;      /* group centre E_g */
+  double *de;       /* group width Delta E_g */
+  double *s_face;   /* mass stopping power at the faces, ng+1 */
+  double *ts;       /* group-averaged scattering power, ng */
+  double *sig;      /* catastrophic removal (mass), ng */
+  double *p1;       /* [gp][g] probability of gp -> g */
+  double *p2;       /* [g][a][ap] density in (u,v) of ap -> a */
+  double *u, *v;    /* angle nodes */
+};
+
+/* ------------------------------------------------------------------ */
+/* Physics tables (Appendix A with the Bragg-Kleeman and Highland      */
+/* substitutions of the workloads; Section 4, Appendix A.4)            */
+/* ------------------------------------------------------------------ */
+
+/* Mass stopping power from the Bragg-Kleeman range law R(E) = alpha E^p:
+ * S = dE / d(rho x) = 1 / (dR/dE) = E^(1-p) / (alpha p). */
+static double bk_stopping(const orc_phys *ph, double e) {
+  return ph->s_scale * pow(e, 1.0 - ph->bk_p) / (ph->bk_alpha * ph->bk_p);
+}
+
+/* Antiderivative in E of the Highland-type scattering power
+ *   T_s(E) = (Es / (p v))^2 / X0,  p v = E (E + 2M) / (E + M),
+ * written with w = E + M as (Es^2/X0) w^2 / (w^2 - M^2)^2, whose primitive is
+ *   (Es^2/X0) [ ln((w-M)/(w+M)) / (4M) - w / (2 (w^2 - M^2)) ]. */
+static double highland_primitive(const orc_phys *ph, double e) {
+  double m = ph->mp, w = e + m;
+  double k = ph->es * ph->es / ph->x0;
+  return k * (log((w - m) / (w + m)) / (4.0 * m) - w / (2.0 * (w * w - m * m)));
+}
+
+double orc_highland(const orc_phys *ph, double e) {
+  double m = ph->mp;
+  double pv = e * (e + 2.0 * m) / (e + m);
+  return ph->ts_scale * (ph->es / pv) * (ph->es / pv) / ph->x0;
+}
+
+/* Gamma density of the catastrophic deflection angle (Appendix A.4). */
+static double gamma_pdf(double th, double al, double be) {
+  if (th <= 0.0) return (al == 1.0) ? be : 0.0;
+  return pow(be, al) / tgamma(al) * pow(th, al - 1.0) * exp(-be * th);
+}
+
+orc_ctx *orc_create(const orc_grid *gr, const orc_phys *ph) {
+  orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+  int G = gr->ng, na;
+  if (!c) return NULL;
+  c->ny = gr->ny; c->nz = gr->nz; c->ng = G; c->nu = gr->nu; c->nv = gr->nv;
+  c->na = na = gr->nu * gr->nv;
+  c->dy = gr->dy; c->dz = gr->dz; c->u_max = gr->u_max; c->v_max = gr->v_max;
+  c->ph = *ph;
+  /* Reading (angular grid, Section 3.4): N unknowns per angle with zero
+   * Dirichlet values one spacing beyond the outermost nodes, so the spacing
+   * is 2 u_max / (N + 1) and the nodes sit symmetrically about 0. */
+  c->du = 2.0 * gr->u_max / (gr->nu + 1);
+  c->dv = 2.0 * gr->v_max / (gr->nv + 1);
+  c->e_faces = (double *)malloc(sizeof(double) * (G + 1));
+  c->e_c = (double *)malloc(sizeof(double) * G);
+  c->de = (double *)malloc(sizeof(double) * G);
+  c->s_face = (double *)malloc(sizeof(double) * (G + 1));
+  c->ts = (double *)malloc(sizeof(double) * G);
+  c->sig = (double *)malloc(sizeof(double) * G);
+  c->p1 = (double *)calloc((size_t)G * G, sizeof(double));
+  c->p2 = (double *)calloc((size_t)G * na * na, sizeof(double));
+  c->u = (double *)malloc(sizeof(double) * gr->nu);
+  c->v = (double *)malloc(sizeof(double) * gr->nv);
+  for (int f = 0; f <= G; f++) c->e_faces[f] = gr->e_faces[f];
+  for (int g = 0; g < G; g++) {
+    c->de[g] = c->e_faces[g + 1] - c->e_faces[g];
+    c->e_c[g] = 0.5 * (c->e_faces[g + 1] + c->e_faces[g]);
+  }
+  for (int i = 0; i < gr->nu; i++) c->u[i] = (i - 0.5 * (gr->nu - 1)) * c->du;
+  for (int j = 0; j < gr->nv; j++) c->v[j] = (j - 0.5 * (gr->nv - 1)) * c->dv;
+
+  /* Reading (energy floor): a face at E <= 0 has no finite Bragg-Kleeman
+   * stopping power; it is evaluated at half the lowest group width instead. */
+  double e_floor = 0.5 * c->de[0];
+  for (int f = 0; f <= G; f++) {
+    double e = c->e_faces[f] > e_floor ? c->e_faces[f] : e_floor;
+    c->s_face[f] = bk_stopping(ph, e);
+  }
+  /* sigma_tr,g is the group average of the scattering coefficient
+   * (after Eq. (0041-d)); here rho*sigma_tr is the Highland scattering power,
+   * averaged exactly over [max(E_lo, floor), E_hi]. */
+  for (int g = 0; g < G; g++) {
+    double lo = c->e_faces[g] > e_floor ? c->e_faces[g] : e_floor;
+    double hi = c->e_faces[g + 1];
+    c->ts[g] = ph->ts_scale * (highland_primitive(ph, hi) - highland_primitive(ph, lo)) / (hi - lo);
+    c->sig[g] = ph->sigma_ct;
+  }
+  /* P^1(g'->g) = lambda exp(-lambda (E_g' - E_g)) for g <= g' (protons only
+   * lose energy), normalised so that each source group's probabilities over
+   * the destination groups sum to one (particle conservation). */
+  for (int gp = 0; gp < G; gp++) {
+    double z = 0.0;
+    for (int g = 0; g <= gp; g++) z += ph->lambda_p1 * exp(-ph->lambda_p1 * (c->e_c[gp] - c->e_c[g]));
+    for (int g = 0; g <= gp; g++)
+      c->p1[(size_t)gp * G + g] = ph->lambda_p1 * exp(-ph->lambda_p1 * (c->e_c[gp] - c->e_c[g])) / z;
+  }
+  /* P^2_g((u',v') -> (u,v)) = Gamma(theta; alpha, beta) / K with
+   * theta = arccos Theta, Theta = (1 + u u' + v v') / (|(1,u,v)| |(1,u',v')|)
+ * (the angle between the two directions);
+   * K normalises the outgoing density: sum_a P^2 du dv = 1 for every a'. */
+  for (int g = 0; g < G; g++) {
+    for (int ap = 0; ap < na; ap++) {
+      double up = c->u[ap % c->nu], vp = c->v[ap / c->nu];
+      double k = 0.0;
+      for (int a = 0; a < na; a++) {
+        double uu = c->u[a % c->nu], vv = c->v[a / c->nu];
+        /* theta = arccos(Theta), evaluated as atan2(|n x n'|, n . n') with
+         * n = (1,u,v): the same angle, without the loss of accuracy of
+         * arccos near theta = 0. */
+        double cx = uu * vp - vv * up, cy = vv - vp, cz = up - uu;
+        double th = atan2(sqrt(cx * cx + cy * cy + cz * cz), 1.0 + uu * up + vv * vp);
+        double val = gamma_pdf(th, ph->g_alpha, ph->g_beta);
+        c->p2[((size_t)g * na + a) * na + ap] = val;
+        k += val * c->du * c->dv;
+      }
+      for (int a = 0; a < na; a++) c->p2[((size_t)g * na + a) * na + ap] /= (k > 0.0 ? k : 1.0);
+    }
+  }
+  return c;
+}
+
+void orc_destroy(orc_ctx *c) {
+  if (!c) return;
+  free(c->e_faces); free(c->e_c); free(c->de); free(c->s_face); free(c->ts);
+  free(c->sig); free(c->p1); free(c->p2); free(c->u); free(c->v);
+  free(c);
+}
+
+void orc_get_tables(const orc_ctx *c, double *s_face, double *ts, double *sig, double *p1, double *p2,
+                    double *u, double *v) {
+  int G = c->ng, na = c->na;
+  if (s_face) memcpy(s_face, c->s_face, sizeof(double) * (G + 1));
+  if (ts) memcpy(ts, c->ts, sizeof(double) * G);
+  if (sig) memcpy(sig, c->sig, sizeof(double) * G);
+  if (p1) memcpy(p1, c->p1, sizeof(double) * G * G);
+  if (p2) memcpy(p2, c->p2, sizeof(double) * G * na * na);
+  if (u) memcpy(u, c->u, sizeof(double) * c->nu);
+  if (v) memcpy(v, c->v, sizeof(double) * c->nv);
+}
+
+/* ------------------------------------------------------------------ */
+/* Energy operator (Section 3.2, Eq. (0041-d) with T = 0)              */
+/* ------------------------------------------------------------------ */
+
+/* The 2x2 blocks of the semi-discrete energy operator for group g in a
+ * medium of density rho:  d psi_g / dx = Agg psi_g + Aup psi_{g+1}.
+ * Row 1 tests with phi^1/dE, row 2 with 3 phi^2/dE.  The interface value
+ * at E_{g+1/2} is the upwind one from group g+1, psi^1_{g+1} - psi^2_{g+1}.
+ * Reading (sign of the phi^2-tested lower-face flux): phi^2 = -1 at the
+ * lower face, so [S psi phi^2] at E_{g-1/2} enters with a PLUS sign:
+ *   + 3 S_- (psi^1_g - psi^2_g) / dE.
+ * The printed minus sign would make a constant state with constant S drift. */
+void orc_energy_blocks(const orc_ctx *c, int g, double rho, double agg[2][2], double aup[2][2]) {
+  double a = rho / c->de[g];
+  double sp = c->s_face[g + 1], sm = c->s_face[g];
+  double sg = rho * c->sig[g];
+  /* psi^1 row */
+  agg[0][0] = -a * sm - sg;
+  agg[0][1] = a * sm;
+  /* psi^2 row: +3aS-(psi1 - psi2) - 3a(S+ + S-) psi1 - a(S+ - S-) psi2 - sigma psi2 */
+  agg[1][0] = 3.0 * a * sm - 3.0 * a * (sp + sm);
+  agg[1][1] = -3.0 * a * sm - a * (sp - sm) - sg;
+  /* inflow from the group above: S+ (psi^1_{g+1} - psi^2_{g+1}) */
+  if (g + 1 < c->ng) {
+    aup[0][0] = a * sp;        aup[0][1] = -a * sp;
+    aup[1][0] = 3.0 * a * sp;  aup[1][1] = -3.0 * a * sp;
+  } else { /* nothing enters above the top face */
+    aup[0][0] = aup[0][1] = aup[1][0] = aup[1][1] = 0.0;
+  }
+}
+
+/* Apply the semi-discrete energy operator to one lane: out = A x.
+ * x and out are [g][c] (2G values). */
+void orc_energy_apply(const orc_ctx *c, double rho, const double *x, double *out) {
+  int G = c->ng;
+  for (int g = 0; g < G; g++) {
+    double agg[2][2], aup[2][2];
+    orc_energy_blocks(c, g, rho, agg, aup);
+    for (int r = 0; r < 2; r++) {
+      double acc = agg[r][0] * x[2 * g] + agg[r][1] * x[2 * g + 1];
+      if (g + 1 < G) acc += aup[r][0] * x[2 * g + 2] + aup[r][1] * x[2 * g + 3];
+      out[2 * g + r] = acc;
+    }
+  }
+}
+
+/* Energy content per unit (u,v,y,z) of a DG state:  int E psi dE =
+ *   sum_g dE_g (E_g psi^1_g + dE_g psi^2_g / 6). */
+static double energy_content(const orc_ctx *c, const double *x) {
+  double s = 0.0;
+  for (int g = 0; g < c->ng; g++) s += c->de[g] * (c->e_c[g] * x[2 * g] + c->de[g] * x[2 * g + 1] / 6.0);
+  return s;
+}
+
+/* One Crank-Nicolson step of length h for one lane:
+ *   (I - h/2 A) x_new = (I + h/2 A) x_old + h/2 (src_old + src_new),
+ * where src_sum = src_old + src_new acts on psi^1 only (Remark 1).
+ * A is block upper-bidiagonal, so the system is solved from the top group
+ * down (x_{G+1} = 0): M_g x_g = rhs_g + h/2 Aup x_{g+1}.
+ * Returns the deposited energy content of the lane (difference form) and,
+ * through *edep_w, the same quantity from the operator form
+ *   -(h/2) phi^T A (x_old + x_new) - (h/2) phi^T src_sum. */
+double orc_energy_cn_lane(const orc_ctx *c, double rho, double h, double *x, const double *src_sum,
+                          double *edep_w) {
+  int G = c->ng;
+  double *old = (double *)malloc(sizeof(double) * 2 * G);
+  double *ax = (double *)malloc(sizeof(double) * 2 * G);
+  double *rhs = (double *)malloc(sizeof(double) * 2 * G);
+  double hh = 0.5 * h;
+  memcpy(old, x, sizeof(double) * 2 * G);
+  orc_energy_apply(c, rho, old, ax);
+  for (int k = 0; k < 2 * G; k++) rhs[k] = old[k] + hh * ax[k];
+  if (src_sum)
+    for (int g = 0; g < G; g++) rhs[2 * g] += hh * src_sum[g];
+  for (int g = G - 1; g >= 0; g--) {
+    double agg[2][2], aup[2][2], m[2][2], b[2];
+    orc_energy_blocks(c, g, rho, agg, aup);
+    b[0] = rhs[2 * g];
+    b[1] = rhs[2 * g + 1];
+    if (g + 1 < G) {
+      b[0] += hh * (aup[0][0] * x[2 * g + 2] + aup[0][1] * x[2 * g + 3]);
+      b[1] += hh * (aup[1][0] * x[2 * g + 2] + aup[1][1] * x[2 * g + 3]);
+    }
+    m[0][0] = 1.0 - hh * agg[0][0]; m[0][1] = -hh * agg[0][1];
+    m[1][0] = -hh * agg[1][0];      m[1][1] = 1.0 - hh * agg[1][1];
+    double det = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+    x[2 * g] = (m[1][1] * b[0] - m[0][1] * b[1]) / det;
+    x[2 * g + 1] = (-m[1][0] * b[0] + m[0][0] * b[1]) / det;
+  }
+  double dep = energy_content(c, old) - energy_content(c, x);
+  if (edep_w) {
+    double *sum = rhs; /* reuse */
+    for (int k = 0; k < 2 * G; k++) sum[k] = old[k] + x[k];
+    orc_energy_apply(c, rho, sum, ax);
+    double w = -hh * energy_content(c, ax);
+    if (src_sum) {
+      double s = 0.0;
+      for (int g = 0; g < G; g++) s += c->de[g] * c->e_c[g] * src_sum[g];
+      w -= hh * s;
+    }
+    *edep_w = w;
+  }
+  free(old); free(ax); free(rhs);
+  return dep;
+}
+
+/* Energy substep E(h) for every lane (y,z,u,v) of one component (Remark 2:
+ * independent lanes).  psi is one component [g][c][a][p][q]; src_sum is
+ * [g][a][p][q] or NULL; rho_yz is [p][q].  Deposited energy per lateral cell
+ * (MeV per source proton, i.e. already multiplied by du dv dy dz) is added to
+ * edep_yz[p][q] and edep_w_yz (operator form) when those are non-NULL. */
+void orc_energy_substep(const orc_ctx *c, double h, const double *rho_yz, double *psi, const double *src_sum,
+                        double *edep_yz, double *edep_w_yz) {
+  int G = c->ng, na = c->na, ny = c->ny, nz = c->nz;
+  double cellw = c->du * c->dv * c->dy * c->dz;
+#pragma omp parallel for schedule(static)
+  for (int pq = 0; pq < ny * nz; pq++) {
+    int p = pq / nz, q = pq % nz;
+    double *x = (double *)malloc(sizeof(double) * 2 * G);
+    double *s = src_sum ? (double *)malloc(sizeof(double) * G) : NULL;
+    double dep = 0.0, depw = 0.0;
+    for (int a = 0; a < na; a++) {
+      for (int g = 0; g < G; g++) {
+        x[2 * g] = psi[IDX5(c, g, 0, a, p, q)];
+        x[2 * g + 1] = psi[IDX5(c, g, 1, a, p, q)];
+        if (s) s[g] = src_sum[(((size_t)g * na + a) * ny + p) * nz + q];
+      }
+      double w = 0.0;
+      dep += orc_energy_cn_lane(c, rho_yz[pq], h, x, s, &w);
+      depw += w;
+      for (int g = 0; g < G; g++) {
+        psi[IDX5(c, g, 0, a, p, q)] = x[2 * g];
+        psi[IDX5(c, g, 1, a, p, q)] = x[2 * g + 1];
+      }
+    }
+    if (edep_yz) edep_yz[pq] += dep * cellw;
+    if (edep_w_yz) edep_w_yz[pq] += depw * cellw;
+    free(x); free(s);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Catastrophic source (Remark 1, Section 4, Appendix A.4)              */
+/* ------------------------------------------------------------------ */
+
+/* src^1_g(a) = du dv sum_{a'} sum_{g' >= g} sigma_{c,s,g'->g}(a'->a)
+ *              psi^1_{g'}(a') dE_{g'} / dE_g,
+ * with sigma_{c,s,g'->g}(a'->a) = rho sigma_{c,t,g'} P^1(g'->g) P^2_g(a'->a).
+ * Reading: the removal rate is the source group's sigma_{c,t,g'}.
+ * prev is the previous component [g][c][a][p][q]; out is [g][a][p][q]. */
+void orc_source(const orc_ctx *c, const double *rho_yz, const double *prev, double *out) {
+  int G = c->ng, na = c->na, ny = c->ny, nz = c->nz;
+#pragma omp parallel for schedule(static)
+  for (int pq = 0; pq < ny * nz; pq++) {
+    int p = pq / nz, q = pq % nz;
+    double rho = rho_yz[pq];
+    double *r = (double *)malloc(sizeof(double) * na);
+    for (int g = 0; g < G; g++) {
+      /* the energy sum first: r(a') = sum_{g' >= g} rho sigma_g' P^1(g'->g) psi^1_g'(a') dE_g' / dE_g */
+      for (int ap = 0; ap < na; ap++) {
+        double inner = 0.0;
+        for (int gp = g; gp < G; gp++)
+          inner += rho * c->sig[gp] * c->p1[(size_t)gp * G + g] * prev[IDX5(c, gp, 0, ap, p, q)] * c->de[gp] / c->de[g];
+        r[ap] = inner;
+      }
+      /* then the angle sum with P^2_g */
+      for (int a = 0; a < na; a++) {
+        double acc = 0.0;
+        for (int ap = 0; ap < na; ap++) acc += c->p2[((size_t)g * na + a) * na + ap] * r[ap];
+        out[(((size_t)g * na + a) * ny + p) * nz + q] = c->du * c->dv * acc;
+      }
+    }
+    free(r);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Lateral transport (Section 3.4, Eq. (distansport), Remark 3)         */
+/* ------------------------------------------------------------------ */
+
+/* Slope limiter eta(theta) = max[0, min(2 theta, 1), min(theta, 2)]. */
+static double eta_limiter(double th) {
+  double a = fmin(2.0 * th, 1.0), b = fmin(th, 2.0);
+  double m = a > b ? a : b;
+  return m > 0.0 ? m : 0.0;
+}
+
+/* Limited slope delta = (psi_{p+1} - psi_p) eta(theta), theta = num / (psi_{p+1} - psi_p).
+ * Where psi_{p+1} = psi_p the slope is zero whatever eta (eta <= 2). */
+static double limited_slope(double num, double den) {
+  if (den == 0.0) return 0.0;
+  return den * eta_limiter(num / den);
+}
+
+/* Numerical flux through the face between cells m (left) and m+1 (right)
+ * along one line of values f[] with zero ghost cells outside 0..n-1:
+ *   Psi = s+ psi^L - s- psi^R,
+ *   psi^L = psi_m + delta^L / 2,      theta^L = (psi_m - psi_{m-1}) / (psi_{m+1} - psi_m),
+ *   psi^R = psi_{m+1} - delta^R / 2,  theta^R = (psi_{m+2} - psi_{m+1}) / (psi_{m+1} - psi_m).
+ * Reading: the paper prints theta only for the left state; the right state
+ * uses the mirrored ratio, as in the flux-limiter form it cites. */
+static double face_flux(const double *f, int n, long stride, int m, double s) {
+#define VAL(k) (((k) >= 0 && (k) < n) ? f[(long)(k) * stride] : 0.0)
+  double pm1 = VAL(m - 1), p0 = VAL(m), p1 = VAL(m + 1), p2 = VAL(m + 2);
+#undef VAL
+  double sp = s > 0.0 ? s : 0.0, sm = s < 0.0 ? -s : 0.0;
+  double flux = 0.0;
+  if (sp > 0.0) flux += sp * (p0 + 0.5 * limited_slope(p0 - pm1, p1 - p0));
+  if (sm > 0.0) flux -= sm * (p1 - 0.5 * limited_slope(p2 - p1, p1 - p0));
+  return flux;
+}
+
+/* Semi-discrete right-hand side L(psi) = -(F_{p+1/2} - F_{p-1/2})/dy
+ *                                        - (G_{q+1/2} - G_{q-1/2})/dz
+ * for one (y,z) plane moving with angle (uu, vv). */
+static void transport_rhs(const orc_ctx *c, double uu, double vv, const double *f, double *out) {
+  int ny = c->ny, nz = c->nz;
+  for (int p = 0; p < ny; p++)
+    for (int q = 0; q < nz; q++) {
+      const double *col = f + q;            /* line along y at fixed q */
+      const double *row = f + (long)p * nz; /* line along z at fixed p */
+      double fy = face_flux(col, ny, nz, p, uu) - face_flux(col, ny, nz, p - 1, uu);
+      double fz = face_flux(row, nz, 1, q, vv) - face_flux(row, nz, 1, q - 1, vv);
+      out[(long)p * nz + q] = -fy / c->dy - fz / c->dz;
+    }
+}
+
+/* Transport substep T(h) for every (g, c, u, v) plane (Remark 2).
+ * Reading (Remark 3, depth integration): the slope is treated explicitly,
+ * which makes the Crank-Nicolson average an explicit trapezoid (Heun):
+ *   psi* = psi + h L(psi),  psi_new = psi + h/2 (L(psi) + L(psi*)). */
+void orc_transport_substep(const orc_ctx *c, double h, double *psi) {
+  int G = c->ng, na = c->na, n = c->ny * c->nz;
+#pragma omp parallel for schedule(static)
+  for (int plane = 0; plane < G * 2 * na; plane++) {
+    int a = plane % na;
+    double uu = c->u[a % c->nu], vv = c->v[a / c->nu];
+    double *f = psi + (size_t)plane * n;
+    double *l0 = (double *)malloc(sizeof(double) * n);
+    double *st = (double *)malloc(sizeof(double) * n);
+    double *l1 = (double *)malloc(sizeof(double) * n);
+    transport_rhs(c, uu, vv, f, l0);
+    for (int k = 0; k < n; k++) st[k] = f[k] + h * l0[k];
+    transport_rhs(c, uu, vv, st, l1);
+    for (int k = 0; k < n; k++) f[k] = f[k] + 0.5 * h * (l0[k] + l1[k]);
+    free(l0); free(st); free(l1);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Angular diffusion (Section 3.4, Eqs. (sd), (fly))                   */
+/* ------------------------------------------------------------------ */
+
+/* Angular substep A(h) for every (g, c, y, z) slab (Remark 2).  The
+ * five-point Laplacian with zero Dirichlet values is diagonalised by the
+ * discrete sine transform; each mode (m,n) has eigenvalue
+ *   lam = (2cos(pi m/(Nu+1)) - 2)/du^2 + (2cos(pi n/(Nv+1)) - 2)/dv^2
+ * and Crank-Nicolson with coefficient kappa/2, kappa = rho sigma_tr,g,
+ * multiplies it by r = (1 + h kappa lam / 4) / (1 - h kappa lam / 4).
+ * The transform is written as explicit sine sums with the orthonormal
+ * scaling sqrt(2/(N+1)) in each direction (the paper's 1/(IJ) inverse
+ * scaling with I = N+1 is the same map). */
+void orc_angular_substep(const orc_ctx *c, double h, const double *rho_yz, double *psi) {
+  int G = c->ng, nu = c->nu, nv = c->nv, na = c->na, ny = c->ny, nz = c->nz;
+  double *su = (double *)malloc(sizeof(double) * nu * nu);
+  double *sv = (double *)malloc(sizeof(double) * nv * nv);
+  double *lam = (double *)malloc(sizeof(double) * na);
+  const double pi = 3.14159265358979323846;
+  for (int m = 0; m < nu; m++)
+    for (int i = 0; i < nu; i++) su[m * nu + i] = sqrt(2.0 / (nu + 1)) * sin(pi * (m + 1) * (i + 1) / (nu + 1));
+  for (int n = 0; n < nv; n++)
+    for (int j = 0; j < nv; j++) sv[n * nv + j] = sqrt(2.0 / (nv + 1)) * sin(pi * (n + 1) * (j + 1) / (nv + 1));
+  for (int n = 0; n < nv; n++)
+    for (int m = 0; m < nu; m++)
+      lam[n * nu + m] = (2.0 * cos(pi * (m + 1) / (nu + 1)) - 2.0) / (c->du * c->du) +
+                        (2.0 * cos(pi * (n + 1) / (nv + 1)) - 2.0) / (c->dv * c->dv);
+#pragma omp parallel for schedule(static)
+  for (long slab = 0; slab < (long)G * 2 * ny * nz; slab++) {
+    long gc = slab / ((long)ny * nz);
+    int pq = (int)(slab % ((long)ny * nz));
+    int g = (int)(gc / 2);
+    double kappa = rho_yz[pq] * c->ts[g];
+    double *base = psi + (size_t)gc * na * ny * nz + pq;
+    long st = (long)ny * nz; /* stride between angles */
+    double *x = (double *)malloc(sizeof(double) * na);
+    double *t = (double *)malloc(sizeof(double) * na);
+    for (int a = 0; a < na; a++) x[a] = base[a * st];
+    /* forward: t[n][m] = sum_j sum_i sv[n][j] su[m][i] x[j][i] */
+    for (int n = 0; n < nv; n++)
+      for (int m = 0; m < nu; m++) {
+        double acc = 0.0;
+        for (int j = 0; j < nv; j++)
+          for (int i = 0; i < nu; i++) acc += sv[n * nv + j] * su[m * nu + i] * x[j * nu + i];
+        double q = 0.25 * h * kappa * lam[n * nu + m];
+        t[n * nu + m] = acc * (1.0 + q) / (1.0 - q);
+      }
+    /* inverse (the orthonormal DST-I is its own inverse) */
+    for (int j = 0; j < nv; j++)
+      for (int i = 0; i < nu; i++) {
+        double acc = 0.0;
+        for (int n = 0; n < nv; n++)
+          for (int m = 0; m < nu; m++) acc += sv[n * nv + j] * su[m * nu + i] * t[n * nu + m];
+        x[j * nu + i] = acc;
+      }
+    for (int a = 0; a < na; a++) base[a * st] = x[a];
+    free(x); free(t);
+  }
+  free(su); free(sv); free(lam);
+}
+
+/* ------------------------------------------------------------------ */
+/* Beam (Section 4, Eq. (bdy))                                          */
+/* ------------------------------------------------------------------ */
+
+static double std_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+static double std_pdf(double x) { return exp(-0.5 * x * x) / sqrt(2.0 * 3.14159265358979323846); }
+
+/* Probability mass of N(mu, s^2) in [lo, hi]. */
+static double gauss_mass(double lo, double hi, double mu, double s) {
+  double a = (lo - mu) / s, b = (hi - mu) / s;
+  if (a > 0.0) return std_cdf(-a) - std_cdf(-b); /* upper tail: avoid 1 - 1 */
+  return std_cdf(b) - std_cdf(a);
+}
+
+/* psi_p(x=0): the Gaussian of Eq. (bdy) projected on the discrete space.
+ * Lateral: cell averages.  Angle: average over each node's cell of width
+ * du (Reading: with sigma_u = 1e-6 the beam is narrower than one node, and
+ * the cell average splits it evenly between the nodes next to u0).
+ * Energy: DG L2 projection, psi^1 = (1/dE) int f, psi^2 = (3/dE) int f phi^2.
+ * The constant C is fixed by sum psi^1 dE du dv dy dz = 1 (one proton). */
+void orc_init_beam(const orc_ctx *c, const orc_beam *b, double *psi) {
+  int G = c->ng, nu = c->nu, nv = c->nv, na = c->na, ny = c->ny, nz = c->nz;
+  double *ey = (double *)malloc(sizeof(double) * 2 * G);
+  double *ay = (double *)malloc(sizeof(double) * na);
+  double *yy = (double *)malloc(sizeof(double) * ny);
+  double *zz = (double *)malloc(sizeof(double) * nz);
+  double tot_e = 0.0, tot_a = 0.0, tot_y = 0.0, tot_z = 0.0;
+  for (int g = 0; g < G; g++) {
+    double lo = c->e_faces[g], hi = c->e_faces[g + 1], de = c->de[g];
+    double m0 = gauss_mass(lo, hi, b->e0, b->sigma_e);
+    double al = (lo - b->e0) / b->sigma_e, be = (hi - b->e0) / b->sigma_e;
+    double m1 = b->sigma_e * (std_pdf(al) - std_pdf(be)) + (b->e0 - c->e_c[g]) * m0; /* int (E-E_g) f */
+    ey[2 * g] = m0 / de;
+    ey[2 * g + 1] = 3.0 / de * (2.0 / de) * m1;
+    tot_e += ey[2 * g] * de;
+  }
+  for (int j = 0; j < nv; j++)
+    for (int i = 0; i < nu; i++) {
+      double mu = gauss_mass(c->u[i] - 0.5 * c->du, c->u[i] + 0.5 * c->du, b->u0, b->sigma_u) / c->du;
+      double mv = gauss_mass(c->v[j] - 0.5 * c->dv, c->v[j] + 0.5 * c->dv, b->v0, b->sigma_v) / c->dv;
+      ay[j * nu + i] = mu * mv;
+      tot_a += mu * mv * c->du * c->dv;
+    }
+  for (int p = 0; p < ny; p++) {
+    double lo = (p - 0.5 * ny) * c->dy, hi = (p + 1 - 0.5 * ny) * c->dy;
+    yy[p] = gauss_mass(lo, hi, b->y0, b->sigma_y) / c->dy;
+    tot_y += yy[p] * c->dy;
+  }
+  for (int q = 0; q < nz; q++) {
+    double lo = (q - 0.5 * nz) * c->dz, hi = (q + 1 - 0.5 * nz) * c->dz;
+    zz[q] = gauss_mass(lo, hi, b->z0, b->sigma_z) / c->dz;
+    tot_z += zz[q] * c->dz;
+  }
+  double norm = 1.0 / (tot_e * tot_a * tot_y * tot_z);
+  for (int g = 0; g < G; g++)
+    for (int cc = 0; cc < 2; cc++)
+      for (int a = 0; a < na; a++)
+        for (int p = 0; p < ny; p++)
+          for (int q = 0; q < nz; q++)
+            psi[IDX5(c, g, cc, a, p, q)] = norm * ey[2 * g + cc] * ay[a] * yy[p] * zz[q];
+  free(ey); free(ay); free(yy); free(zz);
+}
+
+/* ------------------------------------------------------------------ */
+/* Depth march (Sections 3.1 and 3.3)                                   */
+/* ------------------------------------------------------------------ */
+
+/* Energy substep of length h for all components in lock-step.  The source
+ * of component k (k >= 1) is the catastrophic source of component k-1,
+ * evaluated at the start and at the end of the same substep (trapezoid). */
+static void energy_all(const orc_ctx *c, const orc_march_opts *o, double h, const double *rho_yz, double *psi,
+                       double *edep_yz, double *edep_w_yz, double *srcA, double *srcB) {
+  size_t ncomp = (size_t)c->ng * 2 * c->na * c->ny * c->nz;
+  size_t nsrc = (size_t)c->ng * c->na * c->ny * c->nz;
+  for (int k = 0; k <= o->n_scatter; k++) {
+    double *pk = psi + (size_t)k * ncomp;
+    const double *src = NULL;
+    if (k >= 1) src = srcB; /* holds src(psi_{k-1}, old) + src(psi_{k-1}, new) */
+    if (k < o->n_scatter) orc_source(c, rho_yz, pk, srcA); /* source for k+1 from the old state */
+    orc_energy_substep(c, h, rho_yz, pk, src, edep_yz, edep_w_yz);
+    if (k < o->n_scatter) {
+      double *tmp = (double *)malloc(sizeof(double) * nsrc);
+      orc_source(c, rho_yz, pk, tmp); /* ... and from the new state */
+      for (size_t e = 0; e < nsrc; e++) srcB[e] = srcA[e] + tmp[e];
+      free(tmp);
+    }
+  }
+}
+
+int orc_march(const orc_ctx *c, const orc_march_opts *o, const orc_beam *b, const double *rho, int n_steps,
+              double dx, double *psi, double *dose, double *edep_w, double *fluence) {
+  int ny = c->ny, nz = c->nz, ncomp_k = o->n_scatter + 1;
+  size_t ncomp = (size_t)c->ng * 2 * c->na * ny * nz;
+  size_t nsrc = (size_t)c->ng * c->na * ny * nz;
+  double *srcA = o->n_scatter > 0 ? (double *)calloc(nsrc, sizeof(double)) : NULL;
+  double *srcB = o->n_scatter > 0 ? (double *)calloc(nsrc, sizeof(double)) : NULL;
+  double *edep = (double *)calloc((size_t)ny * nz, sizeof(double));
+  double *edw = (double *)calloc((size_t)ny * nz, sizeof(double));
+  if (b) {
+    memset(psi, 0, sizeof(double) * ncomp * ncomp_k);
+    orc_init_beam(c, b, psi);
+  }
+  if (fluence) orc_fluence(c, psi, ncomp_k, fluence);
+  for (int s = 0; s < n_steps; s++) {
+    const double *rho_yz = rho + (size_t)s * ny * nz;
+    memset(edep, 0, sizeof(double) * ny * nz);
+    memset(edw, 0, sizeof(double) * ny * nz);
+    if (o->scheme == 0) {
+      /* Strang: E(h/2) T(h/2) A(h) T(h/2) E(h/2), CN in each substep */
+      if (o->do_energy) energy_all(c, o, 0.5 * dx, rho_yz, psi, edep, edw, srcA, srcB);
+      if (o->do_transport)
+        for (int k = 0; k < ncomp_k; k++) orc_transport_substep(c, 0.5 * dx, psi + k * ncomp);
+      if (o->do_angular)
+        for (int k = 0; k < ncomp_k; k++) orc_angular_substep(c, dx, rho_yz, psi + k * ncomp);
+      if (o->do_transport)
+        for (int k = 0; k < ncomp_k; k++) orc_transport_substep(c, 0.5 * dx, psi + k * ncomp);
+      if (o->do_energy) energy_all(c, o, 0.5 * dx, rho_yz, psi, edep, edw, srcA, srcB);
+    } else {
+      /* first-order (Lie) splitting: E(h) T(h) A(h), Eqs. (split-1..3) */
+      if (o->do_energy) energy_all(c, o, dx, rho_yz, psi, edep, edw, srcA, srcB);
+      if (o->do_transport)
+        for (int k = 0; k < ncomp_k; k++) orc_transport_substep(c, dx, psi + k * ncomp);
+      if (o->do_angular)
+        for (int k = 0; k < ncomp_k; k++) orc_angular_substep(c, dx, rho_yz, psi + k * ncomp);
+    }
+    /* D = E_dep / rho per unit volume (Eq. (en_d) and the definition above it) */
+    for (int pq = 0; pq < ny * nz; pq++) {
+      double m = rho_yz[pq] * dx * c->dy * c->dz;
+      if (dose) dose[(size_t)s * ny * nz + pq] = m > 0.0 ? edep[pq] / m : 0.0;
+      if (edep_w) edep_w[(size_t)s * ny * nz + pq] = m > 0.0 ? edw[pq] / m : 0.0;
+    }
+    if (fluence) orc_fluence(c, psi, ncomp_k, fluence + (size_t)(s + 1) * ny * nz);
+  }
+  free(srcA); free(srcB); free(edep); free(edw);
+  return 0;
+}
+
+/* Planar fluence per lateral cell: du dv sum_{k,g,a} psi^1 dE (protons/cm^2). */
+void orc_fluence(const orc_ctx *c, const double *psi, int ncomp_k, double *out) {
+  int ny = c->ny, nz = c->nz;
+  size_t ncomp = (size_t)c->ng * 2 * c->na * ny * nz;
+  for (int pq = 0; pq < ny * nz; pq++) {
+    double s = 0.0;
+    for (int k = 0; k < ncomp_k; k++)
+      for (int g = 0; g < c->ng; g++)
+        for (int a = 0; a < c->na; a++) s += psi[k * ncomp + IDX5(c, g, 0, a, pq / nz, pq % nz)] * c->de[g];
+    out[pq] = s * c->du * c->dv;
+  }
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
