@@ -1,0 +1,195 @@
+/*
+ * pbs.h -- C ABI of the GB300 (sm_103a) proton pencil-beam depth-march solver.
+ *
+ * The library computes the deterministic linear-Boltzmann proton-beam model of
+ * Zhang, Bai & Tang (arXiv 2504.00340): the phase-space density
+ * psi(x; y, z, E, u, v) is marched in depth x (the time-like variable,
+ * Section 3.3) by Strang splitting into three Crank-Nicolson subsystems:
+ *   E  energy loss, DG-P1 in energy (Section 3.2, Eq. 0041-d),
+ *   T  lateral transport, flux-limited MUSCL finite volumes (Section 3.4,
+ *      Eq. distansport, Remark 3),
+ *   A  angular diffusion, five-point Laplacian diagonalised by sine transforms
+ *      (Section 3.4, Eqs. sd and fly),
+ * applied as E(h/2) T(h/2) A(h) T(h/2) E(h/2) per depth step h.  Protons are
+ * split into the primary field and K catastrophically scattered fields by
+ * source iteration (Section 3.1, Eq. pri-se; Remark 1), and dose is tallied per
+ * voxel from the energy lost in the E substeps (Section 4, Eq. en_d).
+ *
+ * Conventions for every entry point:
+ *   - All functions return pbs_status; no C++ exception crosses the ABI.
+ *   - Host arrays passed in are borrowed for the duration of the call only
+ *     (copied in).  Host arrays passed out are written by the call.
+ *   - Device memory: the caller owns the workspace it binds with
+ *     pbs_bind_workspace; the library allocates no device memory itself
+ *     (its coefficient tables and device status word live in the workspace).
+ *   - Stream: all device work is issued on the stream given to pbs_create
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *     pbs_launch_beam, pbs_step and the substep calls are asynchronous;
+ *     pbs_read_* synchronise the stream.
+ *   - A context is bound to the CUDA device current at pbs_create; call it
+ *     with that device current.  A context is not thread-safe.
+ *   - Calling out of order (e.g. pbs_step before pbs_launch_beam) returns
+ *     PBS_ERR_STATE; bad sizes or NULL pointers return PBS_ERR_ARG; CUDA
+ *     failures return PBS_ERR_CUDA; a device wait that gave up returns
+ *     PBS_ERR_TIMEOUT.  pbs_last_error describes the last failure.
+ *
+ * Logical layout of one component of psi (row-major, used by pbs_read_psi,
+ * pbs_write_psi and on the device):  psi[g][c][j][i][p][q] with
+ *   g energy group 0..ng-1 (0 = lowest energy), c DG coefficient
+ *   (0 = group mean psi^1, 1 = slope psi^2), j,i angle indices in v,u,
+ *   p,q lateral cell indices in y,z.
+ */
+#ifndef PBS_H
+#define PBS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PBS_OK = 0,
+  PBS_ERR_ARG = -1,
+  PBS_ERR_CUDA = -2,
+  PBS_ERR_NOMEM = -3,
+  PBS_ERR_STATE = -4,
+  PBS_ERR_TIMEOUT = -5,
+  PBS_ERR_UNSUPPORTED = -6
+} pbs_status;
+
+typedef enum {
+  PBS_FP64 = 0,   /* psi, arithmetic and the source contraction in FP64       */
+  PBS_FP32 = 1,   /* psi and arithmetic in FP32, FP64 dose tally              */
+  PBS_MIXED = 2   /* FP32 psi; the catastrophic-source angle contraction on
+                     tensor cores in BF16 with FP32 accumulation             */
+} pbs_precision;
+
+/* Discretisation.  Lateral cells are centred on (y,z) = 0; angle nodes are
+ * u_i = (i - (nu-1)/2) du with du = 2 u_max / (nu + 1) (zero Dirichlet values
+ * one spacing beyond the outermost nodes, Section 3.4); energy faces are
+ * given explicitly (ng+1 values, strictly ascending, MeV). */
+typedef struct {
+  int ny, nz;              /* lateral cells (y, z)                          */
+  int ng;                  /* energy groups                                 */
+  int nu, nv;              /* angle nodes (u, v); the device path needs even
+                              nu, nv with nu, nv <= 16                      */
+  int nx;                  /* depth steps the context can hold dose for     */
+  int n_scatter;           /* K: number of scattered components (0 = primary
+                              only)                                         */
+  double dy, dz;           /* lateral cell sizes (cm)                       */
+  double dx;               /* depth step h (cm)                             */
+  double u_max, v_max;     /* half-widths of the angle box                  */
+  const double *e_faces;   /* ng+1 ascending group faces (MeV), borrowed    */
+} pbs_grid;
+
+/* Physics of water-equivalent media (Appendix A with substitutes): mass
+ * stopping power from the Bragg-Kleeman range law R = bk_alpha E^bk_p,
+ * multiple-scattering power (Highland form) T = (es / pv)^2 / x0 used as
+ * rho * sigma_tr, catastrophic removal sigma_ct (cm^2/g), exponential energy
+ * transfer P^1 with rate lambda_p1 (1/MeV) and Gamma(g_alpha, g_beta)
+ * angular deflection P^2 (Section 4 and Appendix A.4).  s_scale and ts_scale
+ * multiply S and the scattering power (0 switches a process off). */
+typedef struct {
+  double bk_alpha, bk_p;
+  double x0;
+  double mp;
+  double es;
+  double sigma_ct;
+  double lambda_p1;
+  double g_alpha, g_beta;
+  double s_scale, ts_scale;
+} pbs_physics;
+
+/* Pencil beam of Eq. (bdy): Gaussian in y, z (cm), u, v and E (MeV). */
+typedef struct {
+  double e0, sigma_e, y0, z0, sigma_y, sigma_z, u0, v0, sigma_u, sigma_v;
+} pbs_beam;
+
+typedef struct pbs_ctx pbs_ctx;
+
+/* Create a context for the grid on the current device.  precision is a
+ * pbs_precision.  stream is a cudaStream_t (may be NULL).  *out receives the
+ * context; destroy it with pbs_destroy.  Returns PBS_ERR_UNSUPPORTED for
+ * grids the device kernels do not handle (odd or > 16 angle counts, nz > 1024,
+ * ng > 2048). */
+pbs_status pbs_create(pbs_ctx **out, const pbs_grid *grid, int precision, void *stream);
+
+/* Bytes of device workspace the context needs (psi of all K+1 components,
+ * source buffers, material, dose and fluence tallies, tables). */
+pbs_status pbs_workspace_size(const pbs_ctx *ctx, size_t *bytes);
+
+/* Bind caller-owned device memory of at least pbs_workspace_size bytes,
+ * 256-byte aligned; the call zeroes it (synchronously on the context's
+ * stream).  The caller keeps ownership and must keep it alive until
+ * pbs_destroy or a new bind.  A new bind forgets the material and the beam. */
+pbs_status pbs_bind_workspace(pbs_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Build the FP64 coefficient tables on the host from the physics model and
+ * upload them (group faces' stopping power, group-averaged scattering power,
+ * removal cross section, P^1 decay factors, P^2 matrices). */
+pbs_status pbs_set_physics(pbs_ctx *ctx, const pbs_physics *phys);
+
+/* Copy the FP64 host tables out (any pointer may be NULL):
+ * s_face[ng+1] (MeV cm^2/g), ts[ng] (rad^2 cm^2/g), sig[ng] (cm^2/g),
+ * p1[ng*ng] ([g'][g], probability g' -> g), p2[ng*na*na] ([g][a][a'],
+ * density in (u,v) of a' -> a), u[nu], v[nv]. */
+pbs_status pbs_get_tables(const pbs_ctx *ctx, double *s_face, double *ts, double *sig, double *p1, double *p2,
+                          double *u, double *v);
+
+/* Density rho[s][p][q] (g/cm^3) for depth steps s = 0..n_slabs-1
+ * (n_slabs <= grid.nx).  Step s uses slab s in all five substeps. */
+pbs_status pbs_set_material(pbs_ctx *ctx, const double *rho, int n_slabs);
+
+/* Project the beam of Eq. (bdy) onto psi_p (cell averages in y, z, u, v;
+ * DG L2 projection in E; normalised to one proton), zero psi_s1..psi_sK,
+ * the dose and the fluence, and reset the depth counter to 0. */
+pbs_status pbs_launch_beam(pbs_ctx *ctx, const pbs_beam *beam);
+
+/* March n_steps depth steps (Strang order E T A T E per step, all
+ * components in lock-step).  Asynchronous.  PBS_ERR_ARG if the march would
+ * pass the material's last slab. */
+pbs_status pbs_step(pbs_ctx *ctx, int n_steps);
+
+/* Depth steps marched since pbs_launch_beam. */
+pbs_status pbs_get_depth(const pbs_ctx *ctx, int *steps_done);
+
+/* Dose D[s][p][q] (MeV/g per source proton, Section 4: D = E_dep / rho) for
+ * the first n_slabs slabs; n must equal n_slabs*ny*nz. Synchronises. */
+pbs_status pbs_read_dose(pbs_ctx *ctx, double *host_out, size_t n);
+
+/* Planar fluence F[s][p][q] = du dv sum_{k,g,a} psi^1 dE (protons/cm^2) at
+ * depths s*dx, s = 0..n_planes-1 (s = 0 is the entrance); n must equal
+ * n_planes*ny*nz with n_planes <= steps done + 1.  Synchronises. */
+pbs_status pbs_read_fluence(pbs_ctx *ctx, double *host_out, size_t n);
+
+/* Copy component k of psi to / from the host as FP64 in the logical layout
+ * above (n = ng*2*nu*nv*ny*nz).  Synchronises. */
+pbs_status pbs_read_psi(pbs_ctx *ctx, int k, double *host_out, size_t n);
+pbs_status pbs_write_psi(pbs_ctx *ctx, int k, const double *host_in, size_t n);
+
+/* Single substeps for testing and for callers composing their own march.
+ * energy: E(h) on all components in lock-step with the source chain, dose
+ *   added to slab `slab`, fluence written to plane `fluence_plane` if >= 0.
+ * transport: T(h) on all components.  angular: A(h) on all components with
+ *   the density of slab `slab`. */
+pbs_status pbs_substep_energy(pbs_ctx *ctx, double h, int slab, int fluence_plane);
+pbs_status pbs_substep_transport(pbs_ctx *ctx, double h);
+pbs_status pbs_substep_angular(pbs_ctx *ctx, double h, int slab);
+
+/* Catastrophic source of Remark 1 from component k_from at its current
+ * state with the density of slab `slab`: host_out[g][j][i][p][q] (FP64),
+ * n = ng*nu*nv*ny*nz.  Synchronises. */
+pbs_status pbs_eval_source(pbs_ctx *ctx, int k_from, int slab, double *host_out, size_t n);
+
+/* Number of kernel launches the library has issued since pbs_create. */
+pbs_status pbs_kernel_launches(const pbs_ctx *ctx, long long *count);
+
+const char *pbs_last_error(const pbs_ctx *ctx);
+const char *pbs_status_string(int status);
+void pbs_destroy(pbs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,340 @@
+"""Thin Python binding of the C ABI in include/pbs.h (argument marshalling only).
+
+Every function named ``pbs_*`` here calls the C function of the same name in
+``_lib/libpbs.so``; all arithmetic of the method runs in that library's CUDA
+kernels.  PyTorch is used only to allocate the caller-owned device workspace
+and to name the CUDA stream.  If the library has not been built, or no CUDA
+device is present, these calls raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+PBS_FP64, PBS_FP32, PBS_MIXED = 0, 1, 2
+PRECISIONS = {"fp64": PBS_FP64, "fp32": PBS_FP32, "mixed": PBS_MIXED}
+STATUS = {0: "PBS_OK", -1: "PBS_ERR_ARG", -2: "PBS_ERR_CUDA", -3: "PBS_ERR_NOMEM", -4: "PBS_ERR_STATE",
+          -5: "PBS_ERR_TIMEOUT", -6: "PBS_ERR_UNSUPPORTED"}
+
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+
+
+class PbsGrid(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int), ("nz", ctypes.c_int), ("ng", ctypes.c_int), ("nu", ctypes.c_int),
+                ("nv", ctypes.c_int), ("nx", ctypes.c_int), ("n_scatter", ctypes.c_int),
+                ("dy", ctypes.c_double), ("dz", ctypes.c_double), ("dx", ctypes.c_double),
+                ("u_max", ctypes.c_double), ("v_max", ctypes.c_double), ("e_faces", _D)]
+
+
+class PbsPhysics(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("bk_alpha", "bk_p", "x0", "mp", "es", "sigma_ct", "lambda_p1",
+                                               "g_alpha", "g_beta", "s_scale", "ts_scale")]
+
+
+class PbsBeam(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("e0", "sigma_e", "y0", "z0", "sigma_y", "sigma_z", "u0", "v0",
+                                               "sigma_u", "sigma_v")]
+
+
+class PbsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+# (name, restype, argtypes) of every exported entry point of include/pbs.h
+SIGNATURES = [
+    ("pbs_create", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(PbsGrid), ctypes.c_int, _VP]),
+    ("pbs_workspace_size", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    ("pbs_bind_workspace", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    ("pbs_set_physics", ctypes.c_int, [_VP, ctypes.POINTER(PbsPhysics)]),
+    ("pbs_get_tables", ctypes.c_int, [_VP, _D, _D, _D, _D, _D, _D, _D]),
+    ("pbs_set_material", ctypes.c_int, [_VP, _D, ctypes.c_int]),
+    ("pbs_launch_beam", ctypes.c_int, [_VP, ctypes.POINTER(PbsBeam)]),
+    ("pbs_step", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("pbs_get_depth", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    ("pbs_read_dose", ctypes.c_int, [_VP, _D, ctypes.c_size_t]),
+    ("pbs_read_fluence", ctypes.c_int, [_VP, _D, ctypes.c_size_t]),
+    ("pbs_read_psi", ctypes.c_int, [_VP, ctypes.c_int, _D, ctypes.c_size_t]),
+    ("pbs_write_psi", ctypes.c_int, [_VP, ctypes.c_int, _D, ctypes.c_size_t]),
+    ("pbs_substep_energy", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    ("pbs_substep_transport", ctypes.c_int, [_VP, ctypes.c_double]),
+    ("pbs_substep_angular", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
+    ("pbs_eval_source", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _D, ctypes.c_size_t]),
+    ("pbs_kernel_launches", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    ("pbs_last_error", ctypes.c_char_p, [_VP]),
+    ("pbs_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("pbs_destroy", None, [_VP]),
+]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libpbs.so (building it first if asked).  Raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+            lib = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return ctypes.cast(None, _D)
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_D)
+
+
+def _check(ctx, status):
+    if status != 0:
+        lib = load_library()
+        msg = lib.pbs_last_error(ctx).decode() if ctx else lib.pbs_status_string(status).decode()
+        raise PbsError(status, msg)
+
+
+# ---------------------------------------------------------------- C-ABI names
+
+def pbs_create(grid: PbsGrid, precision: int, stream: int | None) -> int:
+    lib = load_library()
+    out = _VP()
+    st = lib.pbs_create(ctypes.byref(out), ctypes.byref(grid), int(precision), _VP(stream or 0))
+    if st != 0:
+        raise PbsError(st, lib.pbs_status_string(st).decode())
+    return out.value
+
+
+def pbs_workspace_size(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, load_library().pbs_workspace_size(_VP(ctx), ctypes.byref(n)))
+    return n.value
+
+
+def pbs_bind_workspace(ctx, dev_ptr: int, nbytes: int) -> None:
+    _check(ctx, load_library().pbs_bind_workspace(_VP(ctx), _VP(dev_ptr), nbytes))
+
+
+def pbs_set_physics(ctx, phys: PbsPhysics) -> None:
+    _check(ctx, load_library().pbs_set_physics(_VP(ctx), ctypes.byref(phys)))
+
+
+def pbs_get_tables(ctx, s_face, ts, sig, p1, p2, u, v) -> None:
+    _check(ctx, load_library().pbs_get_tables(_VP(ctx), *(_ptr(x) for x in (s_face, ts, sig, p1, p2, u, v))))
+
+
+def pbs_set_material(ctx, rho: np.ndarray, n_slabs: int) -> None:
+    _check(ctx, load_library().pbs_set_material(_VP(ctx), _ptr(rho), int(n_slabs)))
+
+
+def pbs_launch_beam(ctx, beam: PbsBeam) -> None:
+    _check(ctx, load_library().pbs_launch_beam(_VP(ctx), ctypes.byref(beam)))
+
+
+def pbs_step(ctx, n_steps: int) -> None:
+    _check(ctx, load_library().pbs_step(_VP(ctx), int(n_steps)))
+
+
+def pbs_get_depth(ctx) -> int:
+    s = ctypes.c_int()
+    _check(ctx, load_library().pbs_get_depth(_VP(ctx), ctypes.byref(s)))
+    return s.value
+
+
+def pbs_read_dose(ctx, out: np.ndarray) -> None:
+    _check(ctx, load_library().pbs_read_dose(_VP(ctx), _ptr(out), out.size))
+
+
+def pbs_read_fluence(ctx, out: np.ndarray) -> None:
+    _check(ctx, load_library().pbs_read_fluence(_VP(ctx), _ptr(out), out.size))
+
+
+def pbs_read_psi(ctx, k: int, out: np.ndarray) -> None:
+    _check(ctx, load_library().pbs_read_psi(_VP(ctx), int(k), _ptr(out), out.size))
+
+
+def pbs_write_psi(ctx, k: int, arr: np.ndarray) -> None:
+    _check(ctx, load_library().pbs_write_psi(_VP(ctx), int(k), _ptr(arr), arr.size))
+
+
+def pbs_substep_energy(ctx, h: float, slab: int, fluence_plane: int = -1) -> None:
+    _check(ctx, load_library().pbs_substep_energy(_VP(ctx), float(h), int(slab), int(fluence_plane)))
+
+
+def pbs_substep_transport(ctx, h: float) -> None:
+    _check(ctx, load_library().pbs_substep_transport(_VP(ctx), float(h)))
+
+
+def pbs_substep_angular(ctx, h: float, slab: int) -> None:
+    _check(ctx, load_library().pbs_substep_angular(_VP(ctx), float(h), int(slab)))
+
+
+def pbs_eval_source(ctx, k_from: int, slab: int, out: np.ndarray) -> None:
+    _check(ctx, load_library().pbs_eval_source(_VP(ctx), int(k_from), int(slab), _ptr(out), out.size))
+
+
+def pbs_kernel_launches(ctx) -> int:
+    n = ctypes.c_longlong()
+    _check(ctx, load_library().pbs_kernel_launches(_VP(ctx), ctypes.byref(n)))
+    return n.value
+
+
+def pbs_last_error(ctx) -> str:
+    return load_library().pbs_last_error(_VP(ctx)).decode()
+
+
+def pbs_destroy(ctx) -> None:
+    if ctx:
+        load_library().pbs_destroy(_VP(ctx))
+
+
+# ---------------------------------------------------------------- convenience
+
+DEFAULT_PHYSICS = dict(bk_alpha=0.0022, bk_p=1.77, x0=36.08, mp=938.272, es=13.6, sigma_ct=0.012, lambda_p1=0.05,
+                       g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0)
+_BEAM_DEFAULTS = dict(e0=100.0, sigma_e=1.0, y0=0.0, z0=0.0, sigma_y=0.3, sigma_z=0.3, u0=0.0, v0=0.0,
+                      sigma_u=1e-6, sigma_v=1e-6)
+
+
+class Solver:
+    """One beam context on the current CUDA device.
+
+    grid: dict with ny, nz, nu, nv, dy, dz, u_max, v_max, e_faces (ng+1, MeV);
+    nx: number of depth steps (dose slabs); dx: step (cm); n_scatter: K;
+    precision: 'fp64' | 'fp32' | 'mixed'; stream: a torch.cuda.Stream or None
+    (the current stream)."""
+
+    def __init__(self, grid: dict, nx: int, dx: float, n_scatter: int = 0, precision: str = "fp32",
+                 stream=None, physics: dict | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (the library has no CPU path)")
+        self.torch = torch
+        self.e_faces = np.ascontiguousarray(np.asarray(grid["e_faces"], dtype=np.float64))
+        self.ny, self.nz, self.nu, self.nv = (int(grid[k]) for k in ("ny", "nz", "nu", "nv"))
+        self.ng = len(self.e_faces) - 1
+        self.na = self.nu * self.nv
+        self.nx, self.dx, self.K = int(nx), float(dx), int(n_scatter)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._g = PbsGrid(self.ny, self.nz, self.ng, self.nu, self.nv, self.nx, self.K, float(grid["dy"]),
+                          float(grid["dz"]), self.dx, float(grid["u_max"]), float(grid["v_max"]),
+                          _ptr(self.e_faces))
+        self._precision = PRECISIONS[precision]
+        self.ctx = pbs_create(self._g, self._precision, self.stream.cuda_stream)
+        nbytes = pbs_workspace_size(self.ctx)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        pbs_bind_workspace(self.ctx, self.workspace.data_ptr(), nbytes)
+        self.set_physics(**(physics or {}))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pbs_destroy(self.ctx)
+            self.ctx = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def comp_shape(self):
+        return (self.ng, 2, self.nv, self.nu, self.ny, self.nz)
+
+    def set_physics(self, **kw):
+        p = dict(DEFAULT_PHYSICS)
+        p.update(kw)
+        pbs_set_physics(self.ctx, PbsPhysics(**p))
+
+    def tables(self) -> dict:
+        G, na = self.ng, self.na
+        out = dict(s_face=np.zeros(G + 1), ts=np.zeros(G), sig=np.zeros(G), p1=np.zeros((G, G)),
+                   p2=np.zeros((G, na, na)), u=np.zeros(self.nu), v=np.zeros(self.nv))
+        pbs_get_tables(self.ctx, out["s_face"], out["ts"], out["sig"], out["p1"], out["p2"], out["u"], out["v"])
+        return out
+
+    def set_material(self, rho):
+        rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64)).reshape(-1, self.ny, self.nz)
+        pbs_set_material(self.ctx, rho, rho.shape[0])
+
+    def launch_beam(self, **beam):
+        b = dict(_BEAM_DEFAULTS)
+        b.update({k: float(v) for k, v in beam.items() if k in b})
+        pbs_launch_beam(self.ctx, PbsBeam(**b))
+
+    def step(self, n: int):
+        pbs_step(self.ctx, n)
+
+    @property
+    def depth(self) -> int:
+        return pbs_get_depth(self.ctx)
+
+    def read_dose(self, n_slabs: int | None = None):
+        n = self.nx if n_slabs is None else n_slabs
+        out = np.zeros((n, self.ny, self.nz))
+        pbs_read_dose(self.ctx, out)
+        return out
+
+    def read_fluence(self, n_planes: int | None = None):
+        n = self.depth + 1 if n_planes is None else n_planes
+        out = np.zeros((n, self.ny, self.nz))
+        pbs_read_fluence(self.ctx, out)
+        return out
+
+    def read_psi(self, k: int = 0):
+        out = np.zeros(self.comp_shape)
+        pbs_read_psi(self.ctx, k, out)
+        return out
+
+    def write_psi(self, k: int, arr):
+        a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64)).reshape(self.comp_shape)
+        pbs_write_psi(self.ctx, k, a)
+
+    def psi_view(self, k: int = 0):
+        """Device view (torch tensor, no copy) of component k in the documented
+        layout [g][c][v][u][y][z]; psi sits at the start of the workspace."""
+        torch = self.torch
+        dt = torch.float64 if self._precision == PBS_FP64 else torch.float32
+        n = int(np.prod(self.comp_shape))
+        esz = 8 if dt == torch.float64 else 4
+        raw = self.workspace[k * n * esz:(k + 1) * n * esz]
+        return raw.view(dt).view(self.comp_shape)
+
+    def substep_energy(self, h, slab, fluence_plane=-1):
+        pbs_substep_energy(self.ctx, h, slab, fluence_plane)
+
+    def substep_transport(self, h):
+        pbs_substep_transport(self.ctx, h)
+
+    def substep_angular(self, h, slab):
+        pbs_substep_angular(self.ctx, h, slab)
+
+    def eval_source(self, k_from: int, slab: int):
+        out = np.zeros((self.ng, self.nv, self.nu, self.ny, self.nz))
+        pbs_eval_source(self.ctx, k_from, slab, out)
+        return out
+
+    @property
+    def kernel_launches(self) -> int:
+        return pbs_kernel_launches(self.ctx)

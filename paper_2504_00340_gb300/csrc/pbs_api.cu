@@ -1,0 +1,609 @@
+// pbs_api.cu -- C ABI of the library (include/pbs.h): context, caller-bound
+// workspace, FP64 host tables, beam projection and the depth-march driver.
+//
+// Per depth step s (Section 3.3, Strang splitting with Crank-Nicolson in each
+// subsystem) every component k = 0..K goes through
+//   E(h/2)  T(h/2)  A(h)  T(h/2)  E(h/2)
+// with the density of slab s.  In each E substep the components run in
+// order; component k (k >= 1) takes the catastrophic source of component
+// k-1 (Section 3.1, Eq. pri-se; Remark 1) evaluated at the start and end of
+// the same substep (trapezoid), which the energy kernel of k-1 emits fused as
+// R and the contraction kernel turns into src = du dv P^2_g R.
+#include "pbs_internal.cuh"
+#include "pbs.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace pbs;
+
+struct pbs_ctx {
+  int dev = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  int precision = PBS_FP32;
+  int ny, nz, ng, nu, nv, na, nx, K;
+  double dy, dz, dx, u_max, v_max, du, dv;
+  std::vector<double> e_faces, e_c, de;
+  Dims d;
+  // FP64 host tables
+  std::vector<double> s_face, ts, sig, p1, p2, q1, decay, u, v;
+  bool have_tables = false, have_material = false, have_beam = false;
+  int n_slabs = 0;
+  int steps_done = 0;
+  // workspace
+  unsigned char *ws = nullptr;
+  size_t ws_bytes = 0;
+  size_t off_psi, off_r, off_s, off_rho, off_dose, off_flu, off_coef, off_ts, off_p2, off_init, off_err, total;
+  size_t rsize, ssize;  // element sizes of real and of the source storage
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+pbs_status fail(pbs_ctx *c, pbs_status st, const std::string &msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+pbs_status cuda_fail(pbs_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, PBS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PBS_CUDA(c, call)                                \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+void layout(pbs_ctx *c) {
+  const size_t S = c->rsize, SS = c->ssize;
+  const size_t nyz = (size_t)c->ny * c->nz;
+  size_t o = 0;
+  c->off_psi = o; o = align256(o + (size_t)c->d.ncomp * c->d.comp_elems * S);
+  const size_t nsrc = (c->K > 0) ? (size_t)c->ng * c->na * nyz : 0;
+  c->off_r = o; o = align256(o + nsrc * SS);
+  c->off_s = o; o = align256(o + nsrc * SS);
+  c->off_rho = o; o = align256(o + (size_t)c->nx * nyz * S);
+  c->off_dose = o; o = align256(o + (size_t)c->nx * nyz * 8);
+  c->off_flu = o; o = align256(o + (size_t)(c->nx + 1) * nyz * 8);
+  c->off_coef = o; o = align256(o + (size_t)c->ng * 10 * S);
+  c->off_ts = o; o = align256(o + (size_t)c->ng * S);
+  c->off_p2 = o; o = align256(o + ((c->K > 0) ? (size_t)c->ng * c->na * c->na * SS : 0));
+  c->off_init = o; o = align256(o + (size_t)(2 * c->ng + c->na + c->ny + c->nz) * 8);
+  c->off_err = o; o = align256(o + 64);
+  c->total = o;
+}
+
+template <typename T>
+T *at(pbs_ctx *c, size_t off) { return reinterpret_cast<T *>(c->ws + off); }
+
+LaunchCtx lctx(pbs_ctx *c) { return LaunchCtx{c->stream, c->num_sms, &c->launches}; }
+
+// ---------------------------------------------------------------- host tables
+
+// Mass stopping power of the Bragg-Kleeman range law R(E) = alpha E^p:
+// S(E) = 1 / R'(E).
+double stopping_bk(const pbs_physics &ph, double e) {
+  return ph.s_scale / (ph.bk_alpha * ph.bk_p * std::pow(e, ph.bk_p - 1.0));
+}
+
+// Primitive of the Highland scattering power (Es / pv)^2 / X0 in E, with
+// pv = E (E + 2M) / (E + M):  (Es^2/X0) [ ln(E/(E+2M)) / (4M) - (E+M) / (2E(E+2M)) ].
+double highland_primitive(const pbs_physics &ph, double e) {
+  const double m = ph.mp;
+  return ph.es * ph.es / ph.x0 * (std::log(e / (e + 2.0 * m)) / (4.0 * m) - (e + m) / (2.0 * e * (e + 2.0 * m)));
+}
+
+double gamma_density(double th, double al, double be) {
+  if (!(th > 0.0)) return al == 1.0 ? be : 0.0;
+  return std::exp(al * std::log(be) + (al - 1.0) * std::log(th) - be * th - std::lgamma(al));
+}
+
+void build_tables(pbs_ctx *c, const pbs_physics &ph) {
+  const int G = c->ng, na = c->na;
+  c->s_face.assign(G + 1, 0.0);
+  c->ts.assign(G, 0.0);
+  c->sig.assign(G, ph.sigma_ct);
+  c->p1.assign((size_t)G * G, 0.0);
+  c->q1.assign(G, 0.0);
+  c->decay.assign(G, 0.0);
+  // a face at E <= 0 takes the stopping power at half the lowest group width
+  const double floor_e = 0.5 * c->de[0];
+  for (int f = 0; f <= G; f++) c->s_face[f] = stopping_bk(ph, std::max(c->e_faces[f], floor_e));
+  for (int g = 0; g < G; g++) {
+    const double lo = std::max(c->e_faces[g], floor_e), hi = c->e_faces[g + 1];
+    c->ts[g] = ph.ts_scale * (highland_primitive(ph, hi) - highland_primitive(ph, lo)) / (hi - lo);
+  }
+  // exponential energy transfer, normalised per emitting group g'
+  for (int gp = 0; gp < G; gp++) {
+    double z = 0.0;
+    for (int g = gp; g >= 0; g--) z += ph.lambda_p1 * std::exp(-ph.lambda_p1 * (c->e_c[gp] - c->e_c[g]));
+    for (int g = 0; g <= gp; g++)
+      c->p1[(size_t)gp * G + g] = ph.lambda_p1 * std::exp(-ph.lambda_p1 * (c->e_c[gp] - c->e_c[g])) / z;
+    c->q1[gp] = ph.lambda_p1 * ph.sigma_ct * c->de[gp] / z;
+    c->decay[gp] = (gp + 1 < G) ? std::exp(-ph.lambda_p1 * (c->e_c[gp + 1] - c->e_c[gp])) : 0.0;
+  }
+  // angular transfer: Gamma density of the angle between (1,u',v') and (1,u,v),
+  // normalised so that sum_a P2 du dv = 1 for every incoming a'
+  c->p2.assign((size_t)G * na * na, 0.0);
+  std::vector<double> col(na);
+  for (int ap = 0; ap < na; ap++) {
+    const double u1 = c->u[ap % c->nu], v1 = c->v[ap / c->nu];
+    double k = 0.0;
+    for (int a = 0; a < na; a++) {
+      const double u2 = c->u[a % c->nu], v2 = c->v[a / c->nu];
+      const double cx = u2 * v1 - v2 * u1, cy = v2 - v1, cz = u1 - u2;  // (1,u2,v2) x (1,u1,v1)
+      const double th = std::atan2(std::sqrt(cx * cx + cy * cy + cz * cz), 1.0 + u1 * u2 + v1 * v2);
+      col[a] = gamma_density(th, ph.g_alpha, ph.g_beta);
+      k += col[a];
+    }
+    k *= c->du * c->dv;
+    for (int g = 0; g < G; g++)
+      for (int a = 0; a < na; a++) c->p2[((size_t)g * na + a) * na + ap] = k > 0.0 ? col[a] / k : 0.0;
+  }
+}
+
+template <typename st>
+st to_storage(double x) { return (st)x; }
+template <>
+__nv_bfloat16 to_storage<__nv_bfloat16>(double x) { return __float2bfloat16_rn((float)x); }
+
+template <typename st>
+double from_storage(st x) { return (double)x; }
+template <>
+double from_storage<__nv_bfloat16>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+
+template <typename real, typename st>
+pbs_status upload_tables(pbs_ctx *c) {
+  const int G = c->ng;
+  std::vector<GroupCoef<real>> coef(G);
+  for (int g = 0; g < G; g++) {
+    GroupCoef<real> &k = coef[g];
+    k.sm = (real)(c->s_face[g] / c->de[g]);
+    k.sp = (real)(c->s_face[g + 1] / c->de[g]);
+    k.sig = (real)c->sig[g];
+    k.ehat = (real)(c->e_c[g] * c->de[g]);
+    k.dq = (real)(c->de[g] * c->de[g] / 6.0);
+    k.de = (real)c->de[g];
+    k.inv_de = (real)(1.0 / c->de[g]);
+    k.q1 = (real)c->q1[g];
+    k.decay = (real)c->decay[g];
+    k.pad = 0;
+  }
+  std::vector<real> ts(G);
+  for (int g = 0; g < G; g++) ts[g] = (real)c->ts[g];
+  PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_coef), coef.data(), sizeof(GroupCoef<real>) * G,
+                              cudaMemcpyHostToDevice, c->stream));
+  PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_ts), ts.data(), sizeof(real) * G, cudaMemcpyHostToDevice, c->stream));
+  std::vector<st> p2;
+  if (c->K > 0) {
+    p2.resize(c->p2.size());
+    for (size_t e = 0; e < p2.size(); e++) p2[e] = to_storage<st>(c->p2[e]);
+    PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_p2), p2.data(), sizeof(st) * p2.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+  }
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));  // host staging buffers die here
+  return PBS_OK;
+}
+
+// ---------------------------------------------------------------- beam
+
+double std_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+
+// mass of N(mu, s^2) in [lo, hi], evaluated on the tail side for accuracy
+double normal_mass(double lo, double hi, double mu, double s) {
+  const double a = (lo - mu) / s, b = (hi - mu) / s;
+  if (a > 0.0) return std_cdf(-a) - std_cdf(-b);
+  return std_cdf(b) - std_cdf(a);
+}
+
+void beam_factors(const pbs_ctx *c, const pbs_beam &b, std::vector<double> &out) {
+  const int G = c->ng, na = c->na;
+  out.assign(2 * G + na + c->ny + c->nz, 0.0);
+  double *fe = out.data(), *fa = fe + 2 * G, *fy = fa + na, *fz = fy + c->ny;
+  const double inv_sqrt_2pi = 0.3989422804014326779;
+  double ne = 0.0, nang = 0.0, nyy = 0.0, nzz = 0.0;
+  for (int g = 0; g < G; g++) {
+    const double lo = c->e_faces[g], hi = c->e_faces[g + 1], de = c->de[g];
+    const double m0 = normal_mass(lo, hi, b.e0, b.sigma_e);
+    const double za = (lo - b.e0) / b.sigma_e, zb = (hi - b.e0) / b.sigma_e;
+    // int (E - E_g) N(E) dE = s (n(za) - n(zb)) + (E0 - E_g) m0
+    const double m1 = b.sigma_e * inv_sqrt_2pi * (std::exp(-0.5 * za * za) - std::exp(-0.5 * zb * zb)) +
+                      (b.e0 - c->e_c[g]) * m0;
+    fe[2 * g] = m0 / de;                  // (1/dE) int N
+    fe[2 * g + 1] = 6.0 * m1 / (de * de); // (3/dE) int N phi^2, phi^2 = 2 (E - E_g)/dE
+    ne += fe[2 * g] * de;
+  }
+  for (int j = 0; j < c->nv; j++)
+    for (int i = 0; i < c->nu; i++) {
+      const double pu = normal_mass(c->u[i] - 0.5 * c->du, c->u[i] + 0.5 * c->du, b.u0, b.sigma_u) / c->du;
+      const double pv = normal_mass(c->v[j] - 0.5 * c->dv, c->v[j] + 0.5 * c->dv, b.v0, b.sigma_v) / c->dv;
+      fa[j * c->nu + i] = pu * pv;
+      nang += pu * pv * c->du * c->dv;
+    }
+  for (int p = 0; p < c->ny; p++) {
+    fy[p] = normal_mass((p - 0.5 * c->ny) * c->dy, (p + 1 - 0.5 * c->ny) * c->dy, b.y0, b.sigma_y) / c->dy;
+    nyy += fy[p] * c->dy;
+  }
+  for (int q = 0; q < c->nz; q++) {
+    fz[q] = normal_mass((q - 0.5 * c->nz) * c->dz, (q + 1 - 0.5 * c->nz) * c->dz, b.z0, b.sigma_z) / c->dz;
+    nzz += fz[q] * c->dz;
+  }
+  const double norm = 1.0 / (ne * nang * nyy * nzz);
+  for (int e = 0; e < 2 * G; e++) fe[e] *= norm;
+}
+
+// ---------------------------------------------------------------- march
+
+template <typename real, typename st>
+pbs_status energy_all(pbs_ctx *c, double h, int slab, int flu_plane) {
+  LaunchCtx lc = lctx(c);
+  const size_t nyz = (size_t)c->ny * c->nz;
+  real *psi = at<real>(c, c->off_psi);
+  const real *rho = at<real>(c, c->off_rho) + (size_t)slab * nyz;
+  double *dose = at<double>(c, c->off_dose) + (size_t)slab * nyz;
+  double *flu = flu_plane >= 0 ? at<double>(c, c->off_flu) + (size_t)flu_plane * nyz : nullptr;
+  st *rbuf = at<st>(c, c->off_r), *sbuf = at<st>(c, c->off_s);
+  const auto *coef = at<GroupCoef<real>>(c, c->off_coef);
+  for (int k = 0; k <= c->K; k++) {
+    cudaError_t e = launch_energy<real, st>(lc, c->d, psi + (size_t)k * c->d.comp_elems, k >= 1 ? sbuf : nullptr,
+                                            k < c->K ? rbuf : nullptr, rho, coef, dose, flu, (real)(0.5 * h),
+                                            c->du * c->dv / c->dx, c->du * c->dv);
+    if (e != cudaSuccess) return cuda_fail(c, e, "energy kernel");
+    if (k < c->K) {
+      e = launch_source<real, st>(lc, c->d, at<st>(c, c->off_p2), rbuf, sbuf, c->du * c->dv);
+      if (e != cudaSuccess) return cuda_fail(c, e, "source kernel");
+    }
+  }
+  return PBS_OK;
+}
+
+template <typename real>
+pbs_status transport_all(pbs_ctx *c, double h) {
+  cudaError_t e = launch_transport<real>(lctx(c), c->d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz,
+                                         at<int>(c, c->off_err));
+  return e == cudaSuccess ? PBS_OK : cuda_fail(c, e, "transport kernel");
+}
+
+template <typename real>
+pbs_status angular_all(pbs_ctx *c, double h, int slab) {
+  const size_t nyz = (size_t)c->ny * c->nz;
+  cudaError_t e = launch_angular<real>(lctx(c), c->d, at<real>(c, c->off_psi),
+                                       at<real>(c, c->off_rho) + (size_t)slab * nyz, at<real>(c, c->off_ts), h, c->du,
+                                       c->dv);
+  return e == cudaSuccess ? PBS_OK : cuda_fail(c, e, "angular kernel");
+}
+
+template <typename real, typename st>
+pbs_status step_impl(pbs_ctx *c, int n) {
+  for (int i = 0; i < n; i++) {
+    const int s = c->steps_done;
+    pbs_status r;
+    if ((r = energy_all<real, st>(c, 0.5 * c->dx, s, -1)) != PBS_OK) return r;
+    if ((r = transport_all<real>(c, 0.5 * c->dx)) != PBS_OK) return r;
+    if ((r = angular_all<real>(c, c->dx, s)) != PBS_OK) return r;
+    if ((r = transport_all<real>(c, 0.5 * c->dx)) != PBS_OK) return r;
+    if ((r = energy_all<real, st>(c, 0.5 * c->dx, s, s + 1)) != PBS_OK) return r;
+    c->steps_done++;
+  }
+  return PBS_OK;
+}
+
+template <typename real, typename st>
+pbs_status launch_impl(pbs_ctx *c, const pbs_beam &b) {
+  const size_t nyz = (size_t)c->ny * c->nz;
+  std::vector<double> f;
+  beam_factors(c, b, f);
+  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_psi), 0, (size_t)c->d.ncomp * c->d.comp_elems * sizeof(real),
+                              c->stream));
+  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_dose), 0, (size_t)c->nx * nyz * 8, c->stream));
+  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_flu), 0, (size_t)(c->nx + 1) * nyz * 8, c->stream));
+  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_err), 0, 64, c->stream));
+  PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_init), f.data(), f.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  const double *fe = at<double>(c, c->off_init);
+  cudaError_t e = launch_init<real>(lctx(c), c->d, at<real>(c, c->off_psi), fe, fe + 2 * c->ng,
+                                    fe + 2 * c->ng + c->na, fe + 2 * c->ng + c->na + c->ny);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+  e = launch_fluence<real>(lctx(c), c->d, at<real>(c, c->off_psi), at<GroupCoef<real>>(c, c->off_coef),
+                           at<double>(c, c->off_flu), c->du * c->dv);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fluence kernel");
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));  // f dies here
+  c->steps_done = 0;
+  return PBS_OK;
+}
+
+pbs_status check_device_status(pbs_ctx *c) {
+  int w[2] = {0, 0};
+  PBS_CUDA(c, cudaMemcpyAsync(w, at<void>(c, c->off_err), sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (w[0] != 0) return fail(c, PBS_ERR_TIMEOUT, "a device wait gave up (code " + std::to_string(w[1]) + ")");
+  return PBS_OK;
+}
+
+template <typename real>
+pbs_status read_psi_impl(pbs_ctx *c, int k, double *out) {
+  std::vector<real> tmp(c->d.comp_elems);
+  PBS_CUDA(c, cudaMemcpyAsync(tmp.data(), at<real>(c, c->off_psi) + (size_t)k * c->d.comp_elems,
+                              sizeof(real) * tmp.size(), cudaMemcpyDeviceToHost, c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (size_t e = 0; e < tmp.size(); e++) out[e] = (double)tmp[e];
+  return check_device_status(c);
+}
+
+template <typename real>
+pbs_status write_psi_impl(pbs_ctx *c, int k, const double *in) {
+  std::vector<real> tmp(c->d.comp_elems);
+  for (size_t e = 0; e < tmp.size(); e++) tmp[e] = (real)in[e];
+  PBS_CUDA(c, cudaMemcpyAsync(at<real>(c, c->off_psi) + (size_t)k * c->d.comp_elems, tmp.data(),
+                              sizeof(real) * tmp.size(), cudaMemcpyHostToDevice, c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PBS_OK;
+}
+
+template <typename real>
+pbs_status set_material_impl(pbs_ctx *c, const double *rho, int n) {
+  const size_t cnt = (size_t)n * c->ny * c->nz;
+  std::vector<real> tmp(cnt);
+  for (size_t e = 0; e < cnt; e++) tmp[e] = (real)rho[e];
+  PBS_CUDA(c, cudaMemcpyAsync(at<real>(c, c->off_rho), tmp.data(), sizeof(real) * cnt, cudaMemcpyHostToDevice,
+                              c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PBS_OK;
+}
+
+template <typename real, typename st>
+pbs_status eval_source_impl(pbs_ctx *c, int k_from, int slab, double *out) {
+  const size_t nyz = (size_t)c->ny * c->nz;
+  cudaError_t e = launch_source_input(lctx(c), c->d, at<real>(c, c->off_psi) + (size_t)k_from * c->d.comp_elems,
+                                      at<real>(c, c->off_rho) + (size_t)slab * nyz, at<void>(c, c->off_coef),
+                                      at<void>(c, c->off_r), c->precision);
+  if (e != cudaSuccess) return cuda_fail(c, e, "source input kernel");
+  e = launch_source<real, st>(lctx(c), c->d, at<st>(c, c->off_p2), at<st>(c, c->off_r), at<st>(c, c->off_s),
+                              c->du * c->dv);
+  if (e != cudaSuccess) return cuda_fail(c, e, "source kernel");
+  const size_t n = (size_t)c->ng * c->na * nyz;
+  std::vector<st> tmp(n);
+  PBS_CUDA(c, cudaMemcpyAsync(tmp.data(), at<st>(c, c->off_s), sizeof(st) * n, cudaMemcpyDeviceToHost, c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < n; i++) out[i] = from_storage<st>(tmp[i]);
+  return PBS_OK;
+}
+
+bool ready_to_march(pbs_ctx *c) { return c->ws && c->have_tables && c->have_material && c->have_beam; }
+
+}  // namespace
+
+#define PBS_DISPATCH(c, FN, ...)                                                    \
+  ((c)->precision == PBS_FP64    ? FN<double, double>(__VA_ARGS__)                  \
+   : (c)->precision == PBS_FP32 ? FN<float, float>(__VA_ARGS__)                     \
+                                 : FN<float, __nv_bfloat16>(__VA_ARGS__))
+#define PBS_DISPATCH_R(c, FN, ...) \
+  ((c)->precision == PBS_FP64 ? FN<double>(__VA_ARGS__) : FN<float>(__VA_ARGS__))
+
+extern "C" {
+
+pbs_status pbs_create(pbs_ctx **out, const pbs_grid *g, int precision, void *stream) {
+  if (!out || !g || !g->e_faces) return PBS_ERR_ARG;
+  *out = nullptr;
+  if (g->ny < 1 || g->nz < 1 || g->ng < 1 || g->nu < 1 || g->nv < 1 || g->nx < 1 || g->n_scatter < 0 ||
+      !(g->dy > 0) || !(g->dz > 0) || !(g->dx > 0) || !(g->u_max > 0) || !(g->v_max > 0))
+    return PBS_ERR_ARG;
+  if (precision < PBS_FP64 || precision > PBS_MIXED) return PBS_ERR_ARG;
+  for (int f = 0; f < g->ng; f++)
+    if (!(g->e_faces[f + 1] > g->e_faces[f])) return PBS_ERR_ARG;
+  if (!angular_supported(g->nu, g->nv) || g->nz > 1024 || g->ng > 2048) return PBS_ERR_UNSUPPORTED;
+  pbs_ctx *c = new (std::nothrow) pbs_ctx();
+  if (!c) return PBS_ERR_NOMEM;
+  if (cudaGetDevice(&c->dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
+    delete c;
+    return PBS_ERR_CUDA;
+  }
+  c->stream = (cudaStream_t)stream;
+  c->precision = precision;
+  c->ny = g->ny; c->nz = g->nz; c->ng = g->ng; c->nu = g->nu; c->nv = g->nv; c->na = g->nu * g->nv;
+  c->nx = g->nx; c->K = g->n_scatter;
+  c->dy = g->dy; c->dz = g->dz; c->dx = g->dx; c->u_max = g->u_max; c->v_max = g->v_max;
+  c->du = 2.0 * g->u_max / (g->nu + 1);
+  c->dv = 2.0 * g->v_max / (g->nv + 1);
+  c->e_faces.assign(g->e_faces, g->e_faces + g->ng + 1);
+  c->e_c.resize(g->ng);
+  c->de.resize(g->ng);
+  for (int k = 0; k < g->ng; k++) {
+    c->de[k] = c->e_faces[k + 1] - c->e_faces[k];
+    c->e_c[k] = 0.5 * (c->e_faces[k + 1] + c->e_faces[k]);
+  }
+  c->u.resize(g->nu);
+  c->v.resize(g->nv);
+  for (int i = 0; i < g->nu; i++) c->u[i] = (i - 0.5 * (g->nu - 1)) * c->du;
+  for (int j = 0; j < g->nv; j++) c->v[j] = (j - 0.5 * (g->nv - 1)) * c->dv;
+  Dims &d = c->d;
+  d.ny = c->ny; d.nz = c->nz; d.ng = c->ng; d.nu = c->nu; d.nv = c->nv; d.na = c->na;
+  d.nyz = c->ny * c->nz; d.ncomp = c->K + 1;
+  d.lanes = (long long)d.na * d.nyz;
+  d.comp_elems = (long long)d.ng * 2 * d.lanes;
+  c->rsize = precision == PBS_FP64 ? 8 : 4;
+  c->ssize = precision == PBS_FP64 ? 8 : (precision == PBS_FP32 ? 4 : 2);
+  layout(c);
+  *out = c;
+  return PBS_OK;
+}
+
+pbs_status pbs_workspace_size(const pbs_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return PBS_ERR_ARG;
+  *bytes = c->total;
+  return PBS_OK;
+}
+
+pbs_status pbs_bind_workspace(pbs_ctx *c, void *p, size_t bytes) {
+  if (!c || !p) return fail(c, PBS_ERR_ARG, "null workspace");
+  if (bytes < c->total) return fail(c, PBS_ERR_ARG, "workspace too small");
+  if (((uintptr_t)p) & 255) return fail(c, PBS_ERR_ARG, "workspace not 256-byte aligned");
+  c->ws = (unsigned char *)p;
+  c->ws_bytes = bytes;
+  c->have_beam = false;
+  c->have_material = false;
+  // start from a defined state: zero state, tallies and the device status word
+  PBS_CUDA(c, cudaMemsetAsync(c->ws, 0, c->total, c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->have_tables) {
+    pbs_status r = PBS_DISPATCH(c, upload_tables, c);
+    if (r != PBS_OK) return r;
+  }
+  return PBS_OK;
+}
+
+pbs_status pbs_set_physics(pbs_ctx *c, const pbs_physics *ph) {
+  if (!c || !ph) return fail(c, PBS_ERR_ARG, "null physics");
+  if (!(ph->bk_alpha > 0) || !(ph->bk_p > 0) || !(ph->x0 > 0) || !(ph->mp > 0) || !(ph->lambda_p1 > 0) ||
+      !(ph->g_beta > 0) || !(ph->g_alpha > 0) || ph->sigma_ct < 0 || ph->s_scale < 0 || ph->ts_scale < 0)
+    return fail(c, PBS_ERR_ARG, "physics parameters out of range");
+  build_tables(c, *ph);
+  c->have_tables = true;
+  if (!c->ws) return PBS_OK;  // uploaded at bind time
+  return PBS_DISPATCH(c, upload_tables, c);
+}
+
+pbs_status pbs_get_tables(const pbs_ctx *c, double *s_face, double *ts, double *sig, double *p1, double *p2, double *u,
+                          double *v) {
+  if (!c) return PBS_ERR_ARG;
+  if (!c->have_tables) return PBS_ERR_STATE;
+  if (s_face) std::memcpy(s_face, c->s_face.data(), 8 * c->s_face.size());
+  if (ts) std::memcpy(ts, c->ts.data(), 8 * c->ts.size());
+  if (sig) std::memcpy(sig, c->sig.data(), 8 * c->sig.size());
+  if (p1) std::memcpy(p1, c->p1.data(), 8 * c->p1.size());
+  if (p2) std::memcpy(p2, c->p2.data(), 8 * c->p2.size());
+  if (u) std::memcpy(u, c->u.data(), 8 * c->u.size());
+  if (v) std::memcpy(v, c->v.data(), 8 * c->v.size());
+  return PBS_OK;
+}
+
+pbs_status pbs_set_material(pbs_ctx *c, const double *rho, int n) {
+  if (!c || !rho || n < 1 || n > c->nx) return fail(c, PBS_ERR_ARG, "bad material");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "bind a workspace first");
+  for (size_t e = 0; e < (size_t)n * c->ny * c->nz; e++)
+    if (!(rho[e] >= 0.0) || !std::isfinite(rho[e])) return fail(c, PBS_ERR_ARG, "density must be finite and >= 0");
+  pbs_status r = PBS_DISPATCH_R(c, set_material_impl, c, rho, n);
+  if (r != PBS_OK) return r;
+  c->n_slabs = n;
+  c->have_material = true;
+  return PBS_OK;
+}
+
+pbs_status pbs_launch_beam(pbs_ctx *c, const pbs_beam *b) {
+  if (!c || !b) return fail(c, PBS_ERR_ARG, "null beam");
+  if (!c->ws || !c->have_tables) return fail(c, PBS_ERR_STATE, "bind a workspace and set the physics first");
+  if (!(b->sigma_e > 0) || !(b->sigma_y > 0) || !(b->sigma_z > 0) || !(b->sigma_u > 0) || !(b->sigma_v > 0))
+    return fail(c, PBS_ERR_ARG, "beam widths must be > 0");
+  pbs_status r = PBS_DISPATCH(c, launch_impl, c, *b);
+  if (r != PBS_OK) return r;
+  c->have_beam = true;
+  return PBS_OK;
+}
+
+pbs_status pbs_step(pbs_ctx *c, int n) {
+  if (!c || n < 0) return fail(c, PBS_ERR_ARG, "bad step count");
+  if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
+  if (c->steps_done + n > c->n_slabs) return fail(c, PBS_ERR_ARG, "march would pass the last material slab");
+  return PBS_DISPATCH(c, step_impl, c, n);
+}
+
+pbs_status pbs_get_depth(const pbs_ctx *c, int *s) {
+  if (!c || !s) return PBS_ERR_ARG;
+  *s = c->steps_done;
+  return PBS_OK;
+}
+
+pbs_status pbs_read_dose(pbs_ctx *c, double *out, size_t n) {
+  if (!c || !out) return fail(c, PBS_ERR_ARG, "null output");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  const size_t nyz = (size_t)c->ny * c->nz;
+  if (n % nyz != 0 || n / nyz > (size_t)c->nx) return fail(c, PBS_ERR_ARG, "n must be n_slabs*ny*nz");
+  PBS_CUDA(c, cudaMemcpyAsync(out, at<void>(c, c->off_dose), n * 8, cudaMemcpyDeviceToHost, c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_device_status(c);
+}
+
+pbs_status pbs_read_fluence(pbs_ctx *c, double *out, size_t n) {
+  if (!c || !out) return fail(c, PBS_ERR_ARG, "null output");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  const size_t nyz = (size_t)c->ny * c->nz;
+  if (n % nyz != 0 || n / nyz > (size_t)c->steps_done + 1) return fail(c, PBS_ERR_ARG, "n must be n_planes*ny*nz");
+  PBS_CUDA(c, cudaMemcpyAsync(out, at<void>(c, c->off_flu), n * 8, cudaMemcpyDeviceToHost, c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_device_status(c);
+}
+
+pbs_status pbs_read_psi(pbs_ctx *c, int k, double *out, size_t n) {
+  if (!c || !out || k < 0 || k > c->K) return fail(c, PBS_ERR_ARG, "bad component");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  if (n != (size_t)c->d.comp_elems) return fail(c, PBS_ERR_ARG, "n must be ng*2*nu*nv*ny*nz");
+  return PBS_DISPATCH_R(c, read_psi_impl, c, k, out);
+}
+
+pbs_status pbs_write_psi(pbs_ctx *c, int k, const double *in, size_t n) {
+  if (!c || !in || k < 0 || k > c->K) return fail(c, PBS_ERR_ARG, "bad component");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  if (n != (size_t)c->d.comp_elems) return fail(c, PBS_ERR_ARG, "n must be ng*2*nu*nv*ny*nz");
+  return PBS_DISPATCH_R(c, write_psi_impl, c, k, in);
+}
+
+pbs_status pbs_substep_energy(pbs_ctx *c, double h, int slab, int flu_plane) {
+  if (!c || !(h >= 0) || slab < 0 || slab >= c->n_slabs || flu_plane > c->nx)
+    return fail(c, PBS_ERR_ARG, "bad substep arguments");
+  if (!c->ws || !c->have_tables || !c->have_material) return fail(c, PBS_ERR_STATE, "not set up");
+  return PBS_DISPATCH(c, energy_all, c, h, slab, flu_plane);
+}
+
+pbs_status pbs_substep_transport(pbs_ctx *c, double h) {
+  if (!c || !(h >= 0)) return fail(c, PBS_ERR_ARG, "bad substep arguments");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "not set up");
+  return PBS_DISPATCH_R(c, transport_all, c, h);
+}
+
+pbs_status pbs_substep_angular(pbs_ctx *c, double h, int slab) {
+  if (!c || !(h >= 0) || slab < 0 || slab >= c->n_slabs) return fail(c, PBS_ERR_ARG, "bad substep arguments");
+  if (!c->ws || !c->have_tables || !c->have_material) return fail(c, PBS_ERR_STATE, "not set up");
+  return PBS_DISPATCH_R(c, angular_all, c, h, slab);
+}
+
+pbs_status pbs_eval_source(pbs_ctx *c, int k_from, int slab, double *out, size_t n) {
+  if (!c || !out || k_from < 0 || k_from > c->K || slab < 0 || slab >= c->n_slabs)
+    return fail(c, PBS_ERR_ARG, "bad arguments");
+  if (c->K < 1) return fail(c, PBS_ERR_STATE, "the context has no scattered component (n_scatter = 0)");
+  if (!c->ws || !c->have_tables || !c->have_material) return fail(c, PBS_ERR_STATE, "not set up");
+  if (n != (size_t)c->ng * c->na * c->ny * c->nz) return fail(c, PBS_ERR_ARG, "n must be ng*nu*nv*ny*nz");
+  return PBS_DISPATCH(c, eval_source_impl, c, k_from, slab, out);
+}
+
+pbs_status pbs_kernel_launches(const pbs_ctx *c, long long *count) {
+  if (!c || !count) return PBS_ERR_ARG;
+  *count = c->launches;
+  return PBS_OK;
+}
+
+const char *pbs_last_error(const pbs_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+const char *pbs_status_string(int s) {
+  switch (s) {
+    case PBS_OK: return "ok";
+    case PBS_ERR_ARG: return "invalid argument";
+    case PBS_ERR_CUDA: return "CUDA error";
+    case PBS_ERR_NOMEM: return "out of memory";
+    case PBS_ERR_STATE: return "call out of order";
+    case PBS_ERR_TIMEOUT: return "device wait timed out";
+    case PBS_ERR_UNSUPPORTED: return "unsupported grid";
+  }
+  return "unknown status";
+}
+
+void pbs_destroy(pbs_ctx *c) { delete c; }
+
+}  // extern "C"

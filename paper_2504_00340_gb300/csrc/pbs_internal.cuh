@@ -1,0 +1,167 @@
+// pbs_internal.cuh -- device-side definitions shared by the library's kernels.
+//
+// Layout of the device workspace (one context):
+//   psi   [k][g][c][a][p][q]      (K+1) components, real = double or float
+//   rbuf  [g][a][p][q]            energy-summed catastrophic source input R (K>0)
+//   sbuf  [g][a][p][q]            catastrophic source src = du dv P2_g R  (K>0)
+//   rho   [s][p][q]               density per depth slab, real
+//   dose  [s][p][q]               FP64 dose tally
+//   flu   [s][p][q]               FP64 planar fluence at depth s*dx
+//   coef  [g]                     GroupCoef<real>
+//   ts    [g]                     group-averaged scattering power, real
+//   p2    [g][a][a']              P^2 densities (source storage type)
+//   err   int[4]                  device status word (timeouts)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace pbs {
+
+constexpr int kMaxAngle = 16;  // nu, nv <= 16 on the device path
+
+// Per-group energy coefficients, per unit density (multiply by rho).
+template <typename real>
+struct GroupCoef {
+  real sm;      // S_{g-1/2} / dE_g
+  real sp;      // S_{g+1/2} / dE_g
+  real sig;     // sigma_ct (mass)
+  real ehat;    // E_g dE_g        (energy-content weight of psi^1)
+  real dq;      // dE_g^2 / 6      (energy-content weight of psi^2)
+  real de;      // dE_g            (particle-count weight of psi^1)
+  real inv_de;  // 1 / dE_g
+  real q1;      // lambda sigma_g dE_g / Z_g   (source weight of group g as emitter)
+  real decay;   // exp(-lambda (E_{g+1} - E_g)), 0 for the top group
+  real pad;
+};
+
+struct Dims {
+  int ny, nz, ng, nu, nv, na, nyz, ncomp;  // ncomp = K + 1
+  long long lanes;                          // na * nyz
+  long long comp_elems;                     // ng * 2 * lanes
+};
+
+// Device status word: slot 0 counts timeouts, slot 1 records where.
+enum : int { kErrTimeoutTransport = 1 };
+
+// ----------------------------------------------------------------------------
+// PTX helpers: shared-memory addresses, mbarriers, 1-D bulk (TMA) copies.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier to complete, giving up after about
+// `max_cycles` SM clocks.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, long long max_cycles) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > max_cycles) return false;
+  }
+  return true;
+}
+
+// Bulk copy global -> shared (async proxy), completion signalled on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ----------------------------------------------------------------------------
+// Superbee-limited slope and upwind face flux (Section 3.4, Eq. distansport).
+// slope(a, b) equals b * eta(a / b) with eta(t) = max[0, min(2t,1), min(t,2)]
+// wherever a / b is defined; written without the division:
+//   a b <= 0  ->  0,   otherwise  sign(b) * min(max|.|, 2 min|.|).
+// ----------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ real superbee_slope(real a, real b) {
+  real aa = fabs(a), ab = fabs(b);
+  real m = fmin(fmax(aa, ab), real(2) * fmin(aa, ab));
+  return (a * b > real(0)) ? copysign(m, b) : real(0);
+}
+
+// Flux through the face between cells p0 (left) and p1 (right) for speed s:
+//   s > 0:  s (p0 + slope(p0 - pm1, p1 - p0) / 2)
+//   s < 0:  s (p1 - slope(p2 - p1, p1 - p0) / 2)
+template <typename real>
+__device__ __forceinline__ real face_flux(bool pos, real s, real pm1, real p0, real p1, real p2) {
+  real b = p1 - p0;
+  return pos ? s * (p0 + real(0.5) * superbee_slope(p0 - pm1, b))
+             : s * (p1 - real(0.5) * superbee_slope(p2 - p1, b));
+}
+
+// ----------------------------------------------------------------------------
+// Kernel launchers (defined in the k_*.cu files).
+// ----------------------------------------------------------------------------
+struct LaunchCtx {
+  cudaStream_t stream;
+  int num_sms;
+  long long *launches;  // host counter
+};
+
+template <typename real, typename st>
+cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const st *src, st *r_out,
+                          const real *rho_yz, const GroupCoef<real> *coef, double *dose_yz, double *flu_yz,
+                          real c_half, double dose_scale, double flu_scale);
+
+template <typename real>
+cudaError_t launch_transport(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
+                             double dy, double dz, int *err);
+
+template <typename real>
+cudaError_t launch_angular(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts,
+                           double h, double du, double dv);
+
+bool angular_supported(int nu, int nv);
+
+template <typename real, typename st>
+cudaError_t launch_source(const LaunchCtx &lc, const Dims &d, const st *p2, const st *r, st *src, double dudv);
+
+// R of one state for pbs_eval_source; precision as pbs_precision.
+cudaError_t launch_source_input(const LaunchCtx &lc, const Dims &d, const void *psi_k, const void *rho_yz,
+                                const void *coef, void *r_out, int precision);
+
+template <typename real>
+cudaError_t launch_init(const LaunchCtx &lc, const Dims &d, real *psi0, const double *fe, const double *fa,
+                        const double *fy, const double *fz);
+
+template <typename real>
+cudaError_t launch_fluence(const LaunchCtx &lc, const Dims &d, const real *psi, const GroupCoef<real> *coef,
+                           double *flu_yz, double scale);
+
+}  // namespace pbs

@@ -1,0 +1,164 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.  Tolerances: FP64 GPU within 1e-10 of the
+oracle (relative to the largest value); FP32 within the bounds stated per
+test; mixed precision within 1e-3 of the maximum dose."""
+import numpy as np
+import pytest
+
+from paper_2504_00340_gb300 import binding
+from paper_2504_00340_gb300.workloads import WATER100, random_state, smooth_state
+
+pytestmark = pytest.mark.gpu
+
+
+def _grid(ny, nz, nu, nv, ng, e_min=0.0, e_max=60.0, dy=0.1, dz=0.1, u_max=0.15):
+    return dict(ny=ny, nz=nz, nu=nu, nv=nv, dy=dy, dz=dz, u_max=u_max, v_max=u_max,
+                e_faces=np.linspace(e_min, e_max, ng + 1))
+
+
+def _relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _pair(orc, grid, nx, dx, K, precision, rho=None, seed=0):
+    s = binding.Solver(grid, nx=nx, dx=dx, n_scatter=K, precision=precision)
+    o = orc.Oracle(grid)
+    if rho is None:
+        rho = np.random.default_rng(seed).uniform(0.3, 1.9, size=(nx, grid["ny"], grid["nz"]))
+    s.set_material(rho)
+    return s, o, rho
+
+
+def test_tables_match_oracle(orc):
+    grid = _grid(4, 4, 6, 4, 40, e_min=0.0, e_max=110.0)
+    s = binding.Solver(grid, nx=1, dx=0.05, n_scatter=1, precision="fp64")
+    t = s.tables()
+    r = orc.Oracle(grid).tables()
+    for k in ("s_face", "ts", "sig", "p1", "p2", "u", "v"):
+        assert _relerr(t[k], r[k]) < 1e-13, k
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_energy_substep_with_source_chain(orc, precision, tol):
+    grid = _grid(6, 7, 4, 4, 37)  # ragged: nyz = 42, 37 groups
+    K = 2
+    s, o, rho = _pair(orc, grid, 3, 0.05, K, precision)
+    states = [smooth_state(6, 7, 37, 4, 4, seed=10 + k) for k in range(K + 1)]
+    for k in range(K + 1):
+        s.write_psi(k, states[k])
+    h, slab = 0.025, 1
+    s.substep_energy(h, slab, fluence_plane=2)
+    # oracle: components in order, source of k from k-1 at start and end (trapezoid)
+    ref = [x.copy() for x in states]
+    edep = np.zeros((6, 7))
+    src_sum = None
+    for k in range(K + 1):
+        src_a = o.source(rho[slab], ref[k]) if k < K else None
+        ref[k], e, _ = o.energy_substep(h, rho[slab], ref[k], src_sum)
+        edep += e
+        if k < K:
+            src_sum = src_a + o.source(rho[slab], ref[k])
+    for k in range(K + 1):
+        assert _relerr(s.read_psi(k), ref[k]) < tol, k
+    dose = s.read_dose(3)[slab]
+    dose_ref = edep / (rho[slab] * 0.05 * 0.1 * 0.1)
+    assert _relerr(dose, dose_ref) < 10 * tol
+    flu = s.read_fluence(3)[2] if s.depth >= 2 else None
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
+@pytest.mark.parametrize("ny,nz", [(21, 12), (9, 5), (40, 32)])
+def test_transport_substep(orc, precision, tol, ny, nz):
+    grid = _grid(ny, nz, 4, 6, 3)
+    s, o, _ = _pair(orc, grid, 1, 0.05, 0, precision)
+    psi = random_state((3, 2, 6, 4, ny, nz), seed=ny * nz)
+    s.write_psi(0, psi)
+    s.substep_transport(0.37)
+    ref = o.transport_substep(0.37, psi)
+    assert _relerr(s.read_psi(0), ref) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
+@pytest.mark.parametrize("nu,nv", [(8, 8), (16, 16), (4, 6)])
+def test_angular_substep(orc, precision, tol, nu, nv):
+    grid = _grid(5, 9, nu, nv, 3)  # nyz = 45: ragged against the 32/16-point tiles
+    s, o, rho = _pair(orc, grid, 2, 0.05, 1, precision)
+    psi = [random_state((3, 2, nv, nu, 5, 9), seed=7 + k) for k in range(2)]
+    for k in range(2):
+        s.write_psi(k, psi[k])
+    s.substep_angular(3.0, 1)
+    for k in range(2):
+        ref = o.angular_substep(3.0, rho[1], psi[k])
+        assert _relerr(s.read_psi(k), ref) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-6), ("mixed", 8e-3)])
+def test_source_contraction(orc, precision, tol):
+    grid = _grid(9, 8, 8, 8, 20)
+    s, o, rho = _pair(orc, grid, 1, 0.05, 1, precision)
+    psi = smooth_state(9, 8, 20, 8, 8, seed=3)
+    s.write_psi(0, psi)
+    got = s.eval_source(0, 0)
+    ref = o.source(rho[0], psi)
+    assert _relerr(got, ref) < tol
+    s.close()
+
+
+def test_full_march_fp64(orc):
+    grid = _grid(18, 14, 8, 8, 24, e_max=60.0)
+    nx, dx = 12, 0.05
+    s, o, rho = _pair(orc, grid, nx, dx, 1, "fp64")
+    beam = dict(e0=50.0, sigma_e=1.0, sigma_y=0.3, sigma_z=0.25, y0=0.05)
+    s.launch_beam(**beam)
+    s.step(5)
+    s.step(nx - 5)
+    ref = o.march(rho, nx, dx, beam=beam, n_scatter=1)
+    assert _relerr(s.read_dose(), ref["dose"]) < 1e-10
+    assert _relerr(s.read_fluence(), ref["fluence"]) < 1e-10
+    for k in range(2):
+        assert _relerr(s.read_psi(k), ref["psi"][k]) < 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("mixed", 1e-3)])
+def test_full_march_reduced_precision(orc, precision, tol):
+    grid = _grid(16, 16, 8, 8, 48, e_max=60.0)
+    nx, dx = 60, 0.05
+    s, o, rho = _pair(orc, grid, nx, dx, 1, precision, rho=np.ones((60, 16, 16)))
+    beam = dict(e0=45.0, sigma_e=1.0, sigma_y=0.3, sigma_z=0.3)
+    s.launch_beam(**beam)
+    s.step(nx)
+    ref = o.march(rho, nx, dx, beam=beam, n_scatter=1)
+    d, dr = s.read_dose(), ref["dose"]
+    assert np.abs(d - dr).max() / np.abs(dr).max() < tol
+    f, fr = s.read_fluence(), ref["fluence"]
+    assert np.abs(f - fr).max() / np.abs(fr).max() < tol
+    s.close()
+
+
+@pytest.mark.slow
+def test_small_workload_full_size_fp64(orc):
+    """The 100 MeV / 32x32 / 64 groups / 8x8 angles / primary + 1 workload,
+    all 180 steps, FP64 on the GPU against the oracle."""
+    w = WATER100
+    grid = w.grid()
+    rho = w.density()
+    s = binding.Solver(grid, nx=w.n_steps, dx=w.dx, n_scatter=w.n_scatter, precision="fp64")
+    s.set_material(rho)
+    s.launch_beam(**w.beam)
+    s.step(w.n_steps)
+    ref = orc.Oracle(grid).march(rho, w.n_steps, w.dx, beam=w.beam, n_scatter=w.n_scatter)
+    assert _relerr(s.read_dose(), ref["dose"]) < 1e-10
+    assert _relerr(s.read_fluence(), ref["fluence"]) < 1e-10
+    s.close()
