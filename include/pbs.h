@@ -182,6 +182,23 @@ pbs_status pbs_substep_angular(pbs_ctx *ctx, double h, int slab);
  * n = ng*nu*nv*ny*nz.  Synchronises. */
 pbs_status pbs_eval_source(pbs_ctx *ctx, int k_from, int slab, double *host_out, size_t n);
 
+/* Kernel kinds for per-kernel timing. */
+typedef enum {
+  PBS_KERNEL_ENERGY = 0,     /* energy substep scan (incl. dose/fluence/R)   */
+  PBS_KERNEL_TRANSPORT = 1,  /* lateral transport substep                    */
+  PBS_KERNEL_ANGULAR = 2,    /* angular substep                              */
+  PBS_KERNEL_SOURCE = 3,     /* catastrophic-source angle contraction        */
+  PBS_KERNEL_KINDS = 4
+} pbs_kernel_kind;
+
+/* Per-kernel timing.  pbs_set_profiling(ctx, 1) clears the totals and makes
+ * every later kernel launch of the march be bracketed by a CUDA event pair
+ * recorded on the context's stream (0 stops recording).  pbs_profile_read
+ * synchronises the stream and returns, for one pbs_kernel_kind, the number of
+ * launches timed and their summed device time in milliseconds. */
+pbs_status pbs_set_profiling(pbs_ctx *ctx, int on);
+pbs_status pbs_profile_read(pbs_ctx *ctx, int kind, long long *launches, double *total_ms);
+
 /* Number of kernel launches the library has issued since pbs_create. */
 pbs_status pbs_kernel_launches(const pbs_ctx *ctx, long long *count);
 

@@ -447,9 +447,9 @@ void orc_transport_substep(const orc_ctx *c, double h, double *psi) {
  *   lam = (2cos(pi m/(Nu+1)) - 2)/du^2 + (2cos(pi n/(Nv+1)) - 2)/dv^2
  * and Crank-Nicolson with coefficient kappa/2, kappa = rho sigma_tr,g,
  * multiplies it by r = (1 + h kappa lam / 4) / (1 - h kappa lam / 4).
- * The transform is written as explicit sine sums with the orthonormal
- * scaling sqrt(2/(N+1)) in each direction (the paper's 1/(IJ) inverse
- * scaling with I = N+1 is the same map). */
+ * The transform is written as explicit sine sums (one direction at a time)
+ * with the orthonormal scaling sqrt(2/(N+1)) in each direction (the paper's
+ * 1/(IJ) inverse scaling with I = N+1 is the same map). */
 void orc_angular_substep(const orc_ctx *c, double h, const double *rho_yz, double *psi) {
   int G = c->ng, nu = c->nu, nv = c->nv, na = c->na, ny = c->ny, nz = c->nz;
   double *su = (double *)malloc(sizeof(double) * nu * nu);
@@ -474,26 +474,39 @@ void orc_angular_substep(const orc_ctx *c, double h, const double *rho_yz, doubl
     long st = (long)ny * nz; /* stride between angles */
     double *x = (double *)malloc(sizeof(double) * na);
     double *t = (double *)malloc(sizeof(double) * na);
+    double *w = (double *)malloc(sizeof(double) * na);
     for (int a = 0; a < na; a++) x[a] = base[a * st];
-    /* forward: t[n][m] = sum_j sum_i sv[n][j] su[m][i] x[j][i] */
+    /* The 2-D sine basis of Eq. (fly) is a product sin(.i) sin(.j), so each
+     * 2-D sum is done as a sum over i followed by a sum over j.
+     * forward: w[j][m] = sum_i su[m][i] x[j][i];  t[n][m] = sum_j sv[n][j] w[j][m] */
+    for (int j = 0; j < nv; j++)
+      for (int m = 0; m < nu; m++) {
+        double acc = 0.0;
+        for (int i = 0; i < nu; i++) acc += su[m * nu + i] * x[j * nu + i];
+        w[j * nu + m] = acc;
+      }
     for (int n = 0; n < nv; n++)
       for (int m = 0; m < nu; m++) {
         double acc = 0.0;
-        for (int j = 0; j < nv; j++)
-          for (int i = 0; i < nu; i++) acc += sv[n * nv + j] * su[m * nu + i] * x[j * nu + i];
+        for (int j = 0; j < nv; j++) acc += sv[n * nv + j] * w[j * nu + m];
         double q = 0.25 * h * kappa * lam[n * nu + m];
         t[n * nu + m] = acc * (1.0 + q) / (1.0 - q);
       }
-    /* inverse (the orthonormal DST-I is its own inverse) */
+    /* inverse (the orthonormal DST-I is its own inverse), same two sums */
+    for (int j = 0; j < nv; j++)
+      for (int m = 0; m < nu; m++) {
+        double acc = 0.0;
+        for (int n = 0; n < nv; n++) acc += sv[n * nv + j] * t[n * nu + m];
+        w[j * nu + m] = acc;
+      }
     for (int j = 0; j < nv; j++)
       for (int i = 0; i < nu; i++) {
         double acc = 0.0;
-        for (int n = 0; n < nv; n++)
-          for (int m = 0; m < nu; m++) acc += sv[n * nv + j] * su[m * nu + i] * t[n * nu + m];
+        for (int m = 0; m < nu; m++) acc += su[m * nu + i] * w[j * nu + m];
         x[j * nu + i] = acc;
       }
     for (int a = 0; a < na; a++) base[a * st] = x[a];
-    free(x); free(t);
+    free(x); free(t); free(w);
   }
   free(su); free(sv); free(lam);
 }

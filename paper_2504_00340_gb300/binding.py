@@ -71,6 +71,9 @@ SIGNATURES = [
     ("pbs_substep_angular", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
     ("pbs_eval_source", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _D, ctypes.c_size_t]),
     ("pbs_kernel_launches", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
+    ("pbs_set_profiling", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("pbs_profile_read", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_double)]),
     ("pbs_last_error", ctypes.c_char_p, [_VP]),
     ("pbs_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("pbs_destroy", None, [_VP]),
@@ -197,6 +200,19 @@ def pbs_kernel_launches(ctx) -> int:
     n = ctypes.c_longlong()
     _check(ctx, load_library().pbs_kernel_launches(_VP(ctx), ctypes.byref(n)))
     return n.value
+
+
+KERNEL_KINDS = {"energy": 0, "transport": 1, "angular": 2, "source": 3}
+
+
+def pbs_set_profiling(ctx, on: bool) -> None:
+    _check(ctx, load_library().pbs_set_profiling(_VP(ctx), int(bool(on))))
+
+
+def pbs_profile_read(ctx, kind: int):
+    n, ms = ctypes.c_longlong(), ctypes.c_double()
+    _check(ctx, load_library().pbs_profile_read(_VP(ctx), int(kind), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
 
 
 def pbs_last_error(ctx) -> str:
@@ -338,3 +354,10 @@ class Solver:
     @property
     def kernel_launches(self) -> int:
         return pbs_kernel_launches(self.ctx)
+
+    def set_profiling(self, on: bool):
+        pbs_set_profiling(self.ctx, on)
+
+    def profile(self) -> dict:
+        """{kind: (launches, total_ms)} of the kernels timed since set_profiling(True)."""
+        return {k: pbs_profile_read(self.ctx, v) for k, v in KERNEL_KINDS.items()}

@@ -9,11 +9,12 @@
 // replaced by dense 16-point sine sums folded by the (anti)symmetry
 // S[m][N-1-i] = (-1)^m S[m][i], which halves the multiply-adds.
 //
-// GB300 design.  A CTA owns one (component, g, c) and 32 lateral points: it
-// loads the [Nv*Nu][32] tile with coalesced 128-byte rows into shared memory;
-// thread (x, j) transforms row j of slab x along u, thread (x, m) transforms
-// column m along v, scales by the mode factor, transforms back along v, and
-// thread (x, j) finally transforms back along u and stores to global memory.
+// GB300 design.  A CTA owns one (component, g, c) and 32 lateral points (16 in
+// FP64).  Thread (x, j) loads row j of slab x straight from global memory
+// (each warp load is one coalesced 128-byte row of the [angle][lateral] plane
+// stack) and transforms it along u into shared memory; thread (x, m)
+// transforms column m along v, scales by the mode factor, transforms back
+// along v; thread (x, j) transforms back along u and stores to global memory.
 // Sine and eigenvalue tables travel as kernel parameters (constant bank).
 #include "pbs_internal.cuh"
 
@@ -53,6 +54,9 @@ __device__ __forceinline__ void dst_apply(const real *__restrict__ S, const real
   }
 }
 
+__device__ __forceinline__ double mode_factor(double den) { return 2.0 / den - 1.0; }
+__device__ __forceinline__ float mode_factor(float den) { return fmaf(2.0f, __frcp_rn(den), -1.0f); }
+
 template <typename real, int NU, int NV>
 __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
     k_angular(real *__restrict__ psi, const real *__restrict__ rho_yz, const real *__restrict__ ts, int nyz,
@@ -69,23 +73,19 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
   const bool active = yz < nyz;
   real *base = psi + kgc * (long long)NA * nyz + yz;
 
-  // load: thread row t covers angles t, t + NT, ...
   constexpr int NT = NU > NV ? NU : NV;
-#pragma unroll
-  for (int a = t; a < NA; a += NT) tile[a][x] = active ? base[(long long)a * nyz] : real(0);
-  __syncthreads();
-
-  // forward transform along u: row j
+  // forward transform along u: thread row t < NV loads row j = t of its slab
+  // straight from global memory (coalesced over the 32 lateral points)
   if (t < NV) {
     real r[NU], y[NU];
 #pragma unroll
-    for (int i = 0; i < NU; i++) r[i] = tile[t * NU + i][x];
+    for (int i = 0; i < NU; i++) r[i] = active ? base[(long long)(t * NU + i) * nyz] : real(0);
     dst_apply<real, NU>(tb.su, r, y);
 #pragma unroll
     for (int i = 0; i < NU; i++) tile[t * NU + i][x] = y[i];
   }
   __syncthreads();
-  // along v: forward, mode factor, inverse (column m)
+  // along v: forward, mode factor, inverse (column m = t)
   if (t < NU) {
     const real q = active ? hq * rho_yz[yz] * ts[g] : real(0);  // h kappa / 4
     real c[NV], y[NV];
@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
     dst_apply<real, NV>(tb.sv, c, y);
 #pragma unroll
     for (int n = 0; n < NV; n++) {
-      const real ql = q * tb.lam[n * NU + t];
-      y[n] = y[n] * (real(1) + ql) / (real(1) - ql);
+      // (1 + q lam) / (1 - q lam) = -1 + 2 / (1 - q lam); lam <= 0, so 1 - q lam >= 1
+      const real den = real(1) - q * tb.lam[n * NU + t];
+      y[n] *= mode_factor(den);
     }
     dst_apply<real, NV>(tb.sv, y, c);
 #pragma unroll
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
       for (int i = 0; i < NU; i++) base[(long long)(t * NU + i) * nyz] = y[i];
     }
   }
+  (void)NT;
 }
 
 template <typename real>

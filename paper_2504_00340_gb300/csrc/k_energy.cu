@@ -40,6 +40,9 @@ __device__ __forceinline__ void store_st<__nv_bfloat16, float>(__nv_bfloat16 *p,
   *p = __float2bfloat16_rn(v);
 }
 
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
 // Neumaier compensated accumulation.
 template <typename real>
 __device__ __forceinline__ void comp_add(real &s, real &c, real x) {
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(kLanesX *kAnglesY) k_energy(Dims d, real *__re
       // M = I - c A_gg = [[1+am+sg, -am], [3ap, 1+ap+2am+sg]]
       const real m00 = real(1) + am + sg;
       const real m11 = real(1) + ap + real(2) * am + sg;
-      const real inv = real(1) / (m00 * m11 + real(3) * am * ap);
+      const real inv = recip(m00 * m11 + real(3) * am * ap);
       const real x1 = (m11 * r0 + am * r1) * inv;
       const real x2 = (m00 * r1 - real(3) * ap * r0) * inv;
       if (active) {

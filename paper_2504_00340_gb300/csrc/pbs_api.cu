@@ -41,6 +41,17 @@ struct pbs_ctx {
   size_t rsize, ssize;  // element sizes of real and of the source storage
   long long launches = 0;
   std::string err;
+  // per-kernel timing (pbs_set_profiling): event pairs recorded on the stream
+  struct Rec { int kind; cudaEvent_t a, b; };
+  bool profiling = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  long long prof_count[PBS_KERNEL_KINDS] = {};
+  double prof_ms[PBS_KERNEL_KINDS] = {};
+  ~pbs_ctx() {
+    for (auto &r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -85,6 +96,52 @@ template <typename T>
 T *at(pbs_ctx *c, size_t off) { return reinterpret_cast<T *>(c->ws + off); }
 
 LaunchCtx lctx(pbs_ctx *c) { return LaunchCtx{c->stream, c->num_sms, &c->launches}; }
+
+cudaEvent_t take_event(pbs_ctx *c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch with an event pair when profiling is on.
+struct ProfScope {
+  pbs_ctx *c;
+  int kind;
+  cudaEvent_t a = nullptr;
+  ProfScope(pbs_ctx *c_, int k) : c(c_), kind(k) {
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (c->profiling && a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, c->stream);
+      c->recs.push_back({kind, a, b});
+    }
+  }
+};
+
+pbs_status fold_profile(pbs_ctx *c) {
+  if (c->recs.empty()) return PBS_OK;
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (auto &r : c->recs) {
+    float ms = 0.f;
+    PBS_CUDA(c, cudaEventElapsedTime(&ms, r.a, r.b));
+    c->prof_count[r.kind]++;
+    c->prof_ms[r.kind] += ms;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  return PBS_OK;
+}
 
 // ---------------------------------------------------------------- host tables
 
@@ -253,11 +310,16 @@ pbs_status energy_all(pbs_ctx *c, double h, int slab, int flu_plane) {
   st *rbuf = at<st>(c, c->off_r), *sbuf = at<st>(c, c->off_s);
   const auto *coef = at<GroupCoef<real>>(c, c->off_coef);
   for (int k = 0; k <= c->K; k++) {
-    cudaError_t e = launch_energy<real, st>(lc, c->d, psi + (size_t)k * c->d.comp_elems, k >= 1 ? sbuf : nullptr,
-                                            k < c->K ? rbuf : nullptr, rho, coef, dose, flu, (real)(0.5 * h),
-                                            c->du * c->dv / c->dx, c->du * c->dv);
+    cudaError_t e;
+    {
+      ProfScope ps(c, PBS_KERNEL_ENERGY);
+      e = launch_energy<real, st>(lc, c->d, psi + (size_t)k * c->d.comp_elems, k >= 1 ? sbuf : nullptr,
+                                  k < c->K ? rbuf : nullptr, rho, coef, dose, flu, (real)(0.5 * h),
+                                  c->du * c->dv / c->dx, c->du * c->dv);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "energy kernel");
     if (k < c->K) {
+      ProfScope ps(c, PBS_KERNEL_SOURCE);
       e = launch_source<real, st>(lc, c->d, at<st>(c, c->off_p2), rbuf, sbuf, c->du * c->dv);
       if (e != cudaSuccess) return cuda_fail(c, e, "source kernel");
     }
@@ -267,14 +329,19 @@ pbs_status energy_all(pbs_ctx *c, double h, int slab, int flu_plane) {
 
 template <typename real>
 pbs_status transport_all(pbs_ctx *c, double h) {
-  cudaError_t e = launch_transport<real>(lctx(c), c->d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz,
-                                         at<int>(c, c->off_err));
+  ProfScope ps(c, PBS_KERNEL_TRANSPORT);
+  cudaError_t e =
+      transport_rows_supported(c->nz)
+          ? launch_transport_rows<real>(lctx(c), c->d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz)
+          : launch_transport<real>(lctx(c), c->d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz,
+                                   at<int>(c, c->off_err));
   return e == cudaSuccess ? PBS_OK : cuda_fail(c, e, "transport kernel");
 }
 
 template <typename real>
 pbs_status angular_all(pbs_ctx *c, double h, int slab) {
   const size_t nyz = (size_t)c->ny * c->nz;
+  ProfScope ps(c, PBS_KERNEL_ANGULAR);
   cudaError_t e = launch_angular<real>(lctx(c), c->d, at<real>(c, c->off_psi),
                                        at<real>(c, c->off_rho) + (size_t)slab * nyz, at<real>(c, c->off_ts), h, c->du,
                                        c->dv);
@@ -586,6 +653,27 @@ pbs_status pbs_eval_source(pbs_ctx *c, int k_from, int slab, double *out, size_t
 pbs_status pbs_kernel_launches(const pbs_ctx *c, long long *count) {
   if (!c || !count) return PBS_ERR_ARG;
   *count = c->launches;
+  return PBS_OK;
+}
+
+pbs_status pbs_set_profiling(pbs_ctx *c, int on) {
+  if (!c) return PBS_ERR_ARG;
+  pbs_status r = fold_profile(c);
+  if (r != PBS_OK) return r;
+  c->profiling = on != 0;
+  for (int k = 0; k < PBS_KERNEL_KINDS; k++) {
+    c->prof_count[k] = 0;
+    c->prof_ms[k] = 0.0;
+  }
+  return PBS_OK;
+}
+
+pbs_status pbs_profile_read(pbs_ctx *c, int kind, long long *count, double *total_ms) {
+  if (!c || kind < 0 || kind >= PBS_KERNEL_KINDS || !count || !total_ms) return fail(c, PBS_ERR_ARG, "bad kind");
+  pbs_status r = fold_profile(c);
+  if (r != PBS_OK) return r;
+  *count = c->prof_count[kind];
+  *total_ms = c->prof_ms[kind];
   return PBS_OK;
 }
 

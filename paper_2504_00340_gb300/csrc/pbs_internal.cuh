@@ -106,13 +106,22 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 // Superbee-limited slope and upwind face flux (Section 3.4, Eq. distansport).
 // slope(a, b) equals b * eta(a / b) with eta(t) = max[0, min(2t,1), min(t,2)]
 // wherever a / b is defined; written without the division:
-//   a b <= 0  ->  0,   otherwise  sign(b) * min(max|.|, 2 min|.|).
+//   opposite signs or a zero  ->  0,   otherwise  sign(b) * min(max|.|, 2 min|.|).
 // ----------------------------------------------------------------------------
+// Sign agreement from the sign bits: a product a*b can underflow to zero in
+// FP32 for tiny (but still representable) differences.
+__device__ __forceinline__ bool same_sign(float a, float b) {
+  return ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u) == 0u;
+}
+__device__ __forceinline__ bool same_sign(double a, double b) {
+  return ((__double_as_longlong(a) ^ __double_as_longlong(b)) & (long long)0x8000000000000000ULL) == 0;
+}
+
 template <typename real>
 __device__ __forceinline__ real superbee_slope(real a, real b) {
   real aa = fabs(a), ab = fabs(b);
-  real m = fmin(fmax(aa, ab), real(2) * fmin(aa, ab));
-  return (a * b > real(0)) ? copysign(m, b) : real(0);
+  real m = fmin(fmax(aa, ab), real(2) * fmin(aa, ab));  // zero if a or b is zero
+  return same_sign(a, b) ? copysign(m, b) : real(0);
 }
 
 // Flux through the face between cells p0 (left) and p1 (right) for speed s:
@@ -142,6 +151,12 @@ cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const
 template <typename real>
 cudaError_t launch_transport(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
                              double dy, double dz, int *err);
+
+// Warp-per-plane streaming transport for nz <= 128 (k_transport_rows.cu).
+bool transport_rows_supported(int nz);
+template <typename real>
+cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
+                                  double dy, double dz);
 
 template <typename real>
 cudaError_t launch_angular(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts,

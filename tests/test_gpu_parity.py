@@ -76,7 +76,7 @@ def test_energy_substep_with_source_chain(orc, precision, tol):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
-@pytest.mark.parametrize("ny,nz", [(21, 12), (9, 5), (40, 32)])
+@pytest.mark.parametrize("ny,nz", [(21, 12), (9, 5), (40, 32), (24, 128), (13, 100), (7, 144), (3, 64)])
 def test_transport_substep(orc, precision, tol, ny, nz):
     grid = _grid(ny, nz, 4, 6, 3)
     s, o, _ = _pair(orc, grid, 1, 0.05, 0, precision)
