@@ -112,7 +112,7 @@ def _kernel_hash(name: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-KERNEL_FILES = {"energy": "k_energy.cu", "transport": "k_transport.cu", "angular": "k_angular.cu",
+KERNEL_FILES = {"energy": "k_energy.cu", "transport": "k_transport_rows.cu", "angular": "k_angular.cu",
                 "source": "k_misc.cu"}
 
 
@@ -170,6 +170,7 @@ def run_ours(a):
     s.set_material(rho)
     s.launch_beam(**w.beam)
     s.step(W)
+    s.flush()
     torch.cuda.synchronize()
 
     props = torch.cuda.get_device_properties(dev)
@@ -187,6 +188,7 @@ def run_ours(a):
     s.set_profiling(True)
     ev0.record(stream)
     s.step(K)
+    s.flush()  # the deferred closing half step of the last timed step
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -293,6 +295,7 @@ def fp64_comparison(binding, w, stream, n=4):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         s.step(n)
+        s.flush()
         e1.record(stream)
         torch.cuda.synchronize()
         out[prec] = w.cells_per_step * (w.n_scatter + 1) * n / (e0.elapsed_time(e1) / 1e3)

@@ -148,8 +148,14 @@ pbs_status pbs_launch_beam(pbs_ctx *ctx, const pbs_beam *beam);
 
 /* March n_steps depth steps (Strang order E T A T E per step, all
  * components in lock-step).  Asynchronous.  PBS_ERR_ARG if the march would
- * pass the material's last slab. */
+ * pass the material's last slab.  The closing E(h/2) of the last step is
+ * deferred so that it can be fused with the opening E(h/2) of the next call
+ * (one pass over psi for the two); pbs_flush applies it, and every read,
+ * write, substep or material call applies it first. */
 pbs_status pbs_step(pbs_ctx *ctx, int n_steps);
+
+/* Apply a deferred closing E(h/2), if any.  Asynchronous. */
+pbs_status pbs_flush(pbs_ctx *ctx);
 
 /* Depth steps marched since pbs_launch_beam. */
 pbs_status pbs_get_depth(const pbs_ctx *ctx, int *steps_done);

@@ -61,6 +61,7 @@ SIGNATURES = [
     ("pbs_set_material", ctypes.c_int, [_VP, _D, ctypes.c_int]),
     ("pbs_launch_beam", ctypes.c_int, [_VP, ctypes.POINTER(PbsBeam)]),
     ("pbs_step", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("pbs_flush", ctypes.c_int, [_VP]),
     ("pbs_get_depth", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     ("pbs_read_dose", ctypes.c_int, [_VP, _D, ctypes.c_size_t]),
     ("pbs_read_fluence", ctypes.c_int, [_VP, _D, ctypes.c_size_t]),
@@ -156,6 +157,10 @@ def pbs_launch_beam(ctx, beam: PbsBeam) -> None:
 
 def pbs_step(ctx, n_steps: int) -> None:
     _check(ctx, load_library().pbs_step(_VP(ctx), int(n_steps)))
+
+
+def pbs_flush(ctx) -> None:
+    _check(ctx, load_library().pbs_flush(_VP(ctx)))
 
 
 def pbs_get_depth(ctx) -> int:
@@ -302,6 +307,9 @@ class Solver:
     def step(self, n: int):
         pbs_step(self.ctx, n)
 
+    def flush(self):
+        pbs_flush(self.ctx)
+
     @property
     def depth(self) -> int:
         return pbs_get_depth(self.ctx)
@@ -329,7 +337,8 @@ class Solver:
 
     def psi_view(self, k: int = 0):
         """Device view (torch tensor, no copy) of component k in the documented
-        layout [g][c][v][u][y][z]; psi sits at the start of the workspace."""
+        layout [g][c][v][u][y][z]; psi sits at the start of the workspace.
+        The view bypasses the API: call flush() after step() before reading it."""
         torch = self.torch
         dt = torch.float64 if self._precision == PBS_FP64 else torch.float32
         n = int(np.prod(self.comp_shape))

@@ -28,16 +28,34 @@ namespace {
 template <typename real>
 __host__ __device__ constexpr int tile_w() { return sizeof(real) == 8 ? 16 : 32; }
 
+// Orthonormal DST-I matrices sqrt(2/(N+1)) sin(pi (m+1)(i+1)/(N+1)) for every
+// size N <= 16, row-major [m][i], in the constant bank (they depend on N
+// only).  Indexed with compile-time offsets, so the multiply-adds read them
+// as constant operands.
+__constant__ float c_dst_f[kMaxAngle + 1][kMaxAngle * kMaxAngle];
+__constant__ double c_dst_d[kMaxAngle + 1][kMaxAngle * kMaxAngle];
+
+template <typename real>
+struct DstTab;
+template <>
+struct DstTab<float> {
+  template <int N>
+  static __device__ __forceinline__ float at(int idx) { return c_dst_f[N][idx]; }
+};
+template <>
+struct DstTab<double> {
+  template <int N>
+  static __device__ __forceinline__ double at(int idx) { return c_dst_d[N][idx]; }
+};
+
 template <typename real>
 struct AngTables {
-  real su[kMaxAngle * kMaxAngle];   // orthonormal DST-I, u direction [m][i]
-  real sv[kMaxAngle * kMaxAngle];   // v direction [n][j]
   real lam[kMaxAngle * kMaxAngle];  // eigenvalues [n][m]
 };
 
 // y[m] = sum_i S[m][i] x[i] for an orthonormal DST-I of even length N.
 template <typename real, int N>
-__device__ __forceinline__ void dst_apply(const real *__restrict__ S, const real (&x)[N], real (&y)[N]) {
+__device__ __forceinline__ void dst_apply(const real (&x)[N], real (&y)[N]) {
   constexpr int H = N / 2;
   real e[H], o[H];
 #pragma unroll
@@ -46,19 +64,18 @@ __device__ __forceinline__ void dst_apply(const real *__restrict__ S, const real
     o[i] = x[i] - x[N - 1 - i];
   }
 #pragma unroll
-  for (int m = 0; m < N; m++) {
-    real acc = 0;
+  for (int m = 0; m < N; m++) y[m] = 0;
 #pragma unroll
-    for (int i = 0; i < H; i++) acc = fma(S[m * N + i], (m & 1) ? o[i] : e[i], acc);
-    y[m] = acc;
-  }
+  for (int i = 0; i < H; i++)
+#pragma unroll
+    for (int m = 0; m < N; m++) y[m] = fma(DstTab<real>::template at<N>(m * N + i), (m & 1) ? o[i] : e[i], y[m]);
 }
 
 __device__ __forceinline__ double mode_factor(double den) { return 2.0 / den - 1.0; }
-__device__ __forceinline__ float mode_factor(float den) { return fmaf(2.0f, __frcp_rn(den), -1.0f); }
+__device__ __forceinline__ float mode_factor(float den) { return __fdividef(2.0f, den) - 1.0f; }
 
 template <typename real, int NU, int NV>
-__global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
+__global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
     k_angular(real *__restrict__ psi, const real *__restrict__ rho_yz, const real *__restrict__ ts, int nyz,
               int ng, real hq, const __grid_constant__ AngTables<real> tb) {
   constexpr int NA = NU * NV;
@@ -80,7 +97,7 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
     real r[NU], y[NU];
 #pragma unroll
     for (int i = 0; i < NU; i++) r[i] = active ? base[(long long)(t * NU + i) * nyz] : real(0);
-    dst_apply<real, NU>(tb.su, r, y);
+    dst_apply<real, NU>(r, y);
 #pragma unroll
     for (int i = 0; i < NU; i++) tile[t * NU + i][x] = y[i];
   }
@@ -91,14 +108,14 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
     real c[NV], y[NV];
 #pragma unroll
     for (int j = 0; j < NV; j++) c[j] = tile[j * NU + t][x];
-    dst_apply<real, NV>(tb.sv, c, y);
+    dst_apply<real, NV>(c, y);
 #pragma unroll
     for (int n = 0; n < NV; n++) {
       // (1 + q lam) / (1 - q lam) = -1 + 2 / (1 - q lam); lam <= 0, so 1 - q lam >= 1
       const real den = real(1) - q * tb.lam[n * NU + t];
       y[n] *= mode_factor(den);
     }
-    dst_apply<real, NV>(tb.sv, y, c);
+    dst_apply<real, NV>(y, c);
 #pragma unroll
     for (int j = 0; j < NV; j++) tile[j * NU + t][x] = c[j];
   }
@@ -108,7 +125,7 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
     real r[NU], y[NU];
 #pragma unroll
     for (int i = 0; i < NU; i++) r[i] = tile[t * NU + i][x];
-    dst_apply<real, NU>(tb.su, r, y);
+    dst_apply<real, NU>(r, y);
     if (active) {
 #pragma unroll
       for (int i = 0; i < NU; i++) base[(long long)(t * NU + i) * nyz] = y[i];
@@ -120,10 +137,6 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV))
 template <typename real>
 void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv) {
   const double pi = 3.14159265358979323846;
-  for (int m = 0; m < nu; m++)
-    for (int i = 0; i < nu; i++) tb.su[m * nu + i] = (real)(std::sqrt(2.0 / (nu + 1)) * std::sin(pi * (m + 1) * (i + 1) / (nu + 1)));
-  for (int n = 0; n < nv; n++)
-    for (int j = 0; j < nv; j++) tb.sv[n * nv + j] = (real)(std::sqrt(2.0 / (nv + 1)) * std::sin(pi * (n + 1) * (j + 1) / (nv + 1)));
   for (int n = 0; n < nv; n++)
     for (int m = 0; m < nu; m++)
       tb.lam[n * nu + m] = (real)((2.0 * std::cos(pi * (m + 1) / (nu + 1)) - 2.0) / (du * du) +
@@ -155,6 +168,22 @@ cudaError_t launch_angular(const LaunchCtx &lc, const Dims &d, real *psi, const 
   PBS_ANG(16, 16) PBS_ANG(4, 8) PBS_ANG(8, 4) PBS_ANG(8, 16) PBS_ANG(16, 8) PBS_ANG(6, 4) PBS_ANG(4, 6)
 #undef PBS_ANG
   return cudaErrorNotSupported;
+}
+
+cudaError_t angular_init_tables() {
+  static float hf[kMaxAngle + 1][kMaxAngle * kMaxAngle];
+  static double hd[kMaxAngle + 1][kMaxAngle * kMaxAngle];
+  const double pi = 3.14159265358979323846;
+  for (int n = 1; n <= kMaxAngle; n++)
+    for (int m = 0; m < n; m++)
+      for (int i = 0; i < n; i++) {
+        const double v = std::sqrt(2.0 / (n + 1)) * std::sin(pi * (m + 1) * (i + 1) / (n + 1));
+        hd[n][m * n + i] = v;
+        hf[n][m * n + i] = (float)v;
+      }
+  cudaError_t e = cudaMemcpyToSymbol(c_dst_f, hf, sizeof(hf));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_dst_d, hd, sizeof(hd));
 }
 
 bool angular_supported(int nu, int nv) {

@@ -20,6 +20,11 @@
 //    T_g = w_g + exp(-lambda (E_{g+1} - E_g)) T_{g+1},
 //    w_g = lambda / Z_g rho sigma_g dE_g (psi^1_old + psi^1_new)_g,
 //    i.e. the trapezoid (old + new) of the source of the next component.
+//
+// Two consecutive E substeps (the closing E(h/2) of depth step s and the
+// opening E(h/2) of step s+1, which Strang splitting puts back to back) are
+// fused: both scans descend in g, so the second consumes the first's output
+// group by group and psi makes one trip through HBM instead of two.
 #include "pbs_internal.cuh"
 
 namespace pbs {
@@ -41,7 +46,7 @@ __device__ __forceinline__ void store_st<__nv_bfloat16, float>(__nv_bfloat16 *p,
 }
 
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }  // ~1 ulp, ample for FP32 psi
 
 // Neumaier compensated accumulation.
 template <typename real>
@@ -55,19 +60,57 @@ constexpr int kLanesX = 32;   // lateral points per block (coalesced)
 constexpr int kAnglesY = 8;   // angles per block (reduced for the dose)
 constexpr int kUnroll = 4;    // groups per prefetch block
 
-template <typename real, typename st, bool HAS_SRC, bool HAS_R>
-__global__ void __launch_bounds__(kLanesX *kAnglesY) k_energy(Dims d, real *__restrict__ psi,
-                                                            const st *__restrict__ src, st *__restrict__ rout,
-                                                            const real *__restrict__ rho_yz,
-                                                            const GroupCoef<real> *__restrict__ coef,
-                                                            double *__restrict__ dose, double *__restrict__ flu,
-                                                            real c, double dose_scale, double flu_scale) {
+// Per-lane state of one CN scan.
+template <typename real>
+struct Scan {
+  real rho, rc, c;
+  real carry;        // (psi^1 - psi^2)_{g+1} of old + new
+  real dep, dep_c;   // deposited energy content (compensated)
+  real tsum;         // source recursion T_g
+
+  __device__ __forceinline__ void init(real rho_, real c_) {
+    rho = rho_;
+    c = c_;
+    rc = rho_ * c_;
+    carry = dep = dep_c = tsum = real(0);
+  }
+  // One group: old (o1, o2) -> new (x1, x2); s = src_old + src_new (or 0).
+  // Returns y1 = o1 + x1 for the source recursion of the next component.
+  template <bool HAS_SRC>
+  __device__ __forceinline__ real group(const GroupCoef<real> &k, real o1, real o2, real s, real &x1, real &x2) {
+    const real am = rc * k.sm, ap = rc * k.sp, sg = rc * k.sig;
+    real r0 = (real(1) - am - sg) * o1 + am * o2 + ap * carry;
+    const real r1 = real(-3) * ap * o1 + (real(1) - ap - real(2) * am - sg) * o2 + real(3) * ap * carry;
+    if (HAS_SRC) r0 += c * s;
+    // M = I - c A_gg = [[1+am+sg, -am], [3ap, 1+ap+2am+sg]]
+    const real m00 = real(1) + am + sg;
+    const real m11 = real(1) + ap + real(2) * am + sg;
+    const real inv = recip(m00 * m11 + real(3) * am * ap);
+    x1 = (m11 * r0 + am * r1) * inv;
+    x2 = (m00 * r1 - real(3) * ap * r0) * inv;
+    // deposited energy content: -(phi_g^T c A_gg y_g + phi_g^T c A_up y_{g+1}) - c phi^T src
+    const real y1 = o1 + x1, y2 = o2 + x2;
+    real t = k.ehat * ((-am - sg) * y1 + am * y2) + k.dq * (real(-3) * ap * y1 + (-ap - real(2) * am - sg) * y2) +
+             (k.ehat + real(3) * k.dq) * ap * carry;
+    if (HAS_SRC) t += c * k.ehat * s;
+    comp_add(dep, dep_c, -t);
+    carry = y1 - y2;
+    return y1;
+  }
+};
+
+template <typename real, typename st, bool HAS_SRC, bool HAS_R, bool TWO>
+__global__ void __launch_bounds__(kLanesX *kAnglesY)
+    k_energy(Dims d, real *__restrict__ psi, const st *__restrict__ src_a, const st *__restrict__ src_b,
+             st *__restrict__ r_a, st *__restrict__ r_b, const real *__restrict__ rho_a,
+             const real *__restrict__ rho_b, const GroupCoef<real> *__restrict__ coef, double *__restrict__ dose_a,
+             double *__restrict__ dose_b, double *__restrict__ flu, real c_a, real c_b, double dose_scale,
+             double flu_scale) {
   extern __shared__ unsigned char smem_raw[];
   GroupCoef<real> *tab = reinterpret_cast<GroupCoef<real> *>(smem_raw);
   const int tid = threadIdx.y * kLanesX + threadIdx.x;
   for (int g = tid; g < d.ng; g += kLanesX * kAnglesY) tab[g] = coef[g];
-  __shared__ double red_dep[kAnglesY][kLanesX];
-  __shared__ double red_flu[kAnglesY][kLanesX];
+  __shared__ double red[3][kAnglesY][kLanesX];
   __syncthreads();
 
   const int yz = blockIdx.x * kLanesX + threadIdx.x;
@@ -75,40 +118,42 @@ __global__ void __launch_bounds__(kLanesX *kAnglesY) k_energy(Dims d, real *__re
   const bool active = (yz < d.nyz) && (a < d.na);
   const long long lane = (long long)a * d.nyz + yz;
   const long long gstride = 2 * d.lanes;
-  const real rho = active ? rho_yz[yz] : real(0);
-  const real rc = rho * c;
 
-  real carry = 0;             // (psi^1 - psi^2)_{g+1} of old + new
-  real dep = 0, dep_c = 0;    // deposited energy content (compensated)
-  real cnt = 0;               // particle count after the substep
-  real tsum = 0;              // source recursion T_g
+  Scan<real> A, B;
+  A.init(active ? rho_a[yz] : real(0), c_a);
+  if (TWO) B.init(active ? rho_b[yz] : real(0), c_b);
+  real cnt = 0;  // particle count after the first scan
 
   real *base = psi + lane;
-  const st *sbase = HAS_SRC ? src + lane : nullptr;
-  st *rbase = HAS_R ? rout + lane : nullptr;
+  const st *sa = HAS_SRC ? src_a + lane : nullptr;
+  const st *sb = (HAS_SRC && TWO) ? src_b + lane : nullptr;
+  st *ra = HAS_R ? r_a + lane : nullptr;
+  st *rb = (HAS_R && TWO) ? r_b + lane : nullptr;
 
-  real cur1[kUnroll], cur2[kUnroll], cs[kUnroll];
-  real nx1[kUnroll], nx2[kUnroll], ns[kUnroll];
+  real cur1[kUnroll], cur2[kUnroll], csa[kUnroll], csb[kUnroll];
+  real nx1[kUnroll], nx2[kUnroll], nsa[kUnroll], nsb[kUnroll];
   const int G = d.ng;
 #pragma unroll
   for (int j = 0; j < kUnroll; j++) {
-    int g = G - 1 - j;
-    cur1[j] = cur2[j] = cs[j] = 0;
+    const int g = G - 1 - j;
+    cur1[j] = cur2[j] = csa[j] = csb[j] = 0;
     if (active && g >= 0) {
       cur1[j] = base[g * gstride];
       cur2[j] = base[g * gstride + d.lanes];
-      if (HAS_SRC) cs[j] = load_src<real, st>(sbase + (long long)g * d.lanes);
+      if (HAS_SRC) csa[j] = load_src<real, st>(sa + (long long)g * d.lanes);
+      if (HAS_SRC && TWO) csb[j] = load_src<real, st>(sb + (long long)g * d.lanes);
     }
   }
   for (int gb = G - 1; gb >= 0; gb -= kUnroll) {
 #pragma unroll
     for (int j = 0; j < kUnroll; j++) {
-      int g = gb - kUnroll - j;
-      nx1[j] = nx2[j] = ns[j] = 0;
+      const int g = gb - kUnroll - j;
+      nx1[j] = nx2[j] = nsa[j] = nsb[j] = 0;
       if (active && g >= 0) {
         nx1[j] = base[g * gstride];
         nx2[j] = base[g * gstride + d.lanes];
-        if (HAS_SRC) ns[j] = load_src<real, st>(sbase + (long long)g * d.lanes);
+        if (HAS_SRC) nsa[j] = load_src<real, st>(sa + (long long)g * d.lanes);
+        if (HAS_SRC && TWO) nsb[j] = load_src<real, st>(sb + (long long)g * d.lanes);
       }
     }
 #pragma unroll
@@ -116,94 +161,99 @@ __global__ void __launch_bounds__(kLanesX *kAnglesY) k_energy(Dims d, real *__re
       const int g = gb - j;
       if (g < 0) break;
       const GroupCoef<real> &k = tab[g];
-      const real o1 = cur1[j], o2 = cur2[j];
-      const real am = rc * k.sm, ap = rc * k.sp, sg = rc * k.sig;
-      // rhs = (I + c A_gg) psi_g + c A_up (old + new)_{g+1} + c src
-      real r0 = (real(1) - am - sg) * o1 + am * o2 + ap * carry;
-      real r1 = real(-3) * ap * o1 + (real(1) - ap - real(2) * am - sg) * o2 + real(3) * ap * carry;
-      if (HAS_SRC) r0 += c * cs[j];
-      // M = I - c A_gg = [[1+am+sg, -am], [3ap, 1+ap+2am+sg]]
-      const real m00 = real(1) + am + sg;
-      const real m11 = real(1) + ap + real(2) * am + sg;
-      const real inv = recip(m00 * m11 + real(3) * am * ap);
-      const real x1 = (m11 * r0 + am * r1) * inv;
-      const real x2 = (m00 * r1 - real(3) * ap * r0) * inv;
+      real x1, x2;
+      const real y1 = A.template group<HAS_SRC>(k, cur1[j], cur2[j], csa[j], x1, x2);
+      cnt += k.de * x1;
+      if (HAS_R) {
+        A.tsum = A.rho * k.q1 * y1 + k.decay * A.tsum;
+        if (active) store_st<st, real>(ra + (long long)g * d.lanes, A.tsum * k.inv_de);
+      }
+      if (TWO) {
+        real z1, z2;
+        const real w1 = B.template group<HAS_SRC>(k, x1, x2, csb[j], z1, z2);
+        if (HAS_R) {
+          B.tsum = B.rho * k.q1 * w1 + k.decay * B.tsum;
+          if (active) store_st<st, real>(rb + (long long)g * d.lanes, B.tsum * k.inv_de);
+        }
+        x1 = z1;
+        x2 = z2;
+      }
       if (active) {
         base[g * gstride] = x1;
         base[g * gstride + d.lanes] = x2;
-      }
-      // deposited energy content: -(phi_g^T c A_gg y_g + phi_g^T c A_up y_{g+1}) - c phi^T src
-      const real y1 = o1 + x1, y2 = o2 + x2;
-      real t = k.ehat * ((-am - sg) * y1 + am * y2) + k.dq * (real(-3) * ap * y1 + (-ap - real(2) * am - sg) * y2) +
-               (k.ehat + real(3) * k.dq) * ap * carry;
-      if (HAS_SRC) t += c * k.ehat * cs[j];
-      comp_add(dep, dep_c, -t);
-      carry = y1 - y2;
-      cnt += k.de * x1;
-      if (HAS_R) {
-        tsum = rho * k.q1 * y1 + k.decay * tsum;
-        if (active) store_st<st, real>(rbase + (long long)g * d.lanes, tsum * k.inv_de);
       }
     }
 #pragma unroll
     for (int j = 0; j < kUnroll; j++) {
       cur1[j] = nx1[j];
       cur2[j] = nx2[j];
-      cs[j] = ns[j];
+      csa[j] = nsa[j];
+      csb[j] = nsb[j];
     }
   }
 
   // reduce over the block's 8 angles and add to the voxel tallies
-  red_dep[threadIdx.y][threadIdx.x] = active ? (double)dep + (double)dep_c : 0.0;
-  red_flu[threadIdx.y][threadIdx.x] = active ? (double)cnt : 0.0;
+  red[0][threadIdx.y][threadIdx.x] = active ? (double)A.dep + (double)A.dep_c : 0.0;
+  red[1][threadIdx.y][threadIdx.x] = active ? (double)cnt : 0.0;
+  red[2][threadIdx.y][threadIdx.x] = (active && TWO) ? (double)B.dep + (double)B.dep_c : 0.0;
   __syncthreads();
   if (threadIdx.y == 0 && yz < d.nyz) {
-    double sd = 0.0, sf = 0.0;
+    double sa_ = 0.0, sf = 0.0, sb_ = 0.0;
 #pragma unroll
     for (int j = 0; j < kAnglesY; j++) {
-      sd += red_dep[j][threadIdx.x];
-      sf += red_flu[j][threadIdx.x];
+      sa_ += red[0][j][threadIdx.x];
+      sf += red[1][j][threadIdx.x];
+      sb_ += red[2][j][threadIdx.x];
     }
-    const double r = (double)rho_yz[yz];
-    if (dose && r > 0.0) atomicAdd(dose + yz, sd * dose_scale / r);
+    const double ra_ = (double)rho_a[yz];
+    if (dose_a && ra_ > 0.0) atomicAdd(dose_a + yz, sa_ * dose_scale / ra_);
     if (flu) atomicAdd(flu + yz, sf * flu_scale);
+    if (TWO) {
+      const double rb_ = (double)rho_b[yz];
+      if (dose_b && rb_ > 0.0) atomicAdd(dose_b + yz, sb_ * dose_scale / rb_);
+    }
   }
 }
 
 }  // namespace
 
 template <typename real, typename st>
-cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const st *src, st *r_out,
-                          const real *rho_yz, const GroupCoef<real> *coef, double *dose_yz, double *flu_yz,
-                          real c_half, double dose_scale, double flu_scale) {
+cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
+                          const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
+                          double dose_scale, double flu_scale) {
   dim3 block(kLanesX, kAnglesY);
   dim3 grid((d.nyz + kLanesX - 1) / kLanesX, (d.na + kAnglesY - 1) / kAnglesY);
-  size_t smem = sizeof(GroupCoef<real>) * d.ng;
+  const size_t smem = sizeof(GroupCoef<real>) * d.ng;
+  const bool has_src = ha.src != nullptr, has_r = ha.r_out != nullptr;
+  const EnergyHalf<real, st> &b = hb ? *hb : ha;
   auto go = [&](auto kern) -> cudaError_t {
     if (smem > 48 * 1024) {
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    kern<<<grid, block, smem, lc.stream>>>(d, psi_k, src, r_out, rho_yz, coef, dose_yz, flu_yz, c_half,
-                                           dose_scale, flu_scale);
+    kern<<<grid, block, smem, lc.stream>>>(d, psi_k, ha.src, b.src, ha.r_out, b.r_out, ha.rho, b.rho, coef, ha.dose,
+                                           b.dose, flu_yz, ha.c, b.c, dose_scale, flu_scale);
     ++*lc.launches;
     return cudaGetLastError();
   };
-  if (src && r_out) return go(k_energy<real, st, true, true>);
-  if (src) return go(k_energy<real, st, true, false>);
-  if (r_out) return go(k_energy<real, st, false, true>);
-  return go(k_energy<real, st, false, false>);
+#define PBS_E(S, R, T) \
+  if (has_src == S && has_r == R && (hb != nullptr) == T) return go(k_energy<real, st, S, R, T>);
+  PBS_E(true, true, true) PBS_E(true, false, true) PBS_E(false, true, true) PBS_E(false, false, true)
+  PBS_E(true, true, false) PBS_E(true, false, false) PBS_E(false, true, false) PBS_E(false, false, false)
+#undef PBS_E
+  return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_energy<double, double>(const LaunchCtx &, const Dims &, double *, const double *,
-                                                   double *, const double *, const GroupCoef<double> *, double *,
-                                                   double *, double, double, double);
-template cudaError_t launch_energy<float, float>(const LaunchCtx &, const Dims &, float *, const float *, float *,
-                                                 const float *, const GroupCoef<float> *, double *, double *,
-                                                 float, double, double);
+template cudaError_t launch_energy<double, double>(const LaunchCtx &, const Dims &, double *,
+                                                   const EnergyHalf<double, double> &,
+                                                   const EnergyHalf<double, double> *, const GroupCoef<double> *,
+                                                   double *, double, double);
+template cudaError_t launch_energy<float, float>(const LaunchCtx &, const Dims &, float *,
+                                                 const EnergyHalf<float, float> &, const EnergyHalf<float, float> *,
+                                                 const GroupCoef<float> *, double *, double, double);
 template cudaError_t launch_energy<float, __nv_bfloat16>(const LaunchCtx &, const Dims &, float *,
-                                                         const __nv_bfloat16 *, __nv_bfloat16 *, const float *,
-                                                         const GroupCoef<float> *, double *, double *, float,
-                                                         double, double);
+                                                         const EnergyHalf<float, __nv_bfloat16> &,
+                                                         const EnergyHalf<float, __nv_bfloat16> *,
+                                                         const GroupCoef<float> *, double *, double, double);
 
 }  // namespace pbs

@@ -7,20 +7,21 @@
 //
 // GB300 design.  A group of lanes owns one (component, g, c, u, v) plane; each
 // lane owns 4 adjacent z columns, so one row of up to 128 columns is one warp.
-// The group streams down the plane one row per iteration:
-//   * rows arrive by per-lane cp.async (16-byte, zero-filled out of range)
-//     into a small per-warp ring in shared memory, P rows ahead; a lane only
-//     reads back what it copied, so no barrier is needed;
-//   * in the march frame the flow is positive, so a face flux only looks
-//     upstream: stage 1 (psi*) runs 1 row behind the newest row and stage 2
-//     (psi_new) 2 rows behind, both from sliding windows of 4 rows kept in
-//     registers; every y face flux is evaluated once;
-//   * z neighbours across lanes come from warp shuffles;
-//   * when u < 0 the group marches from the last row to the first, so in the
-//     march frame the y flow is always positive and the upwind stencil needs
-//     no selection (the scheme is symmetric under y -> -y);
+//   * The scheme is symmetric under y -> -y and z -> -z, so each plane is
+//     processed in a "march frame" in which both speeds are >= 0: rows are
+//     visited from the last to the first when u < 0, and the lane -> column
+//     map is mirrored when v < 0.  Every face flux is then the plain upwind
+//     form  |s| (B + slope(B - A, C - B) / 2)  with no stencil selection, the
+//     left edge is an inflow face (zero flux) and the flux through a lane's
+//     left face is its left neighbour's right face (one shuffle).
+//   * Rows arrive by per-lane cp.async (zero-filled out of range) into a
+//     small per-warp ring in shared memory, kP rows ahead; a lane only reads
+//     back what it copied, so no barrier is needed.
+//   * Stage 1 (psi*) runs 1 row behind the newest row and stage 2 (psi_new)
+//     2 rows behind, from sliding windows kept in registers; every face flux
+//     is evaluated once per stage.
 //   * psi_new is stored in place 2 rows behind the loads.
-// Fluxes are pre-scaled by h/dy (h/dz), so psi* = psi + (F_lo - F_hi) + (G_lo - G_hi).
+// Fluxes are pre-scaled by h/dy (h/dz): psi* = psi + (F_lo - F_hi) + (G_lo - G_hi).
 #include "pbs_internal.cuh"
 
 namespace pbs {
@@ -53,80 +54,215 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Upwind face value for flow from A through B to C (positive direction):
-//   B + slope(B - A, C - B) / 2, with the superbee slope.
+// x with its sign flipped where s is negative.
+__device__ __forceinline__ float flip_by(float x, float s) {
+  return __uint_as_float(__float_as_uint(x) ^ (__float_as_uint(s) & 0x80000000u));
+}
+__device__ __forceinline__ double flip_by(double x, double s) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (__double_as_longlong(s) & (long long)0x8000000000000000ULL));
+}
+
+// Upwind face value for flow from A through B to C:  B + slope / 2 with the
+// superbee slope of d1 = B - A, d2 = C - B:
+//   slope = sign(d2) max(0, min(max(x, |d2|), 2 min(x, |d2|))),  x = d1 sign(d2),
+// which is 0 when d1, d2 differ in sign (x < 0) and otherwise
+// sign(d2) min(max|d|, 2 min|d|) = d2 eta(d1/d2).
 template <typename real>
-__device__ __forceinline__ real face_value(real A, real B, real C) {
-  const real d1 = B - A, d2 = C - B;
-  const real a1 = fabs(d1), a2 = fabs(d2);
-  const real m = fmin(fmax(a1, a2), real(2) * fmin(a1, a2));  // zero if either difference is zero
-  const real sl = same_sign(d1, d2) ? copysign(m, d2) : real(0);
-  return fma(real(0.5), sl, B);
+__device__ __forceinline__ real face_value_d(real B, real d1, real d2) {
+  const real a2 = fabs(d2);
+  const real x = flip_by(d1, d2);
+  real m = fmin(fmax(x, a2), real(2) * fmin(x, a2));
+  m = fmax(m, real(0));
+  return fma(real(0.5), copysign(m, d2), B);
 }
 
 template <typename real, bool VEC>
 struct RowIO {
-  // Issue the copy of row `row` (columns col0..col0+3) of a plane into `dst`.
-  static __device__ __forceinline__ void issue(real *dst, const real *plane_base, int row, int nz, int col0, bool on) {
-    const real *src = plane_base + (long long)row * nz + col0;
+  // Copy row `row` of a plane into the lane's ring slot `dst`.  Mirrored
+  // VEC rows land in physical order and are reversed on read.
+  static __device__ __forceinline__ void issue(real *dst, const real *plane_base, int row, int nz, int col0, bool fz,
+                                               bool on) {
+    const real *rowp = plane_base + (long long)row * nz;
     if (VEC) {
+      const int pc = fz ? col0 : nz - kV - col0;  // physical first column of the lane's chunk
       const unsigned nb = on ? 16u : 0u;
 #pragma unroll
       for (int k = 0; k < (int)(kV * sizeof(real) / 16); k++)
-        cp_async16(dst + k * (16 / sizeof(real)), on ? src + k * (16 / sizeof(real)) : plane_base, nb);
+        cp_async16(dst + k * (16 / sizeof(real)), on ? rowp + pc + k * (16 / sizeof(real)) : plane_base, nb);
     } else {
 #pragma unroll
       for (int k = 0; k < kV; k++) {
-        const bool in = on && (col0 + k < nz);
+        const int q = col0 + k;
+        const bool in = on && (q < nz);
+        const int pcol = fz ? q : nz - 1 - q;
         if (sizeof(real) == 8)
-          cp_async8(dst + k, in ? src + k : plane_base, in ? 8u : 0u);
+          cp_async8(dst + k, in ? rowp + pcol : plane_base, in ? 8u : 0u);
         else
-          cp_async4(dst + k, in ? src + k : plane_base, in ? 4u : 0u);
+          cp_async4(dst + k, in ? rowp + pcol : plane_base, in ? 4u : 0u);
       }
     }
   }
-  static __device__ __forceinline__ void store(real *plane_base, int row, int nz, int col0, bool on, const V4<real> &x) {
-    if (!on) return;
-    real *dst = plane_base + (long long)row * nz + col0;
+  static __device__ __forceinline__ void read(const real *src, bool fz, V4<real> &x) {
     if (VEC) {
-      if (sizeof(real) == 4) {
-        *reinterpret_cast<float4 *>(dst) = make_float4((float)x.v[0], (float)x.v[1], (float)x.v[2], (float)x.v[3]);
-      } else {
-        reinterpret_cast<double2 *>(dst)[0] = make_double2((double)x.v[0], (double)x.v[1]);
-        reinterpret_cast<double2 *>(dst)[1] = make_double2((double)x.v[2], (double)x.v[3]);
+#pragma unroll
+      for (int k = 0; k < kV; k++) {
+        const real a = src[k], b = src[kV - 1 - k];
+        x.v[k] = fz ? a : b;
       }
     } else {
 #pragma unroll
-      for (int k = 0; k < kV; k++)
-        if (col0 + k < nz) dst[k] = x.v[k];
+      for (int k = 0; k < kV; k++) x.v[k] = src[k];
+    }
+  }
+  static __device__ __forceinline__ void store(real *plane_base, int row, int nz, int col0, bool fz, bool on,
+                                               const V4<real> &x) {
+    if (!on) return;
+    real *rowp = plane_base + (long long)row * nz;
+    if (VEC) {
+      const int pc = fz ? col0 : nz - kV - col0;
+      real y[kV];
+#pragma unroll
+      for (int k = 0; k < kV; k++) y[k] = fz ? x.v[k] : x.v[kV - 1 - k];
+      if (sizeof(real) == 4) {
+        *reinterpret_cast<float4 *>(rowp + pc) = make_float4((float)y[0], (float)y[1], (float)y[2], (float)y[3]);
+      } else {
+        reinterpret_cast<double2 *>(rowp + pc)[0] = make_double2((double)y[0], (double)y[1]);
+        reinterpret_cast<double2 *>(rowp + pc)[1] = make_double2((double)y[2], (double)y[3]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kV; k++) {
+        const int q = col0 + k;
+        if (q < nz) rowp[fz ? q : nz - 1 - q] = x.v[k];
+      }
     }
   }
 };
 
-// z-direction contribution G_lo - G_hi for the lane's 4 cells of one row.
-// gs: signed v * h / dz.  Neighbour columns come from the adjacent lanes of
-// the group (zero at the plane's edges).
+// z contribution (G_lo - G_hi) h/dz for the lane's 4 cells of one row in the
+// march frame (positive flow).  gz = |v| h / dz.
 template <typename real>
-__device__ __forceinline__ void z_delta(const V4<real> &c, real gs, bool vpos, int li, int lp, int gw, V4<real> &out) {
-  real l2 = __shfl_up_sync(0xffffffffu, c.v[2], 1, gw);
-  real l1 = __shfl_up_sync(0xffffffffu, c.v[3], 1, gw);
-  real r1 = __shfl_down_sync(0xffffffffu, c.v[0], 1, gw);
-  real r2 = __shfl_down_sync(0xffffffffu, c.v[1], 1, gw);
-  if (li == 0) { l2 = real(0); l1 = real(0); }
-  if (li >= lp - 1) { r1 = real(0); r2 = real(0); }
-  const real x[8] = {l2, l1, c.v[0], c.v[1], c.v[2], c.v[3], r1, r2};
-  real g[5];
+__device__ __forceinline__ void z_delta(const V4<real> &c, real gz, int li, int lp, int gw, V4<real> &out) {
+  real lft = __shfl_up_sync(0xffffffffu, c.v[kV - 1], 1, gw);  // column 4l-1
+  real rgt = __shfl_down_sync(0xffffffffu, c.v[0], 1, gw);     // column 4l+4
+  if (li == 0) lft = real(0);
+  if (li >= lp - 1) rgt = real(0);
+  // right faces 4l+k+1/2 of the lane's cells
+  real g[kV];
+  const real d0 = c.v[0] - lft;
+  const real d1 = c.v[1] - c.v[0];
+  const real d2 = c.v[2] - c.v[1];
+  const real d3 = c.v[3] - c.v[2];
+  const real d4 = rgt - c.v[3];
+  g[0] = gz * face_value_d(c.v[0], d0, d1);
+  g[1] = gz * face_value_d(c.v[1], d1, d2);
+  g[2] = gz * face_value_d(c.v[2], d2, d3);
+  g[3] = gz * face_value_d(c.v[3], d3, d4);
+  real glo = __shfl_up_sync(0xffffffffu, g[kV - 1], 1, gw);  // left face = neighbour's last right face
+  if (li == 0) glo = real(0);                                  // inflow edge: zero ghosts upstream
+  out.v[0] = glo - g[0];
 #pragma unroll
-  for (int k = 0; k < 5; k++) {
-    // face between x[k+1] and x[k+2]
-    const real A = vpos ? x[k] : x[k + 3];
-    const real B = vpos ? x[k + 1] : x[k + 2];
-    const real C = vpos ? x[k + 2] : x[k + 1];
-    g[k] = gs * face_value(A, B, C);
-  }
-#pragma unroll
-  for (int j = 0; j < kV; j++) out.v[j] = g[j] - g[j + 1];
+  for (int j = 1; j < kV; j++) out.v[j] = g[j - 1] - g[j];
 }
+
+template <typename real, bool VEC>
+struct PlaneMarch {
+  real *ring;  // this lane's ring base (slot stride 32*kV)
+  real *pbase;
+  int ny, nz, col0, li, lp, gw;
+  bool fwd, fz, on;
+  real sy, gz;
+  int rd, wr;
+  V4<real> w[4], st[4];  // psi rows i-3..i, psi* rows i-4..i-1 (march order)
+  V4<real> f1, f2;       // carried y face fluxes of stage 1 and stage 2
+  V4<real> e1, e2;       // carried y differences of stage 1 and stage 2
+
+  __device__ __forceinline__ int prow(int m) const { return fwd ? m : ny - 1 - m; }
+
+  __device__ __forceinline__ void prologue() {
+    wr = 0;
+    rd = 0;
+#pragma unroll
+    for (int j = 0; j < kP; j++) {
+      if (j < ny) RowIO<real, VEC>::issue(ring + wr * 32 * kV, pbase, prow(j), nz, col0, fz, on);
+      cp_async_commit();
+      wr++;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+      for (int j = 0; j < kV; j++) w[k].v[j] = st[k].v[j] = real(0);
+  }
+
+  // One march iteration i.  LOAD: row i exists (i < ny).  S1: stage 1 for
+  // row i-1.  S2: stage 2 for row i-2.  FIRST1/FIRST2: the stage's first row
+  // (initialise its carried flux).  IN1: row i-1 < ny.
+  template <bool LOAD, bool S1, bool FIRST1, bool IN1, bool S2, bool FIRST2>
+  __device__ __forceinline__ void iter(int i) {
+    cp_async_wait<kP - 1>();
+    V4<real> x;
+    if (LOAD) {
+      RowIO<real, VEC>::read(ring + rd * 32 * kV, fz, x);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kV; j++) x.v[j] = real(0);
+    }
+    rd = (rd + 1 == kR) ? 0 : rd + 1;
+    if (i + kP < ny) RowIO<real, VEC>::issue(ring + wr * 32 * kV, pbase, prow(i + kP), nz, col0, fz, on);
+    cp_async_commit();
+    wr = (wr + 1 == kR) ? 0 : wr + 1;
+#pragma unroll
+    for (int k = 0; k < 3; k++) w[k] = w[k + 1];
+    w[3] = x;
+
+    if (S1) {  // row m = i-1 needs psi(m-2..m+1) = w[0..3]
+      if (FIRST1) {
+#pragma unroll
+        for (int j = 0; j < kV; j++) {
+          const real d0 = w[1].v[j] - w[0].v[j];
+          const real d = w[2].v[j] - w[1].v[j];
+          f1.v[j] = sy * face_value_d(w[1].v[j], d0, d);  // face m - 1/2
+          e1.v[j] = d;
+        }
+      }
+      V4<real> dz, s;
+      z_delta(w[2], gz, li, lp, gw, dz);
+#pragma unroll
+      for (int j = 0; j < kV; j++) {
+        const real d = w[3].v[j] - w[2].v[j];
+        const real fh = sy * face_value_d(w[2].v[j], e1.v[j], d);  // face m + 1/2
+        e1.v[j] = d;
+        s.v[j] = (IN1 && (VEC || col0 + j < nz)) ? w[2].v[j] + (f1.v[j] - fh) + dz.v[j] : real(0);
+        f1.v[j] = fh;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; k++) st[k] = st[k + 1];
+      st[3] = s;
+    }
+    if (S2) {  // row m' = i-2 needs psi*(m'-2..m'+1) = st[0..3] and psi(m') = w[1]
+      if (FIRST2) {
+#pragma unroll
+        for (int j = 0; j < kV; j++) {
+          const real d0 = st[1].v[j] - st[0].v[j];
+          const real d = st[2].v[j] - st[1].v[j];
+          f2.v[j] = sy * face_value_d(st[1].v[j], d0, d);
+          e2.v[j] = d;
+        }
+      }
+      V4<real> dz, o;
+      z_delta(st[2], gz, li, lp, gw, dz);
+#pragma unroll
+      for (int j = 0; j < kV; j++) {
+        const real d = st[3].v[j] - st[2].v[j];
+        const real fh = sy * face_value_d(st[2].v[j], e2.v[j], d);
+        e2.v[j] = d;
+        o.v[j] = real(0.5) * (w[1].v[j] + st[2].v[j] + (f2.v[j] - fh) + dz.v[j]);
+        f2.v[j] = fh;
+      }
+      RowIO<real, VEC>::store(pbase, prow(i - 2), nz, col0, fz, on, o);
+    }
+  }
+};
 
 template <typename real, bool VEC>
 __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict__ psi, long long nplanes, int ny, int nz,
@@ -135,100 +271,51 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  real *ring = reinterpret_cast<real *>(smem_raw) + ((size_t)warp * kR * 32 + lane) * kV;  // slot stride 32*kV
   const int ngroups = 32 / gw;
   const int gi = lane / gw;
-  const int li = lane % gw;
-  const int col0 = li * kV;
-  const bool lane_on = li < lp;
   const long long gwarp = (long long)blockIdx.x * kWarps + warp;
   const long long nwarps = (long long)gridDim.x * kWarps;
+
+  PlaneMarch<real, VEC> pm;
+  pm.ring = reinterpret_cast<real *>(smem_raw) + ((size_t)warp * kR * 32 + lane) * kV;
+  pm.ny = ny;
+  pm.nz = nz;
+  pm.li = lane % gw;
+  pm.col0 = pm.li * kV;
+  pm.lp = lp;
+  pm.gw = gw;
+  const bool lane_on = pm.li < lp;
 
   for (long long base = gwarp * ngroups; base < nplanes; base += nwarps * ngroups) {
     const long long plane = base + gi;
     const bool valid = plane < nplanes;
-    const bool on = valid && lane_on;
+    pm.on = valid && lane_on;
     const int a = valid ? (int)(plane % na) : 0;
     const real uu = (real)((a % nu) - 0.5 * (nu - 1)) * du;
     const real vv = (real)((a / nu) - 0.5 * (nv - 1)) * dv;
-    const bool fwd = uu >= real(0);
-    const real sy = fabs(uu) * ky;  // |u| h / dy in the march frame
-    const real gz = vv * kz;        // v h / dz (signed)
-    const bool vpos = vv > real(0);
-    real *pbase = psi + (valid ? plane : 0) * (long long)ny * nz;
-
-    // prologue: rows 0..kP-1 of the march order
-    int wr = 0;
-#pragma unroll
-    for (int j = 0; j < kP; j++) {
-      if (j < ny) RowIO<real, VEC>::issue(ring + wr * 32 * kV, pbase, fwd ? j : ny - 1 - j, nz, col0, on);
-      cp_async_commit();
-      wr++;
-    }
-    int rd = 0;
-    // w: psi of march rows i-3..i; st: psi* of march rows i-4..i-1
-    V4<real> w[4], st[4];
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-#pragma unroll
-      for (int j = 0; j < kV; j++) w[k].v[j] = st[k].v[j] = real(0);
-    V4<real> f1, f2;  // carried y face fluxes (face m - 1/2) of stage 1 and stage 2
-#pragma unroll
-    for (int j = 0; j < kV; j++) f1.v[j] = f2.v[j] = real(0);
-
-    for (int i = 0; i < ny + 2; i++) {
-      cp_async_wait<kP - 1>();
-      V4<real> x;
-      if (i < ny) {
-        const real *src = ring + rd * 32 * kV;
-#pragma unroll
-        for (int j = 0; j < kV; j++) x.v[j] = src[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < kV; j++) x.v[j] = real(0);
-      }
-      rd = (rd + 1 == kR) ? 0 : rd + 1;
-      if (i + kP < ny) RowIO<real, VEC>::issue(ring + wr * 32 * kV, pbase, fwd ? i + kP : ny - 1 - (i + kP), nz, col0, on);
-      cp_async_commit();
-      wr = (wr + 1 == kR) ? 0 : wr + 1;
-#pragma unroll
-      for (int k = 0; k < 3; k++) w[k] = w[k + 1];
-      w[3] = x;
-
-      if (i >= 1) {  // stage 1 for march row m = i-1: needs psi(m-2..m+1) = w[0..3]
-        if (i == 1) {
-#pragma unroll
-          for (int j = 0; j < kV; j++) f1.v[j] = sy * face_value(w[0].v[j], w[1].v[j], w[2].v[j]);
-        }
-        V4<real> dz, s;
-        z_delta(w[2], gz, vpos, li, lp, gw, dz);
-        const bool row_in = (i - 1) < ny;
-#pragma unroll
-        for (int j = 0; j < kV; j++) {
-          const real fh = sy * face_value(w[1].v[j], w[2].v[j], w[3].v[j]);  // face m + 1/2
-          s.v[j] = (row_in && col0 + j < nz) ? w[2].v[j] + (f1.v[j] - fh) + dz.v[j] : real(0);
-          f1.v[j] = fh;
-        }
-#pragma unroll
-        for (int k = 0; k < 3; k++) st[k] = st[k + 1];
-        st[3] = s;
-      }
-      if (i >= 2) {  // stage 2 for march row m' = i-2: needs psi*(m'-2..m'+1) = st[0..3], psi(m') = w[1]
-        if (i == 2) {
-#pragma unroll
-          for (int j = 0; j < kV; j++) f2.v[j] = sy * face_value(st[0].v[j], st[1].v[j], st[2].v[j]);
-        }
-        V4<real> dz, o;
-        z_delta(st[2], gz, vpos, li, lp, gw, dz);
-#pragma unroll
-        for (int j = 0; j < kV; j++) {
-          const real fh = sy * face_value(st[1].v[j], st[2].v[j], st[3].v[j]);
-          o.v[j] = real(0.5) * (w[1].v[j] + st[2].v[j] + (f2.v[j] - fh) + dz.v[j]);
-          f2.v[j] = fh;
-        }
-        const int r2 = i - 2;
-        RowIO<real, VEC>::store(pbase, fwd ? r2 : ny - 1 - r2, nz, col0, on, o);
-      }
+    pm.fwd = uu >= real(0);
+    pm.fz = vv >= real(0);
+    pm.sy = fabs(uu) * ky;
+    pm.gz = fabs(vv) * kz;
+    pm.pbase = psi + (valid ? plane : 0) * (long long)ny * nz;
+    pm.prologue();
+    if (ny >= 3) {
+      pm.template iter<true, false, false, true, false, false>(0);
+      pm.template iter<true, true, true, true, false, false>(1);
+      pm.template iter<true, true, false, true, true, true>(2);
+#pragma unroll 2
+      for (int i = 3; i < ny; i++) pm.template iter<true, true, false, true, true, false>(i);
+      pm.template iter<false, true, false, true, true, false>(ny);
+      pm.template iter<false, true, false, false, true, false>(ny + 1);
+    } else if (ny == 2) {
+      pm.template iter<true, false, false, true, false, false>(0);
+      pm.template iter<true, true, true, true, false, false>(1);
+      pm.template iter<false, true, false, true, true, true>(2);
+      pm.template iter<false, true, false, false, true, false>(3);
+    } else {  // ny == 1
+      pm.template iter<true, false, false, true, false, false>(0);
+      pm.template iter<false, true, true, true, false, false>(1);
+      pm.template iter<false, true, false, false, true, true>(2);
     }
   }
   cp_async_wait<0>();

@@ -34,6 +34,7 @@ struct pbs_ctx {
   bool have_tables = false, have_material = false, have_beam = false;
   int n_slabs = 0;
   int steps_done = 0;
+  bool pending = false;  // closing E(h/2) of the last step not applied yet
   // workspace
   unsigned char *ws = nullptr;
   size_t ws_bytes = 0;
@@ -79,8 +80,8 @@ void layout(pbs_ctx *c) {
   size_t o = 0;
   c->off_psi = o; o = align256(o + (size_t)c->d.ncomp * c->d.comp_elems * S);
   const size_t nsrc = (c->K > 0) ? (size_t)c->ng * c->na * nyz : 0;
-  c->off_r = o; o = align256(o + nsrc * SS);
-  c->off_s = o; o = align256(o + nsrc * SS);
+  c->off_r = o; o = align256(o + 2 * nsrc * SS);  // R for the first and second substep of a fused pair
+  c->off_s = o; o = align256(o + 2 * nsrc * SS);
   c->off_rho = o; o = align256(o + (size_t)c->nx * nyz * S);
   c->off_dose = o; o = align256(o + (size_t)c->nx * nyz * 8);
   c->off_flu = o; o = align256(o + (size_t)(c->nx + 1) * nyz * 8);
@@ -299,32 +300,50 @@ void beam_factors(const pbs_ctx *c, const pbs_beam &b, std::vector<double> &out)
 
 // ---------------------------------------------------------------- march
 
+// E substeps on all components in lock-step.  slab_b < 0: one substep E(h)
+// with slab_a.  slab_b >= 0: two back-to-back substeps E(h) (slab_a, then
+// slab_b) fused in one pass per component.  Fluence after the first substep
+// goes to plane flu_plane (if >= 0).
 template <typename real, typename st>
-pbs_status energy_all(pbs_ctx *c, double h, int slab, int flu_plane) {
+pbs_status energy_run(pbs_ctx *c, double h, int slab_a, int slab_b, int flu_plane) {
   LaunchCtx lc = lctx(c);
   const size_t nyz = (size_t)c->ny * c->nz;
+  const size_t nsrc = (size_t)c->ng * c->na * nyz;
   real *psi = at<real>(c, c->off_psi);
-  const real *rho = at<real>(c, c->off_rho) + (size_t)slab * nyz;
-  double *dose = at<double>(c, c->off_dose) + (size_t)slab * nyz;
+  const real *rho = at<real>(c, c->off_rho);
+  double *dose = at<double>(c, c->off_dose);
   double *flu = flu_plane >= 0 ? at<double>(c, c->off_flu) + (size_t)flu_plane * nyz : nullptr;
   st *rbuf = at<st>(c, c->off_r), *sbuf = at<st>(c, c->off_s);
   const auto *coef = at<GroupCoef<real>>(c, c->off_coef);
+  const bool two = slab_b >= 0;
   for (int k = 0; k <= c->K; k++) {
+    EnergyHalf<real, st> ha{rho + (size_t)slab_a * nyz, (real)(0.5 * h), k >= 1 ? sbuf : nullptr,
+                            k < c->K ? rbuf : nullptr, dose + (size_t)slab_a * nyz};
+    EnergyHalf<real, st> hb{two ? rho + (size_t)slab_b * nyz : nullptr, (real)(0.5 * h),
+                            k >= 1 ? sbuf + nsrc : nullptr, k < c->K ? rbuf + nsrc : nullptr,
+                            two ? dose + (size_t)slab_b * nyz : nullptr};
     cudaError_t e;
     {
       ProfScope ps(c, PBS_KERNEL_ENERGY);
-      e = launch_energy<real, st>(lc, c->d, psi + (size_t)k * c->d.comp_elems, k >= 1 ? sbuf : nullptr,
-                                  k < c->K ? rbuf : nullptr, rho, coef, dose, flu, (real)(0.5 * h),
+      e = launch_energy<real, st>(lc, c->d, psi + (size_t)k * c->d.comp_elems, ha, two ? &hb : nullptr, coef, flu,
                                   c->du * c->dv / c->dx, c->du * c->dv);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "energy kernel");
     if (k < c->K) {
-      ProfScope ps(c, PBS_KERNEL_SOURCE);
-      e = launch_source<real, st>(lc, c->d, at<st>(c, c->off_p2), rbuf, sbuf, c->du * c->dv);
-      if (e != cudaSuccess) return cuda_fail(c, e, "source kernel");
+      for (int half = 0; half < (two ? 2 : 1); half++) {
+        ProfScope ps(c, PBS_KERNEL_SOURCE);
+        e = launch_source<real, st>(lc, c->d, at<st>(c, c->off_p2), rbuf + half * nsrc, sbuf + half * nsrc,
+                                    c->du * c->dv);
+        if (e != cudaSuccess) return cuda_fail(c, e, "source kernel");
+      }
     }
   }
   return PBS_OK;
+}
+
+template <typename real, typename st>
+pbs_status energy_all(pbs_ctx *c, double h, int slab, int flu_plane) {
+  return energy_run<real, st>(c, h, slab, -1, flu_plane);
 }
 
 template <typename real>
@@ -348,16 +367,32 @@ pbs_status angular_all(pbs_ctx *c, double h, int slab) {
   return e == cudaSuccess ? PBS_OK : cuda_fail(c, e, "angular kernel");
 }
 
+// Apply a deferred closing E(h/2) (of depth step steps_done - 1).
+template <typename real, typename st>
+pbs_status flush_impl(pbs_ctx *c) {
+  if (!c->pending) return PBS_OK;
+  c->pending = false;
+  return energy_run<real, st>(c, 0.5 * c->dx, c->steps_done - 1, -1, c->steps_done);
+}
+
+// Depth steps.  The closing E(h/2) of a step is deferred and fused with the
+// opening E(h/2) of the next (same arithmetic, one pass over psi instead of
+// two); any read or substep call applies a deferred half first.
 template <typename real, typename st>
 pbs_status step_impl(pbs_ctx *c, int n) {
   for (int i = 0; i < n; i++) {
     const int s = c->steps_done;
     pbs_status r;
-    if ((r = energy_all<real, st>(c, 0.5 * c->dx, s, -1)) != PBS_OK) return r;
+    if (c->pending)
+      r = energy_run<real, st>(c, 0.5 * c->dx, s - 1, s, s);  // close step s-1, open step s
+    else
+      r = energy_run<real, st>(c, 0.5 * c->dx, s, -1, -1);
+    c->pending = false;
+    if (r != PBS_OK) return r;
     if ((r = transport_all<real>(c, 0.5 * c->dx)) != PBS_OK) return r;
     if ((r = angular_all<real>(c, c->dx, s)) != PBS_OK) return r;
     if ((r = transport_all<real>(c, 0.5 * c->dx)) != PBS_OK) return r;
-    if ((r = energy_all<real, st>(c, 0.5 * c->dx, s, s + 1)) != PBS_OK) return r;
+    c->pending = true;
     c->steps_done++;
   }
   return PBS_OK;
@@ -383,6 +418,7 @@ pbs_status launch_impl(pbs_ctx *c, const pbs_beam &b) {
   if (e != cudaSuccess) return cuda_fail(c, e, "fluence kernel");
   PBS_CUDA(c, cudaStreamSynchronize(c->stream));  // f dies here
   c->steps_done = 0;
+  c->pending = false;
   return PBS_OK;
 }
 
@@ -473,6 +509,10 @@ pbs_status pbs_create(pbs_ctx **out, const pbs_grid *g, int precision, void *str
     delete c;
     return PBS_ERR_CUDA;
   }
+  if (angular_init_tables() != cudaSuccess) {
+    delete c;
+    return PBS_ERR_CUDA;
+  }
   c->stream = (cudaStream_t)stream;
   c->precision = precision;
   c->ny = g->ny; c->nz = g->nz; c->ng = g->ng; c->nu = g->nu; c->nv = g->nv; c->na = g->nu * g->nv;
@@ -517,6 +557,7 @@ pbs_status pbs_bind_workspace(pbs_ctx *c, void *p, size_t bytes) {
   c->ws_bytes = bytes;
   c->have_beam = false;
   c->have_material = false;
+  c->pending = false;
   // start from a defined state: zero state, tallies and the device status word
   PBS_CUDA(c, cudaMemsetAsync(c->ws, 0, c->total, c->stream));
   PBS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -555,6 +596,7 @@ pbs_status pbs_get_tables(const pbs_ctx *c, double *s_face, double *ts, double *
 pbs_status pbs_set_material(pbs_ctx *c, const double *rho, int n) {
   if (!c || !rho || n < 1 || n > c->nx) return fail(c, PBS_ERR_ARG, "bad material");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "bind a workspace first");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   for (size_t e = 0; e < (size_t)n * c->ny * c->nz; e++)
     if (!(rho[e] >= 0.0) || !std::isfinite(rho[e])) return fail(c, PBS_ERR_ARG, "density must be finite and >= 0");
   pbs_status r = PBS_DISPATCH_R(c, set_material_impl, c, rho, n);
@@ -582,6 +624,12 @@ pbs_status pbs_step(pbs_ctx *c, int n) {
   return PBS_DISPATCH(c, step_impl, c, n);
 }
 
+pbs_status pbs_flush(pbs_ctx *c) {
+  if (!c) return PBS_ERR_ARG;
+  if (!c->ws) return PBS_OK;
+  return PBS_DISPATCH(c, flush_impl, c);
+}
+
 pbs_status pbs_get_depth(const pbs_ctx *c, int *s) {
   if (!c || !s) return PBS_ERR_ARG;
   *s = c->steps_done;
@@ -591,6 +639,7 @@ pbs_status pbs_get_depth(const pbs_ctx *c, int *s) {
 pbs_status pbs_read_dose(pbs_ctx *c, double *out, size_t n) {
   if (!c || !out) return fail(c, PBS_ERR_ARG, "null output");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   const size_t nyz = (size_t)c->ny * c->nz;
   if (n % nyz != 0 || n / nyz > (size_t)c->nx) return fail(c, PBS_ERR_ARG, "n must be n_slabs*ny*nz");
   PBS_CUDA(c, cudaMemcpyAsync(out, at<void>(c, c->off_dose), n * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -601,6 +650,7 @@ pbs_status pbs_read_dose(pbs_ctx *c, double *out, size_t n) {
 pbs_status pbs_read_fluence(pbs_ctx *c, double *out, size_t n) {
   if (!c || !out) return fail(c, PBS_ERR_ARG, "null output");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   const size_t nyz = (size_t)c->ny * c->nz;
   if (n % nyz != 0 || n / nyz > (size_t)c->steps_done + 1) return fail(c, PBS_ERR_ARG, "n must be n_planes*ny*nz");
   PBS_CUDA(c, cudaMemcpyAsync(out, at<void>(c, c->off_flu), n * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -611,6 +661,7 @@ pbs_status pbs_read_fluence(pbs_ctx *c, double *out, size_t n) {
 pbs_status pbs_read_psi(pbs_ctx *c, int k, double *out, size_t n) {
   if (!c || !out || k < 0 || k > c->K) return fail(c, PBS_ERR_ARG, "bad component");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   if (n != (size_t)c->d.comp_elems) return fail(c, PBS_ERR_ARG, "n must be ng*2*nu*nv*ny*nz");
   return PBS_DISPATCH_R(c, read_psi_impl, c, k, out);
 }
@@ -618,6 +669,7 @@ pbs_status pbs_read_psi(pbs_ctx *c, int k, double *out, size_t n) {
 pbs_status pbs_write_psi(pbs_ctx *c, int k, const double *in, size_t n) {
   if (!c || !in || k < 0 || k > c->K) return fail(c, PBS_ERR_ARG, "bad component");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   if (n != (size_t)c->d.comp_elems) return fail(c, PBS_ERR_ARG, "n must be ng*2*nu*nv*ny*nz");
   return PBS_DISPATCH_R(c, write_psi_impl, c, k, in);
 }
@@ -626,18 +678,21 @@ pbs_status pbs_substep_energy(pbs_ctx *c, double h, int slab, int flu_plane) {
   if (!c || !(h >= 0) || slab < 0 || slab >= c->n_slabs || flu_plane > c->nx)
     return fail(c, PBS_ERR_ARG, "bad substep arguments");
   if (!c->ws || !c->have_tables || !c->have_material) return fail(c, PBS_ERR_STATE, "not set up");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   return PBS_DISPATCH(c, energy_all, c, h, slab, flu_plane);
 }
 
 pbs_status pbs_substep_transport(pbs_ctx *c, double h) {
   if (!c || !(h >= 0)) return fail(c, PBS_ERR_ARG, "bad substep arguments");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "not set up");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   return PBS_DISPATCH_R(c, transport_all, c, h);
 }
 
 pbs_status pbs_substep_angular(pbs_ctx *c, double h, int slab) {
   if (!c || !(h >= 0) || slab < 0 || slab >= c->n_slabs) return fail(c, PBS_ERR_ARG, "bad substep arguments");
   if (!c->ws || !c->have_tables || !c->have_material) return fail(c, PBS_ERR_STATE, "not set up");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   return PBS_DISPATCH_R(c, angular_all, c, h, slab);
 }
 
@@ -646,6 +701,7 @@ pbs_status pbs_eval_source(pbs_ctx *c, int k_from, int slab, double *out, size_t
     return fail(c, PBS_ERR_ARG, "bad arguments");
   if (c->K < 1) return fail(c, PBS_ERR_STATE, "the context has no scattered component (n_scatter = 0)");
   if (!c->ws || !c->have_tables || !c->have_material) return fail(c, PBS_ERR_STATE, "not set up");
+  { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   if (n != (size_t)c->ng * c->na * c->ny * c->nz) return fail(c, PBS_ERR_ARG, "n must be ng*nu*nv*ny*nz");
   return PBS_DISPATCH(c, eval_source_impl, c, k_from, slab, out);
 }

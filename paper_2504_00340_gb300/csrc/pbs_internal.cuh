@@ -2,8 +2,9 @@
 //
 // Layout of the device workspace (one context):
 //   psi   [k][g][c][a][p][q]      (K+1) components, real = double or float
-//   rbuf  [g][a][p][q]            energy-summed catastrophic source input R (K>0)
-//   sbuf  [g][a][p][q]            catastrophic source src = du dv P2_g R  (K>0)
+//   rbuf  2 x [g][a][p][q]        energy-summed catastrophic source input R (K>0),
+//                                 one per E substep of a fused pair
+//   sbuf  2 x [g][a][p][q]        catastrophic source src = du dv P2_g R  (K>0)
 //   rho   [s][p][q]               density per depth slab, real
 //   dose  [s][p][q]               FP64 dose tally
 //   flu   [s][p][q]               FP64 planar fluence at depth s*dx
@@ -143,10 +144,24 @@ struct LaunchCtx {
   long long *launches;  // host counter
 };
 
+// One E substep's per-lane inputs and outputs: density of its slab, c = h/2,
+// source of this component (sum of the trapezoid ends, or NULL), energy-summed
+// source input R for the next component (or NULL), dose slab.
 template <typename real, typename st>
-cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const st *src, st *r_out,
-                          const real *rho_yz, const GroupCoef<real> *coef, double *dose_yz, double *flu_yz,
-                          real c_half, double dose_scale, double flu_scale);
+struct EnergyHalf {
+  const real *rho;
+  real c;
+  const st *src;
+  st *r_out;
+  double *dose;
+};
+
+// E substep on one component; with hb != NULL, two consecutive E substeps
+// (ha then hb) fused in one pass.  flu_yz receives the fluence after ha.
+template <typename real, typename st>
+cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
+                          const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
+                          double dose_scale, double flu_scale);
 
 template <typename real>
 cudaError_t launch_transport(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
@@ -163,6 +178,9 @@ cudaError_t launch_angular(const LaunchCtx &lc, const Dims &d, real *psi, const 
                            double h, double du, double dv);
 
 bool angular_supported(int nu, int nv);
+// Load the sine-transform tables into the current device's constant bank
+// (synchronous; done once per context at creation).
+cudaError_t angular_init_tables();
 
 template <typename real, typename st>
 cudaError_t launch_source(const LaunchCtx &lc, const Dims &d, const st *p2, const st *r, st *src, double dudv);

@@ -23,6 +23,7 @@ def state():
     s.set_material(np.ones((8, w.ny, w.nz)))
     s.launch_beam(**w.beam)
     s.step(3)
+    s.flush()  # apply the deferred closing half step before reading psi through the raw view
     torch.cuda.synchronize()
     yield s, w, oracle, torch
     s.close()
