@@ -188,6 +188,34 @@ pbs_status pbs_substep_angular(pbs_ctx *ctx, double h, int slab);
  * n = ng*nu*nv*ny*nz.  Synchronises. */
 pbs_status pbs_eval_source(pbs_ctx *ctx, int k_from, int slab, double *host_out, size_t n);
 
+/* Allocation-free variant of pbs_eval_source, for callers that cannot
+ * allocate device memory (no cudaMalloc and no caching allocator: e.g. code
+ * embedded in a host framework that hands it pre-carved device buffers).  The
+ * paper has no counterpart to this call; it evaluates the same catastrophic
+ * source of Remark 1 as pbs_eval_source on an FP32 context, without a
+ * context or workspace:
+ *   psi_k    device, FP32 component [g][c][j][i][p][q] (ng*2*nu*nv*ny*nz)
+ *   rho_yz   device, FP32 density of the slab [p][q]
+ *   p2       device, FP32 P^2 matrices [g][a][a'] (ng*na*na), e.g. the FP64
+ *            tables of pbs_get_tables converted to float
+ *   e_faces  host, ng+1 ascending group faces (MeV), read during the call
+ *   sigma_ct, lambda_p1  as in pbs_physics;  u_max, v_max  as in pbs_grid
+ *   src_out  device, FP32 [g][j][i][p][q] (ng*nu*nv*ny*nz), written
+ *   stream   cudaStream_t (may be NULL); the call is asynchronous.
+ * Its only scratch is a 16 MiB array in the library's own device memory
+ * (a file-scope __device__ array that every device loading the library holds
+ * until exit), so ng*nu*nv*ny*nz must not exceed 4 Mi (= 4194304) elements
+ * and ng must not exceed 2048: larger calls return PBS_ERR_UNSUPPORTED.  The
+ * call allocates no device memory.  Its first call on a device looks up the
+ * array's device address (once per device, with that device current): make
+ * that first call before any stream capture.  All calls share the one
+ * scratch array, whose contents are fully overwritten by each call; calls
+ * that overlap on the GPU (different streams, or devices sharing nothing
+ * else) race on it and must be serialised by the caller. */
+pbs_status pbs_eval_source_noalloc(const float *psi_k, const float *rho_yz, const float *p2, const double *e_faces,
+                                   int ng, int nu, int nv, int ny, int nz, double u_max, double v_max,
+                                   double sigma_ct, double lambda_p1, float *src_out, void *stream);
+
 /* Kernel kinds for per-kernel timing. */
 typedef enum {
   PBS_KERNEL_ENERGY = 0,     /* energy substep scan (incl. dose/fluence/R)   */

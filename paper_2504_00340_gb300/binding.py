@@ -71,6 +71,9 @@ SIGNATURES = [
     ("pbs_substep_transport", ctypes.c_int, [_VP, ctypes.c_double]),
     ("pbs_substep_angular", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
     ("pbs_eval_source", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _D, ctypes.c_size_t]),
+    ("pbs_eval_source_noalloc", ctypes.c_int, [_VP, _VP, _VP, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, _VP, _VP]),
     ("pbs_kernel_launches", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong)]),
     ("pbs_set_profiling", ctypes.c_int, [_VP, ctypes.c_int]),
     ("pbs_profile_read", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
@@ -199,6 +202,19 @@ def pbs_substep_angular(ctx, h: float, slab: int) -> None:
 
 def pbs_eval_source(ctx, k_from: int, slab: int, out: np.ndarray) -> None:
     _check(ctx, load_library().pbs_eval_source(_VP(ctx), int(k_from), int(slab), _ptr(out), out.size))
+
+
+def pbs_eval_source_noalloc(psi_k_ptr: int, rho_ptr: int, p2_ptr: int, e_faces: np.ndarray, ng: int, nu: int,
+                            nv: int, ny: int, nz: int, u_max: float, v_max: float, sigma_ct: float,
+                            lambda_p1: float, src_ptr: int, stream: int | None) -> None:
+    """Allocation-free source evaluation on caller-owned FP32 device buffers
+    (raw device pointers); see include/pbs.h."""
+    ef = np.ascontiguousarray(np.asarray(e_faces, dtype=np.float64))
+    st = load_library().pbs_eval_source_noalloc(_VP(psi_k_ptr), _VP(rho_ptr), _VP(p2_ptr), _ptr(ef), int(ng), int(nu),
+                                                int(nv), int(ny), int(nz), float(u_max), float(v_max),
+                                                float(sigma_ct), float(lambda_p1), _VP(src_ptr), _VP(stream or 0))
+    if st != 0:
+        raise PbsError(st, load_library().pbs_status_string(st).decode())
 
 
 def pbs_kernel_launches(ctx) -> int:
