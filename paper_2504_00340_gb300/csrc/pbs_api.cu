@@ -96,7 +96,7 @@ void layout(pbs_ctx *c) {
 template <typename T>
 T *at(pbs_ctx *c, size_t off) { return reinterpret_cast<T *>(c->ws + off); }
 
-LaunchCtx lctx(pbs_ctx *c) { return LaunchCtx{c->stream, c->num_sms, &c->launches}; }
+LaunchCtx lctx(pbs_ctx *c) { return LaunchCtx{c->stream, c->num_sms, &c->launches, at<int>(c, c->off_err)}; }
 
 cudaEvent_t take_event(pbs_ctx *c) {
   if (!c->pool.empty()) {

@@ -44,7 +44,7 @@ struct Dims {
 };
 
 // Device status word: slot 0 counts timeouts, slot 1 records where.
-enum : int { kErrTimeoutTransport = 1 };
+enum : int { kErrTimeoutTransport = 1, kErrTimeoutSourceMma = 2 };
 
 // ----------------------------------------------------------------------------
 // PTX helpers: shared-memory addresses, mbarriers, 1-D bulk (TMA) copies.
@@ -142,6 +142,7 @@ struct LaunchCtx {
   cudaStream_t stream;
   int num_sms;
   long long *launches;  // host counter
+  int *err = nullptr;   // device status word (bounded waits record timeouts here)
 };
 
 // One E substep's per-lane inputs and outputs: density of its slab, c = h/2,

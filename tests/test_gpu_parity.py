@@ -103,11 +103,16 @@ def test_angular_substep(orc, precision, tol, nu, nv):
     s.close()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-6), ("mixed", 8e-3)])
-def test_source_contraction(orc, precision, tol):
-    grid = _grid(9, 8, 8, 8, 20)
+@pytest.mark.parametrize("precision,tol,ny,nz,nu,nv", [
+    ("fp64", 1e-12, 9, 8, 8, 8), ("fp32", 1e-6, 9, 8, 8, 8), ("mixed", 8e-3, 9, 8, 8, 8),
+    # tensor-core path: na = 256 and 128, lateral 72 points (one full and one ragged 64-point tile)
+    ("mixed", 8e-3, 9, 8, 16, 16), ("mixed", 8e-3, 8, 9, 8, 16), ("mixed", 8e-3, 20, 16, 16, 16),
+    # na = 256 with nyz % 8 != 0: the CUDA-core fallback
+    ("mixed", 8e-3, 9, 7, 16, 16)])
+def test_source_contraction(orc, precision, tol, ny, nz, nu, nv):
+    grid = _grid(ny, nz, nu, nv, 20)
     s, o, rho = _pair(orc, grid, 1, 0.05, 1, precision)
-    psi = smooth_state(9, 8, 20, 8, 8, seed=3)
+    psi = smooth_state(ny, nz, 20, nv, nu, seed=3)
     s.write_psi(0, psi)
     got = s.eval_source(0, 0)
     ref = o.source(rho[0], psi)
@@ -144,6 +149,23 @@ def test_full_march_reduced_precision(orc, precision, tol):
     assert np.abs(d - dr).max() / np.abs(dr).max() < tol
     f, fr = s.read_fluence(), ref["fluence"]
     assert np.abs(f - fr).max() / np.abs(fr).max() < tol
+    s.close()
+
+
+def test_full_march_mixed_tensor_core_source(orc):
+    """Mixed precision with the BF16 tensor-core source contraction (16x16
+    angles, K = 2) against the FP64 oracle: dose within 1e-3 of the maximum."""
+    grid = _grid(8, 8, 16, 16, 24, e_max=60.0)
+    nx, dx = 16, 0.05
+    s, o, rho = _pair(orc, grid, nx, dx, 2, "mixed", rho=np.ones((16, 8, 8)))
+    beam = dict(e0=50.0, sigma_e=1.0, sigma_y=0.3, sigma_z=0.3)
+    s.launch_beam(**beam)
+    s.step(nx)
+    ref = o.march(rho, nx, dx, beam=beam, n_scatter=2)
+    d, dr = s.read_dose(), ref["dose"]
+    assert np.abs(d - dr).max() / np.abs(dr).max() < 1e-3
+    p1, r1 = s.read_psi(1), ref["psi"][1]
+    assert np.abs(p1 - r1).max() / np.abs(r1).max() < 1e-2
     s.close()
 
 
