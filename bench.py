@@ -113,7 +113,7 @@ def _kernel_hash(name: str) -> str:
 
 
 KERNEL_FILES = {"energy": "k_energy.cu", "transport": "k_transport_rows.cu", "angular": "k_angular.cu",
-                "source": "k_misc.cu"}
+                "source": "k_source_tc.cu"}
 
 
 def _traffic_from_profiles(kind: str, workload: str):
