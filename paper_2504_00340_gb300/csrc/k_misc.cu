@@ -8,33 +8,39 @@ namespace {
 
 // psi_p(x = 0) of Eq. (bdy) as a separable product of the host-computed FP64
 // projections: fe[g][c] (DG energy), fa[a] (angle cell averages), fy[p], fz[q].
+// grid.y = g*2 + c (row), grid.x covers the row's na*nyz lanes; the product is
+// formed in the working precision.
 template <typename real>
 __global__ void k_init(real *__restrict__ psi0, const double *__restrict__ fe, const double *__restrict__ fa,
                        const double *__restrict__ fy, const double *__restrict__ fz, Dims d) {
-  const long long n = d.comp_elems;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(e % d.nz);
-    long long r = e / d.nz;
-    const int p = (int)(r % d.ny);
-    r /= d.ny;
-    const int a = (int)(r % d.na);
-    r /= d.na;  // r = g * 2 + c
-    psi0[e] = (real)(fe[r] * fa[a] * fy[p] * fz[q]);
+  const int row = blockIdx.y;
+  const int lanes = (int)d.lanes;
+  const real f = (real)fe[row];
+  real *out = psi0 + (long long)row * lanes;
+  for (int L = blockIdx.x * blockDim.x + threadIdx.x; L < lanes; L += gridDim.x * blockDim.x) {
+    const int a = L / d.nyz;
+    const int yz = L - a * d.nyz;
+    const int p = yz / d.nz;
+    const int q = yz - p * d.nz;
+    out[L] = f * (real)fa[a] * (real)fy[p] * (real)fz[q];
   }
 }
 
-// Planar fluence of the current state: flu[yz] += scale * sum_{k,g,a} dE_g psi^1.
+// Planar fluence of the current state: flu[yz] += scale * sum_{k,g,a} dE_g psi^1
+// (one thread per (yz, a); the sum over k and g in the working precision).
 template <typename real>
 __global__ void k_fluence(const real *__restrict__ psi, const GroupCoef<real> *__restrict__ coef, double *flu, Dims d,
                           double scale) {
   const int yz = blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (yz >= d.nyz) return;
-  double acc = 0.0;
-  for (int k = 0; k < d.ncomp; k++)
-    for (int g = 0; g < d.ng; g++)
-      acc += (double)coef[g].de * (double)psi[k * d.comp_elems + (long long)g * 2 * d.lanes + (long long)a * d.nyz + yz];
-  atomicAdd(flu + yz, acc * scale);
+  real acc = 0;
+  const real *p = psi + (long long)a * d.nyz + yz;
+  for (int k = 0; k < d.ncomp; k++) {
+#pragma unroll 8
+    for (int g = 0; g < d.ng; g++) acc += coef[g].de * p[k * d.comp_elems + (long long)g * 2 * d.lanes];
+  }
+  atomicAdd(flu + yz, (double)acc * scale);
 }
 
 template <typename st>
@@ -134,9 +140,10 @@ cudaError_t launch_source_input(const LaunchCtx &lc, const Dims &d, const void *
 template <typename real>
 cudaError_t launch_init(const LaunchCtx &lc, const Dims &d, real *psi0, const double *fe, const double *fa,
                         const double *fy, const double *fz) {
-  long long blocks = (d.comp_elems + 255) / 256;
-  if (blocks > (long long)lc.num_sms * 16) blocks = (long long)lc.num_sms * 16;
-  k_init<real><<<(unsigned)blocks, 256, 0, lc.stream>>>(psi0, fe, fa, fy, fz, d);
+  long long bx = (d.lanes + 255) / 256;
+  if (bx > 1024) bx = 1024;
+  dim3 grid((unsigned)bx, (unsigned)(2 * d.ng));
+  k_init<real><<<grid, 256, 0, lc.stream>>>(psi0, fe, fa, fy, fz, d);
   ++*lc.launches;
   return cudaGetLastError();
 }

@@ -62,17 +62,23 @@ __device__ __forceinline__ double flip_by(double x, double s) {
   return __longlong_as_double(__double_as_longlong(x) ^ (__double_as_longlong(s) & (long long)0x8000000000000000ULL));
 }
 
+__device__ __forceinline__ float max3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(a, fmax(b, c)); }
+
 // Upwind face value for flow from A through B to C:  B + slope / 2 with the
 // superbee slope of d1 = B - A, d2 = C - B:
-//   slope = sign(d2) max(0, min(max(x, |d2|), 2 min(x, |d2|))),  x = d1 sign(d2),
+//   slope = sign(d2) max(0, min(2x, |d2|), min(x, 2|d2|)),  x = d1 sign(d2),
 // which is 0 when d1, d2 differ in sign (x < 0) and otherwise
-// sign(d2) min(max|d|, 2 min|d|) = d2 eta(d1/d2).
+// sign(d2) max(min(2|d1|,|d2|), min(|d1|,2|d2|)) = d2 eta(d1/d2).
 template <typename real>
 __device__ __forceinline__ real face_value_d(real B, real d1, real d2) {
   const real a2 = fabs(d2);
   const real x = flip_by(d1, d2);
-  real m = fmin(fmax(x, a2), real(2) * fmin(x, a2));
-  m = fmax(m, real(0));
+  const real m = max3(real(0), fmin(x + x, a2), fmin(x, a2 + a2));
   return fma(real(0.5), copysign(m, d2), B);
 }
 
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
       pm.template iter<true, false, false, true, false, false>(0);
       pm.template iter<true, true, true, true, false, false>(1);
       pm.template iter<true, true, false, true, true, true>(2);
-#pragma unroll 2
+#pragma unroll 4
       for (int i = 3; i < ny; i++) pm.template iter<true, true, false, true, true, false>(i);
       pm.template iter<false, true, false, true, true, false>(ny);
       pm.template iter<false, true, false, false, true, false>(ny + 1);
