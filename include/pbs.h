@@ -21,7 +21,8 @@
  *     (copied in).  Host arrays passed out are written by the call.
  *   - Device memory: the caller owns the workspace it binds with
  *     pbs_bind_workspace; the library allocates no device memory itself
- *     (its coefficient tables and device status word live in the workspace).
+ *     (its coefficient tables and device status word live in the workspace;
+ *     only the CUDA graph that pbs_run records holds driver-owned memory).
  *   - Stream: all device work is issued on the stream given to pbs_create
  *     (a cudaStream_t passed as void*; NULL = the legacy default stream).
  *     pbs_launch_beam, pbs_step and the substep calls are asynchronous;
@@ -77,6 +78,11 @@ typedef struct {
   int nx;                  /* depth steps the context can hold dose for     */
   int n_scatter;           /* K: number of scattered components (0 = primary
                               only)                                         */
+  int n_beams;             /* independent pencil beams held by the context
+                              (>= 1): each has its own psi_p..psi_sK, beam
+                              projection, dose and fluence; all share the
+                              grid, physics and density field and march in
+                              lock-step, each kernel launch covering all    */
   double dy, dz;           /* lateral cell sizes (cm)                       */
   double dx;               /* depth step h (cm)                             */
   double u_max, v_max;     /* half-widths of the angle box                  */
@@ -143,8 +149,13 @@ pbs_status pbs_set_material(pbs_ctx *ctx, const double *rho, int n_slabs);
 
 /* Project the beam of Eq. (bdy) onto psi_p (cell averages in y, z, u, v;
  * DG L2 projection in E; normalised to one proton), zero psi_s1..psi_sK,
- * the dose and the fluence, and reset the depth counter to 0. */
+ * the dose and the fluence, and reset the depth counter to 0.  With
+ * n_beams > 1 every beam of the context gets this beam. */
 pbs_status pbs_launch_beam(pbs_ctx *ctx, const pbs_beam *beam);
+
+/* As pbs_launch_beam with one beam description per beam of the context
+ * (n must equal grid.n_beams). */
+pbs_status pbs_launch_beams(pbs_ctx *ctx, const pbs_beam *beams, int n);
 
 /* March n_steps depth steps (Strang order E T A T E per step, all
  * components in lock-step).  Asynchronous.  PBS_ERR_ARG if the march would
@@ -157,20 +168,58 @@ pbs_status pbs_step(pbs_ctx *ctx, int n_steps);
 /* Apply a deferred closing E(h/2), if any.  Asynchronous. */
 pbs_status pbs_flush(pbs_ctx *ctx);
 
+/* Depth range of each beam of a batch: beam b marches steps[b] depth steps
+ * (capped by the material's n_slabs) and then only receives its closing
+ * E(h/2); later launches skip it.  steps must be non-increasing in b (order
+ * the beams by range) so that the marching beams always form a prefix and
+ * every launch covers a contiguous block of components.  Default: nx for
+ * every beam.  PBS_ERR_ARG for n != n_beams, a value outside [0, nx] or an
+ * increase; PBS_ERR_STATE after the march has started (launch the beams
+ * again first). */
+pbs_status pbs_set_beam_steps(pbs_ctx *ctx, const int *steps, int n);
+
+/* The whole march of every beam: restart psi, dose and fluence from the
+ * launched beams' projections, march each beam to its depth
+ * (pbs_set_beam_steps) and apply the closing half, so that the dose and
+ * fluence are final.  use_graph != 0 records the sequence once into a CUDA
+ * graph on a stream of the context (again after a change of beam depths,
+ * material extent, launch shapes or workspace) and launches the graph on the
+ * context's stream: one launch for the whole batch.  Asynchronous.  The
+ * first graph call records; call it once before capturing the caller's own
+ * work around it. */
+pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
+
+/* Launch-shape autotuner: times the candidate shapes of the energy pass
+ * (angles per block: 4, 8, 16) and of the streaming transport (resident CTAs
+ * per SM: 1, 2, 3, 4, as many as fit) on the launched beams with CUDA events,
+ * best of reps trials each, and keeps the fastest.  The trials advance the
+ * state, so the beams restart from their projections afterwards (depth 0).
+ * Synchronises.  Results of psi do not depend on the shapes; the dose's
+ * angle reduction order does (rounding only). */
+pbs_status pbs_autotune(pbs_ctx *ctx, int reps);
+
+/* Set / read the launch shapes directly: energy_angles in {4, 8, 16},
+ * transport_ctas in [0, 64] (0 = as many as fit). */
+pbs_status pbs_set_tuning(pbs_ctx *ctx, int energy_angles, int transport_ctas);
+pbs_status pbs_get_tuning(const pbs_ctx *ctx, int *energy_angles, int *transport_ctas);
+
 /* Depth steps marched since pbs_launch_beam. */
 pbs_status pbs_get_depth(const pbs_ctx *ctx, int *steps_done);
 
-/* Dose D[s][p][q] (MeV/g per source proton, Section 4: D = E_dep / rho) for
- * the first n_slabs slabs; n must equal n_slabs*ny*nz. Synchronises. */
+/* Dose D[b][s][p][q] (MeV/g per source proton of beam b, Section 4:
+ * D = E_dep / rho) for the first n_slabs slabs of every beam; n must equal
+ * n_beams*n_slabs*ny*nz. Synchronises. */
 pbs_status pbs_read_dose(pbs_ctx *ctx, double *host_out, size_t n);
 
-/* Planar fluence F[s][p][q] = du dv sum_{k,g,a} psi^1 dE (protons/cm^2) at
- * depths s*dx, s = 0..n_planes-1 (s = 0 is the entrance); n must equal
- * n_planes*ny*nz with n_planes <= steps done + 1.  Synchronises. */
+/* Planar fluence F[b][s][p][q] = du dv sum_{k,g,a} psi^1 dE (protons/cm^2)
+ * of beam b at depths s*dx, s = 0..n_planes-1 (s = 0 is the entrance); n
+ * must equal n_beams*n_planes*ny*nz with n_planes <= steps done + 1.
+ * Synchronises. */
 pbs_status pbs_read_fluence(pbs_ctx *ctx, double *host_out, size_t n);
 
 /* Copy component k of psi to / from the host as FP64 in the logical layout
- * above (n = ng*2*nu*nv*ny*nz).  Synchronises. */
+ * above (n = ng*2*nu*nv*ny*nz); component k = b*(n_scatter+1) + j is
+ * component j of beam b.  Synchronises. */
 pbs_status pbs_read_psi(pbs_ctx *ctx, int k, double *host_out, size_t n);
 pbs_status pbs_write_psi(pbs_ctx *ctx, int k, const double *host_in, size_t n);
 

@@ -30,7 +30,7 @@ _VP = ctypes.c_void_p
 
 class PbsGrid(ctypes.Structure):
     _fields_ = [("ny", ctypes.c_int), ("nz", ctypes.c_int), ("ng", ctypes.c_int), ("nu", ctypes.c_int),
-                ("nv", ctypes.c_int), ("nx", ctypes.c_int), ("n_scatter", ctypes.c_int),
+                ("nv", ctypes.c_int), ("nx", ctypes.c_int), ("n_scatter", ctypes.c_int), ("n_beams", ctypes.c_int),
                 ("dy", ctypes.c_double), ("dz", ctypes.c_double), ("dx", ctypes.c_double),
                 ("u_max", ctypes.c_double), ("v_max", ctypes.c_double), ("e_faces", _D)]
 
@@ -60,6 +60,12 @@ SIGNATURES = [
     ("pbs_get_tables", ctypes.c_int, [_VP, _D, _D, _D, _D, _D, _D, _D]),
     ("pbs_set_material", ctypes.c_int, [_VP, _D, ctypes.c_int]),
     ("pbs_launch_beam", ctypes.c_int, [_VP, ctypes.POINTER(PbsBeam)]),
+    ("pbs_launch_beams", ctypes.c_int, [_VP, ctypes.POINTER(PbsBeam), ctypes.c_int]),
+    ("pbs_set_beam_steps", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    ("pbs_run", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("pbs_autotune", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("pbs_set_tuning", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    ("pbs_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("pbs_step", ctypes.c_int, [_VP, ctypes.c_int]),
     ("pbs_flush", ctypes.c_int, [_VP]),
     ("pbs_get_depth", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
@@ -158,6 +164,34 @@ def pbs_launch_beam(ctx, beam: PbsBeam) -> None:
     _check(ctx, load_library().pbs_launch_beam(_VP(ctx), ctypes.byref(beam)))
 
 
+def pbs_launch_beams(ctx, beams) -> None:
+    arr = (PbsBeam * len(beams))(*beams)
+    _check(ctx, load_library().pbs_launch_beams(_VP(ctx), arr, len(beams)))
+
+
+def pbs_set_beam_steps(ctx, steps) -> None:
+    arr = (ctypes.c_int * len(steps))(*[int(x) for x in steps])
+    _check(ctx, load_library().pbs_set_beam_steps(_VP(ctx), arr, len(steps)))
+
+
+def pbs_run(ctx, use_graph: bool) -> None:
+    _check(ctx, load_library().pbs_run(_VP(ctx), int(bool(use_graph))))
+
+
+def pbs_autotune(ctx, reps: int = 3) -> None:
+    _check(ctx, load_library().pbs_autotune(_VP(ctx), int(reps)))
+
+
+def pbs_set_tuning(ctx, energy_angles: int, transport_ctas: int) -> None:
+    _check(ctx, load_library().pbs_set_tuning(_VP(ctx), int(energy_angles), int(transport_ctas)))
+
+
+def pbs_get_tuning(ctx):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, load_library().pbs_get_tuning(_VP(ctx), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def pbs_step(ctx, n_steps: int) -> None:
     _check(ctx, load_library().pbs_step(_VP(ctx), int(n_steps)))
 
@@ -254,15 +288,17 @@ _BEAM_DEFAULTS = dict(e0=100.0, sigma_e=1.0, y0=0.0, z0=0.0, sigma_y=0.3, sigma_
 
 
 class Solver:
-    """One beam context on the current CUDA device.
+    """One context on the current CUDA device, holding n_beams beams on one grid.
 
     grid: dict with ny, nz, nu, nv, dy, dz, u_max, v_max, e_faces (ng+1, MeV);
     nx: number of depth steps (dose slabs); dx: step (cm); n_scatter: K;
     precision: 'fp64' | 'fp32' | 'mixed'; stream: a torch.cuda.Stream or None
-    (the current stream)."""
+    (the current stream).  With n_beams > 1, read_dose / read_fluence return
+    arrays with a leading beam axis and component k of read_psi is component
+    k % (K+1) of beam k // (K+1)."""
 
     def __init__(self, grid: dict, nx: int, dx: float, n_scatter: int = 0, precision: str = "fp32",
-                 stream=None, physics: dict | None = None):
+                 stream=None, physics: dict | None = None, n_beams: int = 1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (the library has no CPU path)")
@@ -272,8 +308,9 @@ class Solver:
         self.ng = len(self.e_faces) - 1
         self.na = self.nu * self.nv
         self.nx, self.dx, self.K = int(nx), float(dx), int(n_scatter)
+        self.n_beams = int(n_beams)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self._g = PbsGrid(self.ny, self.nz, self.ng, self.nu, self.nv, self.nx, self.K, float(grid["dy"]),
+        self._g = PbsGrid(self.ny, self.nz, self.ng, self.nu, self.nv, self.nx, self.K, self.n_beams, float(grid["dy"]),
                           float(grid["dz"]), self.dx, float(grid["u_max"]), float(grid["v_max"]),
                           _ptr(self.e_faces))
         self._precision = PRECISIONS[precision]
@@ -315,10 +352,36 @@ class Solver:
         rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64)).reshape(-1, self.ny, self.nz)
         pbs_set_material(self.ctx, rho, rho.shape[0])
 
-    def launch_beam(self, **beam):
+    @staticmethod
+    def _beam(beam: dict) -> PbsBeam:
         b = dict(_BEAM_DEFAULTS)
         b.update({k: float(v) for k, v in beam.items() if k in b})
-        pbs_launch_beam(self.ctx, PbsBeam(**b))
+        return PbsBeam(**b)
+
+    def launch_beam(self, **beam):
+        pbs_launch_beam(self.ctx, self._beam(beam))
+
+    def launch_beams(self, beams):
+        """One beam dict per beam of the context."""
+        pbs_launch_beams(self.ctx, [self._beam(b) for b in beams])
+
+    def set_beam_steps(self, steps):
+        pbs_set_beam_steps(self.ctx, steps)
+
+    def run(self, use_graph: bool = True):
+        """The whole march of every beam to its depth (restarting from the
+        launched projections), optionally as one CUDA graph launch."""
+        pbs_run(self.ctx, use_graph)
+
+    def autotune(self, reps: int = 3):
+        pbs_autotune(self.ctx, reps)
+
+    @property
+    def tuning(self):
+        return pbs_get_tuning(self.ctx)
+
+    def set_tuning(self, energy_angles: int, transport_ctas: int):
+        pbs_set_tuning(self.ctx, energy_angles, transport_ctas)
 
     def step(self, n: int):
         pbs_step(self.ctx, n)
@@ -332,15 +395,15 @@ class Solver:
 
     def read_dose(self, n_slabs: int | None = None):
         n = self.nx if n_slabs is None else n_slabs
-        out = np.zeros((n, self.ny, self.nz))
+        out = np.zeros((self.n_beams, n, self.ny, self.nz))
         pbs_read_dose(self.ctx, out)
-        return out
+        return out[0] if self.n_beams == 1 else out
 
     def read_fluence(self, n_planes: int | None = None):
         n = self.depth + 1 if n_planes is None else n_planes
-        out = np.zeros((n, self.ny, self.nz))
+        out = np.zeros((self.n_beams, n, self.ny, self.nz))
         pbs_read_fluence(self.ctx, out)
-        return out
+        return out[0] if self.n_beams == 1 else out
 
     def read_psi(self, k: int = 0):
         out = np.zeros(self.comp_shape)

@@ -77,13 +77,13 @@ __device__ __forceinline__ float mode_factor(float den) { return __fdividef(2.0f
 template <typename real, int NU, int NV>
 __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
     k_angular(real *__restrict__ psi, const real *__restrict__ rho_yz, const real *__restrict__ ts, int nyz,
-              int ng, real hq, const __grid_constant__ AngTables<real> tb) {
+              int ng, real hq, long long kgc0, const __grid_constant__ AngTables<real> tb) {
   constexpr int NA = NU * NV;
   constexpr int kTW = tile_w<real>();
   __shared__ real tile[NA][kTW];
   const int x = threadIdx.x;
   const int t = threadIdx.y;
-  const long long kgc = blockIdx.y;  // (k * ng + g) * 2 + c
+  const long long kgc = kgc0 + blockIdx.y;  // (k * ng + g) * 2 + c
   const int g = (int)((kgc / 2) % ng);
   const int yz0 = blockIdx.x * kTW;
   const int yz = yz0 + x;
@@ -151,10 +151,17 @@ cudaError_t go(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz
   constexpr int NT = NU > NV ? NU : NV;
   constexpr int kTW = tile_w<real>();
   dim3 block(kTW, NT);
-  dim3 grid((d.nyz + kTW - 1) / kTW, (unsigned)((long long)d.ncomp * d.ng * 2));
-  k_angular<real, NU, NV><<<grid, block, 0, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng, (real)(0.25 * h), tb);
-  ++*lc.launches;
-  return cudaGetLastError();
+  // grid.y is limited to 65535 slab stacks per launch: larger batches go in chunks
+  const long long total = (long long)d.ncomp * d.ng * 2;
+  for (long long k0 = 0; k0 < total; k0 += 65535) {
+    const long long cnt = total - k0 < 65535 ? total - k0 : 65535;
+    dim3 grid((d.nyz + kTW - 1) / kTW, (unsigned)cnt);
+    k_angular<real, NU, NV><<<grid, block, 0, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng, (real)(0.25 * h), k0, tb);
+    ++*lc.launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace

@@ -27,6 +27,8 @@
 // group by group and psi makes one trip through HBM instead of two.
 #include "pbs_internal.cuh"
 
+#include <type_traits>
+
 namespace pbs {
 
 namespace {
@@ -57,8 +59,9 @@ __device__ __forceinline__ void comp_add(real &s, real &c, real x) {
 }
 
 constexpr int kLanesX = 32;   // lateral points per block (coalesced)
-constexpr int kAnglesY = 8;   // angles per block (reduced for the dose)
 constexpr int kUnroll = 4;    // groups per prefetch block
+// Angles per block (reduced in shared memory for the dose): a tile-shape
+// knob of the autotuner, 4, 8 (default) or 16.
 
 // Per-lane state of one CN scan.
 template <typename real>
@@ -99,13 +102,29 @@ struct Scan {
   }
 };
 
-template <typename real, typename st, bool HAS_SRC, bool HAS_R, bool TWO>
+template <typename real, typename st, bool HAS_SRC, bool HAS_R, bool TWO, int kAnglesY>
 __global__ void __launch_bounds__(kLanesX *kAnglesY)
     k_energy(Dims d, real *__restrict__ psi, const st *__restrict__ src_a, const st *__restrict__ src_b,
              st *__restrict__ r_a, st *__restrict__ r_b, const real *__restrict__ rho_a,
              const real *__restrict__ rho_b, const GroupCoef<real> *__restrict__ coef, double *__restrict__ dose_a,
              double *__restrict__ dose_b, double *__restrict__ flu, real c_a, real c_b, double dose_scale,
-             double flu_scale) {
+             double flu_scale, BeamStrides bs) {
+  // beam blockIdx.z: shift every per-beam pointer to its copy
+  {
+    const long long b = blockIdx.z;
+    psi += b * bs.psi;
+    if (HAS_SRC) {
+      src_a += b * bs.src;
+      if (TWO) src_b += b * bs.src;
+    }
+    if (HAS_R) {
+      r_a += b * bs.src;
+      if (TWO) r_b += b * bs.src;
+    }
+    if (dose_a) dose_a += b * bs.dose;
+    if (TWO && dose_b) dose_b += b * bs.dose;
+    if (flu) flu += b * bs.flu;
+  }
   extern __shared__ unsigned char smem_raw[];
   GroupCoef<real> *tab = reinterpret_cast<GroupCoef<real> *>(smem_raw);
   const int tid = threadIdx.y * kLanesX + threadIdx.x;
@@ -220,9 +239,10 @@ __global__ void __launch_bounds__(kLanesX *kAnglesY)
 template <typename real, typename st>
 cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
                           const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
-                          double dose_scale, double flu_scale) {
-  dim3 block(kLanesX, kAnglesY);
-  dim3 grid((d.nyz + kLanesX - 1) / kLanesX, (d.na + kAnglesY - 1) / kAnglesY);
+                          double dose_scale, double flu_scale, const BeamStrides &bs) {
+  const int ay = lc.energy_angles;
+  dim3 block(kLanesX, ay);
+  dim3 grid((d.nyz + kLanesX - 1) / kLanesX, (d.na + ay - 1) / ay, d.nbeam);
   const size_t smem = sizeof(GroupCoef<real>) * d.ng;
   const bool has_src = ha.src != nullptr, has_r = ha.r_out != nullptr;
   const EnergyHalf<real, st> &b = hb ? *hb : ha;
@@ -232,28 +252,36 @@ cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const
       if (e != cudaSuccess) return e;
     }
     kern<<<grid, block, smem, lc.stream>>>(d, psi_k, ha.src, b.src, ha.r_out, b.r_out, ha.rho, b.rho, coef, ha.dose,
-                                           b.dose, flu_yz, ha.c, b.c, dose_scale, flu_scale);
+                                           b.dose, flu_yz, ha.c, b.c, dose_scale, flu_scale, bs);
     ++*lc.launches;
     return cudaGetLastError();
   };
+  auto pick = [&](auto ay_tag) -> cudaError_t {
+    constexpr int AY = decltype(ay_tag)::value;
 #define PBS_E(S, R, T) \
-  if (has_src == S && has_r == R && (hb != nullptr) == T) return go(k_energy<real, st, S, R, T>);
-  PBS_E(true, true, true) PBS_E(true, false, true) PBS_E(false, true, true) PBS_E(false, false, true)
-  PBS_E(true, true, false) PBS_E(true, false, false) PBS_E(false, true, false) PBS_E(false, false, false)
+  if (has_src == S && has_r == R && (hb != nullptr) == T) return go(k_energy<real, st, S, R, T, AY>);
+    PBS_E(true, true, true) PBS_E(true, false, true) PBS_E(false, true, true) PBS_E(false, false, true)
+    PBS_E(true, true, false) PBS_E(true, false, false) PBS_E(false, true, false) PBS_E(false, false, false)
 #undef PBS_E
-  return cudaErrorInvalidValue;
+    return cudaErrorInvalidValue;
+  };
+  if (ay == 4) return pick(std::integral_constant<int, 4>{});
+  if (ay == 8) return pick(std::integral_constant<int, 8>{});
+  if (ay == 16) return pick(std::integral_constant<int, 16>{});
+  return cudaErrorInvalidConfiguration;
 }
 
 template cudaError_t launch_energy<double, double>(const LaunchCtx &, const Dims &, double *,
                                                    const EnergyHalf<double, double> &,
                                                    const EnergyHalf<double, double> *, const GroupCoef<double> *,
-                                                   double *, double, double);
+                                                   double *, double, double, const BeamStrides &);
 template cudaError_t launch_energy<float, float>(const LaunchCtx &, const Dims &, float *,
                                                  const EnergyHalf<float, float> &, const EnergyHalf<float, float> *,
-                                                 const GroupCoef<float> *, double *, double, double);
+                                                 const GroupCoef<float> *, double *, double, double, const BeamStrides &);
 template cudaError_t launch_energy<float, __nv_bfloat16>(const LaunchCtx &, const Dims &, float *,
                                                          const EnergyHalf<float, __nv_bfloat16> &,
                                                          const EnergyHalf<float, __nv_bfloat16> *,
-                                                         const GroupCoef<float> *, double *, double, double);
+                                                         const GroupCoef<float> *, double *, double, double,
+                                                         const BeamStrides &);
 
 }  // namespace pbs

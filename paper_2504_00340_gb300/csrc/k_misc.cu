@@ -29,14 +29,14 @@ __global__ void k_init(real *__restrict__ psi0, const double *__restrict__ fe, c
 // Planar fluence of the current state: flu[yz] += scale * sum_{k,g,a} dE_g psi^1
 // (one thread per (yz, a); the sum over k and g in the working precision).
 template <typename real>
-__global__ void k_fluence(const real *__restrict__ psi, const GroupCoef<real> *__restrict__ coef, double *flu, Dims d,
-                          double scale) {
+__global__ void k_fluence(const real *__restrict__ psi, int ncomp_beam, const GroupCoef<real> *__restrict__ coef,
+                          double *flu, Dims d, double scale) {
   const int yz = blockIdx.x * blockDim.x + threadIdx.x;
   const int a = blockIdx.y;
   if (yz >= d.nyz) return;
   real acc = 0;
   const real *p = psi + (long long)a * d.nyz + yz;
-  for (int k = 0; k < d.ncomp; k++) {
+  for (int k = 0; k < ncomp_beam; k++) {
 #pragma unroll 8
     for (int g = 0; g < d.ng; g++) acc += coef[g].de * p[k * d.comp_elems + (long long)g * 2 * d.lanes];
   }
@@ -56,15 +56,16 @@ __device__ __forceinline__ void stf<__nv_bfloat16, float>(__nv_bfloat16 *p, floa
 // 4x4 outputs per thread; acc is the accumulation type.
 template <typename st, typename acc_t>
 __global__ void __launch_bounds__(256) k_source_cc(const st *__restrict__ p2, const st *__restrict__ r, st *__restrict__ src,
-                                                    int na, int nyz, acc_t dudv) {
+                                                    int na, int nyz, int ng, long long gb0, acc_t dudv) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ acc_t As[BK][BM + 1];
   __shared__ acc_t Bs[BK][BN];
-  const int g = blockIdx.z;
+  const long long gb = gb0 + blockIdx.z;  // beam * ng + g
+  const int g = (int)(gb % ng);
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const st *A = p2 + (long long)g * na * na;
-  const st *B = r + (long long)g * na * nyz;
-  st *C = src + (long long)g * na * nyz;
+  const st *B = r + (long long)gb * na * nyz;
+  st *C = src + (long long)gb * na * nyz;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   acc_t acc[4][4] = {};
   for (int k0 = 0; k0 < na; k0 += BK) {
@@ -149,36 +150,48 @@ cudaError_t launch_init(const LaunchCtx &lc, const Dims &d, real *psi0, const do
 }
 
 template <typename real>
-cudaError_t launch_fluence(const LaunchCtx &lc, const Dims &d, const real *psi, const GroupCoef<real> *coef,
-                           double *flu_yz, double scale) {
+cudaError_t launch_fluence(const LaunchCtx &lc, const Dims &d, const real *psi, int ncomp_beam,
+                           const GroupCoef<real> *coef, double *flu_yz, double scale) {
   dim3 grid((d.nyz + 127) / 128, d.na);
-  k_fluence<real><<<grid, 128, 0, lc.stream>>>(psi, coef, flu_yz, d, scale);
+  k_fluence<real><<<grid, 128, 0, lc.stream>>>(psi, ncomp_beam, coef, flu_yz, d, scale);
   ++*lc.launches;
   return cudaGetLastError();
+}
+
+// grid.z is limited to 65535 (beam, group) blocks per launch: larger batches
+// go in chunks.
+template <typename st, typename acc_t>
+cudaError_t launch_source_cc(const LaunchCtx &lc, const Dims &d, const st *p2, const st *r, st *src, acc_t dudv,
+                             int nbatch) {
+  const long long total = (long long)d.ng * nbatch;
+  for (long long z0 = 0; z0 < total; z0 += 65535) {
+    const long long cnt = total - z0 < 65535 ? total - z0 : 65535;
+    dim3 grid((d.nyz + 63) / 64, (d.na + 63) / 64, (unsigned)cnt);
+    k_source_cc<st, acc_t><<<grid, 256, 0, lc.stream>>>(p2, r, src, d.na, d.nyz, d.ng, z0, dudv);
+    ++*lc.launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // BF16 operands, FP32 accumulation on the CUDA cores (reference form of the
 // tensor-core contraction).
 cudaError_t launch_source_bf16_cc(const LaunchCtx &lc, const Dims &d, const __nv_bfloat16 *p2, const __nv_bfloat16 *r,
-                                  __nv_bfloat16 *src, double dudv) {
-  dim3 grid((d.nyz + 63) / 64, (d.na + 63) / 64, d.ng);
-  k_source_cc<__nv_bfloat16, float><<<grid, 256, 0, lc.stream>>>(p2, r, src, d.na, d.nyz, (float)dudv);
-  ++*lc.launches;
-  return cudaGetLastError();
+                                  __nv_bfloat16 *src, double dudv, int nbatch) {
+  return launch_source_cc<__nv_bfloat16, float>(lc, d, p2, r, src, (float)dudv, nbatch);
 }
 
 cudaError_t launch_source_tc(const LaunchCtx &lc, const Dims &d, const __nv_bfloat16 *p2, const __nv_bfloat16 *r,
-                             __nv_bfloat16 *src, double dudv);
+                             __nv_bfloat16 *src, double dudv, int nbatch);
 
 template <typename real, typename st>
-cudaError_t launch_source(const LaunchCtx &lc, const Dims &d, const st *p2, const st *r, st *src, double dudv) {
+cudaError_t launch_source(const LaunchCtx &lc, const Dims &d, const st *p2, const st *r, st *src, double dudv,
+                          int nbatch) {
   if constexpr (sizeof(st) == 2) {
-    return launch_source_tc(lc, d, p2, r, src, dudv);
+    return launch_source_tc(lc, d, p2, r, src, dudv, nbatch);
   } else {
-    dim3 grid((d.nyz + 63) / 64, (d.na + 63) / 64, d.ng);
-    k_source_cc<st, st><<<grid, 256, 0, lc.stream>>>(p2, r, src, d.na, d.nyz, (st)dudv);
-    ++*lc.launches;
-    return cudaGetLastError();
+    return launch_source_cc<st, st>(lc, d, p2, r, src, (st)dudv, nbatch);
   }
 }
 
@@ -186,15 +199,15 @@ template cudaError_t launch_init<double>(const LaunchCtx &, const Dims &, double
                                          const double *, const double *);
 template cudaError_t launch_init<float>(const LaunchCtx &, const Dims &, float *, const double *, const double *,
                                         const double *, const double *);
-template cudaError_t launch_fluence<double>(const LaunchCtx &, const Dims &, const double *, const GroupCoef<double> *,
-                                            double *, double);
-template cudaError_t launch_fluence<float>(const LaunchCtx &, const Dims &, const float *, const GroupCoef<float> *,
-                                           double *, double);
+template cudaError_t launch_fluence<double>(const LaunchCtx &, const Dims &, const double *, int,
+                                            const GroupCoef<double> *, double *, double);
+template cudaError_t launch_fluence<float>(const LaunchCtx &, const Dims &, const float *, int,
+                                           const GroupCoef<float> *, double *, double);
 template cudaError_t launch_source<double, double>(const LaunchCtx &, const Dims &, const double *, const double *,
-                                                   double *, double);
+                                                   double *, double, int);
 template cudaError_t launch_source<float, float>(const LaunchCtx &, const Dims &, const float *, const float *, float *,
-                                                 double);
+                                                 double, int);
 template cudaError_t launch_source<float, __nv_bfloat16>(const LaunchCtx &, const Dims &, const __nv_bfloat16 *,
-                                                         const __nv_bfloat16 *, __nv_bfloat16 *, double);
+                                                         const __nv_bfloat16 *, __nv_bfloat16 *, double, int);
 
 }  // namespace pbs

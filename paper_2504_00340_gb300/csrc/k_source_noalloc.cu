@@ -99,6 +99,7 @@ extern "C" pbs_status pbs_eval_source_noalloc(const float *psi_k, const float *r
   if (cudaGetLastError() != cudaSuccess) return PBS_ERR_CUDA;
   Dims d;
   d.ny = ny; d.nz = nz; d.ng = ng; d.nu = nu; d.nv = nv; d.na = (int)na; d.nyz = (int)nyz; d.ncomp = 1;
+  d.nbeam = 1;
   d.lanes = lanes;
   d.comp_elems = (long long)ng * 2 * lanes;
   int sms = 0;

@@ -24,7 +24,7 @@
 namespace pbs {
 
 cudaError_t launch_source_bf16_cc(const LaunchCtx &lc, const Dims &d, const __nv_bfloat16 *p2,
-                                  const __nv_bfloat16 *r, __nv_bfloat16 *src, double dudv);
+                                  const __nv_bfloat16 *r, __nv_bfloat16 *src, double dudv, int nbatch);
 
 namespace {
 
@@ -95,7 +95,7 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__restrict__ p2,
                                                          const __nv_bfloat16 *__restrict__ r,
                                                          __nv_bfloat16 *__restrict__ src, int na, int nyz, int ng,
-                                                         float dudv, int *__restrict__ err) {
+                                                         int ngb, float dudv, int *__restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // [A tile: (kTM/8) * (na/8) * 128 B][B tile: (kTN/8) * (na/8) * 128 B]
   const int kcm = na / 8;  // core matrices along K
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
 
   const int mtiles = na / kTM;
   const int ntiles = (nyz + kTN - 1) / kTN;
-  const long long ntot = (long long)ng * mtiles * ntiles;
+  const long long ntot = (long long)ngb * mtiles * ntiles;  // ngb = beams * ng (R, src blocks)
   const long long per = (ntot + gridDim.x - 1) / gridDim.x;
   const long long t_beg = blockIdx.x * per;
   const long long t_end = min(ntot, t_beg + per);
@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
     const int nt = (int)(t % ntiles);
     const long long gm = t / ntiles;  // g * mtiles + mt
     const int mt = (int)(gm % mtiles);
-    const int g = (int)(gm / mtiles);
+    const int gb = (int)(gm / mtiles);  // beam * ng + g
+    const int g = gb % ng;
     const int n0 = nt * kTN;
     // ---- stage operands (cp.async, 16-byte chunks)
     if (gm != cur_a) {
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
       cur_a = gm;
     }
     {
-      const __nv_bfloat16 *Bg = r + (long long)g * na * nyz;
+      const __nv_bfloat16 *Bg = r + (long long)gb * na * nyz;
       // chunk (k, n8): row k of R_g, 8 consecutive lateral points
       for (int c = tid; c < na * (kTN / 8); c += kThreads) {
         const int k = c / (kTN / 8), nc = c % (kTN / 8);
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
     // ---- epilogue: warp w owns TMEM lanes (rows) 32w..32w+31
     {
       const int m = warp * 32 + lane;
-      __nv_bfloat16 *out = src + ((long long)g * na + (long long)mt * kTM + m) * nyz + n0;
+      __nv_bfloat16 *out = src + ((long long)gb * na + (long long)mt * kTM + m) * nyz + n0;
 #pragma unroll
       for (int half = 0; half < kTN / 32; half++) {
         float v[32];
@@ -239,8 +240,8 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
 bool source_tc_supported(int na, int nyz) { return na % kTM == 0 && na <= 256 && nyz % 8 == 0; }
 
 cudaError_t launch_source_tc(const LaunchCtx &lc, const Dims &d, const __nv_bfloat16 *p2, const __nv_bfloat16 *r,
-                             __nv_bfloat16 *src, double dudv) {
-  if (!source_tc_supported(d.na, d.nyz)) return launch_source_bf16_cc(lc, d, p2, r, src, dudv);
+                             __nv_bfloat16 *src, double dudv, int nbatch) {
+  if (!source_tc_supported(d.na, d.nyz)) return launch_source_bf16_cc(lc, d, p2, r, src, dudv, nbatch);
   const size_t smem = (size_t)(kTM / 8 + kTN / 8) * (d.na / 8) * 128;
   cudaError_t e = cudaFuncSetAttribute(k_source_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -249,11 +250,11 @@ cudaError_t launch_source_tc(const LaunchCtx &lc, const Dims &d, const __nv_bflo
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   if (per_sm > 2) per_sm = 2;  // TMEM: 2 x 128 columns per SM
-  const long long ntot = (long long)d.ng * (d.na / kTM) * ((d.nyz + kTN - 1) / kTN);
+  const long long ntot = (long long)d.ng * nbatch * (d.na / kTM) * ((d.nyz + kTN - 1) / kTN);
   long long blocks = (long long)per_sm * lc.num_sms;
   if (blocks > ntot) blocks = ntot;
-  k_source_tc<<<(unsigned)blocks, kThreads, smem, lc.stream>>>(p2, r, src, d.na, d.nyz, d.ng, (float)dudv,
-                                                               lc.err);
+  k_source_tc<<<(unsigned)blocks, kThreads, smem, lc.stream>>>(p2, r, src, d.na, d.nyz, d.ng, d.ng * nbatch,
+                                                               (float)dudv, lc.err);
   ++*lc.launches;
   return cudaGetLastError();
 }

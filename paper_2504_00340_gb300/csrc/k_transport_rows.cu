@@ -345,6 +345,7 @@ cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi,
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  if (lc.transport_ctas > 0 && lc.transport_ctas < per_sm) per_sm = lc.transport_ctas;
   const long long groups_per_block = (long long)kWarps * (32 / gw);
   long long blocks = (long long)per_sm * lc.num_sms;
   const long long need = (nplanes + groups_per_block - 1) / groups_per_block;

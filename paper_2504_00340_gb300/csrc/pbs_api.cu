@@ -9,9 +9,18 @@
 // k-1 (Section 3.1, Eq. pri-se; Remark 1) evaluated at the start and end of
 // the same substep (trapezoid), which the energy kernel of k-1 emits fused as
 // R and the contraction kernel turns into src = du dv P^2_g R.
+//
+// A context may hold n_beams independent beams (a batch of spots on one
+// grid).  Beam b owns components b*(K+1) .. b*(K+1)+K, its own R/src slots,
+// dose and fluence; every kernel launch covers all beams still inside their
+// depth range.  Beams are ordered by non-increasing depth (pbs_set_beam_steps)
+// so the active ones at any depth form a prefix and the launches shrink as
+// beams stop.
 #include "pbs_internal.cuh"
 #include "pbs.h"
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,6 +35,8 @@ struct pbs_ctx {
   cudaStream_t stream = nullptr;
   int precision = PBS_FP32;
   int ny, nz, ng, nu, nv, na, nx, K;
+  int B = 1;                       // beams held by the context
+  std::vector<int> beam_steps;     // depth steps of each beam (non-increasing)
   double dy, dz, dx, u_max, v_max, du, dv;
   std::vector<double> e_faces, e_c, de;
   Dims d;
@@ -41,6 +52,14 @@ struct pbs_ctx {
   size_t off_psi, off_r, off_s, off_rho, off_dose, off_flu, off_coef, off_ts, off_p2, off_init, off_err, total;
   size_t rsize, ssize;  // element sizes of real and of the source storage
   long long launches = 0;
+  // launch shapes (pbs_autotune / pbs_set_tuning)
+  int tune_energy_angles = 8, tune_transport_ctas = 0;
+  // whole-march CUDA graph (pbs_run with use_graph)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_depth = -1;
+  long long graph_kernels = 0;
+  bool capturing = false;
   std::string err;
   // per-kernel timing (pbs_set_profiling): event pairs recorded on the stream
   struct Rec { int kind; cudaEvent_t a, b; };
@@ -52,6 +71,8 @@ struct pbs_ctx {
   ~pbs_ctx() {
     for (auto &r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : pool) cudaEventDestroy(e);
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 };
 
@@ -74,21 +95,24 @@ pbs_status cuda_fail(pbs_ctx *c, cudaError_t e, const char *where) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+size_t init_stride(const pbs_ctx *c) { return (size_t)(2 * c->ng + c->na + c->ny + c->nz); }
+
 void layout(pbs_ctx *c) {
-  const size_t S = c->rsize, SS = c->ssize;
+  const size_t S = c->rsize, SS = c->ssize, B = (size_t)c->B;
   const size_t nyz = (size_t)c->ny * c->nz;
   size_t o = 0;
   c->off_psi = o; o = align256(o + (size_t)c->d.ncomp * c->d.comp_elems * S);
   const size_t nsrc = (c->K > 0) ? (size_t)c->ng * c->na * nyz : 0;
-  c->off_r = o; o = align256(o + 2 * nsrc * SS);  // R for the first and second substep of a fused pair
-  c->off_s = o; o = align256(o + 2 * nsrc * SS);
+  // R and src: [half][beam][g][a][yz]; half 0/1 = first/second substep of a fused pair
+  c->off_r = o; o = align256(o + 2 * B * nsrc * SS);
+  c->off_s = o; o = align256(o + 2 * B * nsrc * SS);
   c->off_rho = o; o = align256(o + (size_t)c->nx * nyz * S);
-  c->off_dose = o; o = align256(o + (size_t)c->nx * nyz * 8);
-  c->off_flu = o; o = align256(o + (size_t)(c->nx + 1) * nyz * 8);
+  c->off_dose = o; o = align256(o + B * c->nx * nyz * 8);       // [beam][slab][yz]
+  c->off_flu = o; o = align256(o + B * (c->nx + 1) * nyz * 8);  // [beam][plane][yz]
   c->off_coef = o; o = align256(o + (size_t)c->ng * 10 * S);
   c->off_ts = o; o = align256(o + (size_t)c->ng * S);
   c->off_p2 = o; o = align256(o + ((c->K > 0) ? (size_t)c->ng * c->na * c->na * SS : 0));
-  c->off_init = o; o = align256(o + (size_t)(2 * c->ng + c->na + c->ny + c->nz) * 8);
+  c->off_init = o; o = align256(o + B * init_stride(c) * 8);  // beam projection factors per beam
   c->off_err = o; o = align256(o + 64);
   c->total = o;
 }
@@ -96,7 +120,38 @@ void layout(pbs_ctx *c) {
 template <typename T>
 T *at(pbs_ctx *c, size_t off) { return reinterpret_cast<T *>(c->ws + off); }
 
-LaunchCtx lctx(pbs_ctx *c) { return LaunchCtx{c->stream, c->num_sms, &c->launches, at<int>(c, c->off_err)}; }
+LaunchCtx lctx(pbs_ctx *c) {
+  LaunchCtx lc{c->stream, c->num_sms, &c->launches, at<int>(c, c->off_err)};
+  lc.energy_angles = c->tune_energy_angles;
+  lc.transport_ctas = c->tune_transport_ctas;
+  return lc;
+}
+
+// Dims of the first nb beams (the active prefix).
+Dims dims_for(const pbs_ctx *c, int nb) {
+  Dims d = c->d;
+  d.nbeam = nb;
+  d.ncomp = nb * (c->K + 1);
+  return d;
+}
+
+// Depth steps of beam b, capped by the material's extent.
+int beam_depth(const pbs_ctx *c, int b) { return std::min(c->beam_steps[b], c->n_slabs); }
+
+// Beams still marching at depth step s: a prefix, since depths are non-increasing.
+int active_at(const pbs_ctx *c, int s) {
+  int n = 0;
+  while (n < c->B && beam_depth(c, n) > s) n++;
+  return n;
+}
+
+int max_depth(const pbs_ctx *c) { return c->B > 0 ? beam_depth(c, 0) : 0; }
+
+void drop_graph(pbs_ctx *c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_depth = -1;
+}
 
 cudaEvent_t take_event(pbs_ctx *c) {
   if (!c->pool.empty()) {
@@ -115,7 +170,7 @@ struct ProfScope {
   int kind;
   cudaEvent_t a = nullptr;
   ProfScope(pbs_ctx *c_, int k) : c(c_), kind(k) {
-    if (c->profiling) {
+    if (c->profiling && !c->capturing) {
       a = take_event(c);
       cudaEventRecord(a, c->stream);
     }
@@ -300,40 +355,45 @@ void beam_factors(const pbs_ctx *c, const pbs_beam &b, std::vector<double> &out)
 
 // ---------------------------------------------------------------- march
 
-// E substeps on all components in lock-step.  slab_b < 0: one substep E(h)
-// with slab_a.  slab_b >= 0: two back-to-back substeps E(h) (slab_a, then
-// slab_b) fused in one pass per component.  Fluence after the first substep
-// goes to plane flu_plane (if >= 0).
+// E substeps on the components of beams b0 .. b1-1 in lock-step.  slab_b < 0:
+// one substep E(h) with slab_a.  slab_b >= 0: two back-to-back substeps E(h)
+// (slab_a, then slab_b) fused in one pass per component.  Fluence after the
+// first substep goes to plane flu_plane (if >= 0).
 template <typename real, typename st>
-pbs_status energy_run(pbs_ctx *c, double h, int slab_a, int slab_b, int flu_plane) {
+pbs_status energy_run(pbs_ctx *c, double h, int slab_a, int slab_b, int flu_plane, int b0, int b1) {
+  if (b1 <= b0) return PBS_OK;
   LaunchCtx lc = lctx(c);
+  const Dims d = dims_for(c, b1 - b0);
   const size_t nyz = (size_t)c->ny * c->nz;
   const size_t nsrc = (size_t)c->ng * c->na * nyz;
-  real *psi = at<real>(c, c->off_psi);
+  const size_t half_stride = (size_t)c->B * nsrc;  // second half of a fused pair
+  const BeamStrides bs{(long long)(c->K + 1) * c->d.comp_elems, (long long)nsrc, (long long)c->nx * (long long)nyz,
+                       (long long)(c->nx + 1) * (long long)nyz};
+  real *psi = at<real>(c, c->off_psi) + (size_t)b0 * bs.psi;
   const real *rho = at<real>(c, c->off_rho);
-  double *dose = at<double>(c, c->off_dose);
-  double *flu = flu_plane >= 0 ? at<double>(c, c->off_flu) + (size_t)flu_plane * nyz : nullptr;
-  st *rbuf = at<st>(c, c->off_r), *sbuf = at<st>(c, c->off_s);
+  double *dose = at<double>(c, c->off_dose) + (size_t)b0 * bs.dose;
+  double *flu = flu_plane >= 0 ? at<double>(c, c->off_flu) + (size_t)b0 * bs.flu + (size_t)flu_plane * nyz : nullptr;
+  st *rbuf = at<st>(c, c->off_r) + (size_t)b0 * nsrc, *sbuf = at<st>(c, c->off_s) + (size_t)b0 * nsrc;
   const auto *coef = at<GroupCoef<real>>(c, c->off_coef);
   const bool two = slab_b >= 0;
   for (int k = 0; k <= c->K; k++) {
     EnergyHalf<real, st> ha{rho + (size_t)slab_a * nyz, (real)(0.5 * h), k >= 1 ? sbuf : nullptr,
                             k < c->K ? rbuf : nullptr, dose + (size_t)slab_a * nyz};
     EnergyHalf<real, st> hb{two ? rho + (size_t)slab_b * nyz : nullptr, (real)(0.5 * h),
-                            k >= 1 ? sbuf + nsrc : nullptr, k < c->K ? rbuf + nsrc : nullptr,
+                            k >= 1 ? sbuf + half_stride : nullptr, k < c->K ? rbuf + half_stride : nullptr,
                             two ? dose + (size_t)slab_b * nyz : nullptr};
     cudaError_t e;
     {
       ProfScope ps(c, PBS_KERNEL_ENERGY);
-      e = launch_energy<real, st>(lc, c->d, psi + (size_t)k * c->d.comp_elems, ha, two ? &hb : nullptr, coef, flu,
-                                  c->du * c->dv / c->dx, c->du * c->dv);
+      e = launch_energy<real, st>(lc, d, psi + (size_t)k * c->d.comp_elems, ha, two ? &hb : nullptr, coef, flu,
+                                  c->du * c->dv / c->dx, c->du * c->dv, bs);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "energy kernel");
     if (k < c->K) {
       for (int half = 0; half < (two ? 2 : 1); half++) {
         ProfScope ps(c, PBS_KERNEL_SOURCE);
-        e = launch_source<real, st>(lc, c->d, at<st>(c, c->off_p2), rbuf + half * nsrc, sbuf + half * nsrc,
-                                    c->du * c->dv);
+        e = launch_source<real, st>(lc, d, at<st>(c, c->off_p2), rbuf + half * half_stride,
+                                    sbuf + half * half_stride, c->du * c->dv, b1 - b0);
         if (e != cudaSuccess) return cuda_fail(c, e, "source kernel");
       }
     }
@@ -343,81 +403,176 @@ pbs_status energy_run(pbs_ctx *c, double h, int slab_a, int slab_b, int flu_plan
 
 template <typename real, typename st>
 pbs_status energy_all(pbs_ctx *c, double h, int slab, int flu_plane) {
-  return energy_run<real, st>(c, h, slab, -1, flu_plane);
+  return energy_run<real, st>(c, h, slab, -1, flu_plane, 0, c->B);
 }
 
+// T(h) on the components of the first nb beams.
 template <typename real>
-pbs_status transport_all(pbs_ctx *c, double h) {
+pbs_status transport_run(pbs_ctx *c, double h, int nb) {
+  if (nb <= 0) return PBS_OK;
+  const Dims d = dims_for(c, nb);
   ProfScope ps(c, PBS_KERNEL_TRANSPORT);
   cudaError_t e =
       transport_rows_supported(c->nz)
-          ? launch_transport_rows<real>(lctx(c), c->d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz)
-          : launch_transport<real>(lctx(c), c->d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz,
+          ? launch_transport_rows<real>(lctx(c), d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz)
+          : launch_transport<real>(lctx(c), d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz,
                                    at<int>(c, c->off_err));
   return e == cudaSuccess ? PBS_OK : cuda_fail(c, e, "transport kernel");
 }
 
 template <typename real>
-pbs_status angular_all(pbs_ctx *c, double h, int slab) {
+pbs_status transport_all(pbs_ctx *c, double h) {
+  return transport_run<real>(c, h, c->B);
+}
+
+// A(h) on the components of the first nb beams.
+template <typename real>
+pbs_status angular_run(pbs_ctx *c, double h, int slab, int nb) {
+  if (nb <= 0) return PBS_OK;
   const size_t nyz = (size_t)c->ny * c->nz;
+  const Dims d = dims_for(c, nb);
   ProfScope ps(c, PBS_KERNEL_ANGULAR);
-  cudaError_t e = launch_angular<real>(lctx(c), c->d, at<real>(c, c->off_psi),
+  cudaError_t e = launch_angular<real>(lctx(c), d, at<real>(c, c->off_psi),
                                        at<real>(c, c->off_rho) + (size_t)slab * nyz, at<real>(c, c->off_ts), h, c->du,
                                        c->dv);
   return e == cudaSuccess ? PBS_OK : cuda_fail(c, e, "angular kernel");
 }
 
-// Apply a deferred closing E(h/2) (of depth step steps_done - 1).
+template <typename real>
+pbs_status angular_all(pbs_ctx *c, double h, int slab) {
+  return angular_run<real>(c, h, slab, c->B);
+}
+
+// Apply a deferred closing E(h/2) (of depth step steps_done - 1) to the beams
+// that marched that step.
 template <typename real, typename st>
 pbs_status flush_impl(pbs_ctx *c) {
   if (!c->pending) return PBS_OK;
   c->pending = false;
-  return energy_run<real, st>(c, 0.5 * c->dx, c->steps_done - 1, -1, c->steps_done);
+  const int s = c->steps_done - 1;
+  return energy_run<real, st>(c, 0.5 * c->dx, s, -1, s + 1, 0, active_at(c, s));
 }
 
 // Depth steps.  The closing E(h/2) of a step is deferred and fused with the
 // opening E(h/2) of the next (same arithmetic, one pass over psi instead of
-// two); any read or substep call applies a deferred half first.
+// two); any read or substep call applies a deferred half first.  Beams whose
+// depth ends at step s - 1 get the closing half alone.
 template <typename real, typename st>
 pbs_status step_impl(pbs_ctx *c, int n) {
   for (int i = 0; i < n; i++) {
     const int s = c->steps_done;
+    const int act = active_at(c, s);
     pbs_status r;
-    if (c->pending)
-      r = energy_run<real, st>(c, 0.5 * c->dx, s - 1, s, s);  // close step s-1, open step s
-    else
-      r = energy_run<real, st>(c, 0.5 * c->dx, s, -1, -1);
+    if (c->pending) {
+      const int prev = active_at(c, s - 1);
+      r = energy_run<real, st>(c, 0.5 * c->dx, s - 1, s, s, 0, act);  // close step s-1, open step s
+      if (r == PBS_OK) r = energy_run<real, st>(c, 0.5 * c->dx, s - 1, -1, s, act, prev);  // close only
+    } else {
+      r = energy_run<real, st>(c, 0.5 * c->dx, s, -1, -1, 0, act);
+    }
     c->pending = false;
     if (r != PBS_OK) return r;
-    if ((r = transport_all<real>(c, 0.5 * c->dx)) != PBS_OK) return r;
-    if ((r = angular_all<real>(c, c->dx, s)) != PBS_OK) return r;
-    if ((r = transport_all<real>(c, 0.5 * c->dx)) != PBS_OK) return r;
-    c->pending = true;
+    if ((r = transport_run<real>(c, 0.5 * c->dx, act)) != PBS_OK) return r;
+    if ((r = angular_run<real>(c, c->dx, s, act)) != PBS_OK) return r;
+    if ((r = transport_run<real>(c, 0.5 * c->dx, act)) != PBS_OK) return r;
+    c->pending = act > 0;
     c->steps_done++;
   }
   return PBS_OK;
 }
 
+// Restart every beam from its projection (factors already on the device):
+// zero psi, dose, fluence and the status word, project, tally plane 0.
+// Device work only, so it can be captured into a graph.
 template <typename real, typename st>
-pbs_status launch_impl(pbs_ctx *c, const pbs_beam &b) {
+pbs_status reinit_impl(pbs_ctx *c) {
   const size_t nyz = (size_t)c->ny * c->nz;
-  std::vector<double> f;
-  beam_factors(c, b, f);
   PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_psi), 0, (size_t)c->d.ncomp * c->d.comp_elems * sizeof(real),
                               c->stream));
-  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_dose), 0, (size_t)c->nx * nyz * 8, c->stream));
-  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_flu), 0, (size_t)(c->nx + 1) * nyz * 8, c->stream));
+  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_dose), 0, (size_t)c->B * c->nx * nyz * 8, c->stream));
+  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_flu), 0, (size_t)c->B * (c->nx + 1) * nyz * 8, c->stream));
   PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_err), 0, 64, c->stream));
-  PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_init), f.data(), f.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  const double *fe = at<double>(c, c->off_init);
-  cudaError_t e = launch_init<real>(lctx(c), c->d, at<real>(c, c->off_psi), fe, fe + 2 * c->ng,
-                                    fe + 2 * c->ng + c->na, fe + 2 * c->ng + c->na + c->ny);
-  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
-  e = launch_fluence<real>(lctx(c), c->d, at<real>(c, c->off_psi), at<GroupCoef<real>>(c, c->off_coef),
-                           at<double>(c, c->off_flu), c->du * c->dv);
-  if (e != cudaSuccess) return cuda_fail(c, e, "fluence kernel");
-  PBS_CUDA(c, cudaStreamSynchronize(c->stream));  // f dies here
+  const Dims d1 = dims_for(c, 1);
+  for (int b = 0; b < c->B; b++) {
+    const double *fe = at<double>(c, c->off_init) + (size_t)b * init_stride(c);
+    real *psi_b = at<real>(c, c->off_psi) + (size_t)b * (c->K + 1) * c->d.comp_elems;
+    cudaError_t e = launch_init<real>(lctx(c), d1, psi_b, fe, fe + 2 * c->ng, fe + 2 * c->ng + c->na,
+                                      fe + 2 * c->ng + c->na + c->ny);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    e = launch_fluence<real>(lctx(c), d1, psi_b, c->K + 1, at<GroupCoef<real>>(c, c->off_coef),
+                             at<double>(c, c->off_flu) + (size_t)b * (c->nx + 1) * nyz, c->du * c->dv);
+    if (e != cudaSuccess) return cuda_fail(c, e, "fluence kernel");
+  }
   c->steps_done = 0;
+  c->pending = false;
+  return PBS_OK;
+}
+
+template <typename real, typename st>
+pbs_status launch_impl(pbs_ctx *c, const pbs_beam *beams) {
+  std::vector<double> f((size_t)c->B * init_stride(c)), one;
+  for (int b = 0; b < c->B; b++) {
+    beam_factors(c, beams[b], one);
+    std::copy(one.begin(), one.end(), f.begin() + (size_t)b * init_stride(c));
+  }
+  PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_init), f.data(), f.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  pbs_status r = reinit_impl<real, st>(c);
+  if (r != PBS_OK) return r;
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));  // f dies here
+  return PBS_OK;
+}
+
+// The whole march of every beam (restart, steps to the deepest beam's depth,
+// closing half), issued on the context's stream.
+template <typename real, typename st>
+pbs_status run_impl(pbs_ctx *c) {
+  pbs_status r = reinit_impl<real, st>(c);
+  if (r != PBS_OK) return r;
+  if ((r = step_impl<real, st>(c, max_depth(c))) != PBS_OK) return r;
+  return flush_impl<real, st>(c);
+}
+
+// Record run_impl into a CUDA graph on a private stream (once per beam
+// depths / material extent / launch shapes) and launch it on the context's
+// stream.
+template <typename real, typename st>
+pbs_status run_graph_impl(pbs_ctx *c) {
+  const int depth = max_depth(c);
+  if (!c->graph || c->graph_depth != depth) {
+    drop_graph(c);
+    if (!c->cap_stream) PBS_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = c->stream;
+    const long long before = c->launches;
+    c->stream = c->cap_stream;
+    c->capturing = true;
+    cudaGraph_t g = nullptr;
+    pbs_status r = PBS_OK;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      r = run_impl<real, st>(c);
+      cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    c->capturing = false;
+    c->graph_kernels = c->launches - before;  // kernels per replay, counted when they run
+    c->launches = before;
+    if (r != PBS_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      return cuda_fail(c, e, "graph instantiate");
+    }
+    c->graph_depth = depth;
+  }
+  PBS_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+  c->launches += c->graph_kernels;
+  c->steps_done = depth;
   c->pending = false;
   return PBS_OK;
 }
@@ -481,6 +636,69 @@ pbs_status eval_source_impl(pbs_ctx *c, int k_from, int slab, double *out) {
 
 bool ready_to_march(pbs_ctx *c) { return c->ws && c->have_tables && c->have_material && c->have_beam; }
 
+// Launch-shape autotuner.  Times each candidate shape of the energy pass
+// (angles per block) and of the streaming transport (resident CTAs per SM)
+// on the launched beams with CUDA events, best of `reps`, keeps the fastest,
+// then restarts the beams from their projections (the trial passes advance
+// the state).  Every candidate computes the same psi; only the summation
+// order of the dose reduction depends on the energy shape.
+template <typename real, typename st>
+pbs_status autotune_impl(pbs_ctx *c, int reps) {
+  pbs_status r = flush_impl<real, st>(c);
+  if (r != PBS_OK) return r;
+  const bool prof = c->profiling;
+  c->profiling = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PBS_CUDA(c, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c, PBS_ERR_CUDA, "event create");
+  }
+  auto time_best = [&](auto &&fn, float &best) -> pbs_status {
+    best = 1e30f;
+    for (int i = 0; i < reps; i++) {
+      PBS_CUDA(c, cudaEventRecord(e0, c->stream));
+      pbs_status q = fn();
+      if (q != PBS_OK) return q;
+      PBS_CUDA(c, cudaEventRecord(e1, c->stream));
+      PBS_CUDA(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      PBS_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+      best = std::min(best, ms);
+    }
+    return PBS_OK;
+  };
+  const int slab_b = c->n_slabs > 1 ? 1 : 0;
+  float best_e = 1e30f, best_t = 1e30f;
+  int pick_e = c->tune_energy_angles, pick_t = c->tune_transport_ctas;
+  for (int ay : {4, 8, 16}) {
+    c->tune_energy_angles = ay;
+    float ms;
+    r = time_best([&] { return energy_run<real, st>(c, 0.5 * c->dx, 0, slab_b, -1, 0, c->B); }, ms);
+    if (r != PBS_OK) break;
+    if (ms < best_e) { best_e = ms; pick_e = ay; }
+  }
+  if (r == PBS_OK) {
+    for (int ctas : {1, 2, 3, 4, 0}) {
+      c->tune_transport_ctas = ctas;
+      float ms;
+      r = time_best([&] { return transport_run<real>(c, 0.5 * c->dx, c->B); }, ms);
+      if (r != PBS_OK) break;
+      if (ms < best_t) { best_t = ms; pick_t = ctas; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->profiling = prof;
+  c->tune_energy_angles = pick_e;
+  c->tune_transport_ctas = pick_t;
+  drop_graph(c);
+  if (r != PBS_OK) return r;
+  if ((r = reinit_impl<real, st>(c)) != PBS_OK) return r;
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PBS_OK;
+}
+
 }  // namespace
 
 #define PBS_DISPATCH(c, FN, ...)                                                    \
@@ -496,7 +714,7 @@ pbs_status pbs_create(pbs_ctx **out, const pbs_grid *g, int precision, void *str
   if (!out || !g || !g->e_faces) return PBS_ERR_ARG;
   *out = nullptr;
   if (g->ny < 1 || g->nz < 1 || g->ng < 1 || g->nu < 1 || g->nv < 1 || g->nx < 1 || g->n_scatter < 0 ||
-      !(g->dy > 0) || !(g->dz > 0) || !(g->dx > 0) || !(g->u_max > 0) || !(g->v_max > 0))
+      g->n_beams < 1 || g->n_beams > 65535 || !(g->dy > 0) || !(g->dz > 0) || !(g->dx > 0) || !(g->u_max > 0) || !(g->v_max > 0))
     return PBS_ERR_ARG;
   if (precision < PBS_FP64 || precision > PBS_MIXED) return PBS_ERR_ARG;
   for (int f = 0; f < g->ng; f++)
@@ -517,6 +735,8 @@ pbs_status pbs_create(pbs_ctx **out, const pbs_grid *g, int precision, void *str
   c->precision = precision;
   c->ny = g->ny; c->nz = g->nz; c->ng = g->ng; c->nu = g->nu; c->nv = g->nv; c->na = g->nu * g->nv;
   c->nx = g->nx; c->K = g->n_scatter;
+  c->B = g->n_beams;
+  c->beam_steps.assign(c->B, g->nx);
   c->dy = g->dy; c->dz = g->dz; c->dx = g->dx; c->u_max = g->u_max; c->v_max = g->v_max;
   c->du = 2.0 * g->u_max / (g->nu + 1);
   c->dv = 2.0 * g->v_max / (g->nv + 1);
@@ -533,7 +753,7 @@ pbs_status pbs_create(pbs_ctx **out, const pbs_grid *g, int precision, void *str
   for (int j = 0; j < g->nv; j++) c->v[j] = (j - 0.5 * (g->nv - 1)) * c->dv;
   Dims &d = c->d;
   d.ny = c->ny; d.nz = c->nz; d.ng = c->ng; d.nu = c->nu; d.nv = c->nv; d.na = c->na;
-  d.nyz = c->ny * c->nz; d.ncomp = c->K + 1;
+  d.nyz = c->ny * c->nz; d.nbeam = c->B; d.ncomp = c->B * (c->K + 1);
   d.lanes = (long long)d.na * d.nyz;
   d.comp_elems = (long long)d.ng * 2 * d.lanes;
   c->rsize = precision == PBS_FP64 ? 8 : 4;
@@ -553,6 +773,7 @@ pbs_status pbs_bind_workspace(pbs_ctx *c, void *p, size_t bytes) {
   if (!c || !p) return fail(c, PBS_ERR_ARG, "null workspace");
   if (bytes < c->total) return fail(c, PBS_ERR_ARG, "workspace too small");
   if (((uintptr_t)p) & 255) return fail(c, PBS_ERR_ARG, "workspace not 256-byte aligned");
+  drop_graph(c);
   c->ws = (unsigned char *)p;
   c->ws_bytes = bytes;
   c->have_beam = false;
@@ -609,11 +830,65 @@ pbs_status pbs_set_material(pbs_ctx *c, const double *rho, int n) {
 pbs_status pbs_launch_beam(pbs_ctx *c, const pbs_beam *b) {
   if (!c || !b) return fail(c, PBS_ERR_ARG, "null beam");
   if (!c->ws || !c->have_tables) return fail(c, PBS_ERR_STATE, "bind a workspace and set the physics first");
-  if (!(b->sigma_e > 0) || !(b->sigma_y > 0) || !(b->sigma_z > 0) || !(b->sigma_u > 0) || !(b->sigma_v > 0))
-    return fail(c, PBS_ERR_ARG, "beam widths must be > 0");
-  pbs_status r = PBS_DISPATCH(c, launch_impl, c, *b);
+  std::vector<pbs_beam> all(c->B, *b);
+  return pbs_launch_beams(c, all.data(), c->B);
+}
+
+pbs_status pbs_launch_beams(pbs_ctx *c, const pbs_beam *beams, int n) {
+  if (!c || !beams) return fail(c, PBS_ERR_ARG, "null beams");
+  if (n != c->B) return fail(c, PBS_ERR_ARG, "n must equal the context's n_beams");
+  if (!c->ws || !c->have_tables) return fail(c, PBS_ERR_STATE, "bind a workspace and set the physics first");
+  for (int i = 0; i < n; i++) {
+    const pbs_beam *b = beams + i;
+    if (!(b->sigma_e > 0) || !(b->sigma_y > 0) || !(b->sigma_z > 0) || !(b->sigma_u > 0) || !(b->sigma_v > 0))
+      return fail(c, PBS_ERR_ARG, "beam widths must be > 0");
+  }
+  pbs_status r = PBS_DISPATCH(c, launch_impl, c, beams);
   if (r != PBS_OK) return r;
   c->have_beam = true;
+  return PBS_OK;
+}
+
+pbs_status pbs_set_beam_steps(pbs_ctx *c, const int *steps, int n) {
+  if (!c || !steps) return fail(c, PBS_ERR_ARG, "null steps");
+  if (n != c->B) return fail(c, PBS_ERR_ARG, "n must equal the context's n_beams");
+  for (int i = 0; i < n; i++) {
+    if (steps[i] < 0 || steps[i] > c->nx) return fail(c, PBS_ERR_ARG, "beam steps must lie in [0, nx]");
+    if (i > 0 && steps[i] > steps[i - 1]) return fail(c, PBS_ERR_ARG, "beam steps must be non-increasing");
+  }
+  if (c->steps_done != 0 || c->pending) return fail(c, PBS_ERR_STATE, "set beam depths before marching");
+  c->beam_steps.assign(steps, steps + n);
+  drop_graph(c);
+  return PBS_OK;
+}
+
+pbs_status pbs_run(pbs_ctx *c, int use_graph) {
+  if (!c) return PBS_ERR_ARG;
+  if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
+  if (use_graph) return PBS_DISPATCH(c, run_graph_impl, c);
+  return PBS_DISPATCH(c, run_impl, c);
+}
+
+pbs_status pbs_autotune(pbs_ctx *c, int reps) {
+  if (!c || reps < 1) return fail(c, PBS_ERR_ARG, "reps must be >= 1");
+  if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
+  return PBS_DISPATCH(c, autotune_impl, c, reps);
+}
+
+pbs_status pbs_set_tuning(pbs_ctx *c, int energy_angles, int transport_ctas) {
+  if (!c) return PBS_ERR_ARG;
+  if ((energy_angles != 4 && energy_angles != 8 && energy_angles != 16) || transport_ctas < 0 || transport_ctas > 64)
+    return fail(c, PBS_ERR_ARG, "energy_angles must be 4, 8 or 16 and transport_ctas in [0, 64]");
+  c->tune_energy_angles = energy_angles;
+  c->tune_transport_ctas = transport_ctas;
+  drop_graph(c);
+  return PBS_OK;
+}
+
+pbs_status pbs_get_tuning(const pbs_ctx *c, int *energy_angles, int *transport_ctas) {
+  if (!c || !energy_angles || !transport_ctas) return PBS_ERR_ARG;
+  *energy_angles = c->tune_energy_angles;
+  *transport_ctas = c->tune_transport_ctas;
   return PBS_OK;
 }
 
@@ -640,9 +915,11 @@ pbs_status pbs_read_dose(pbs_ctx *c, double *out, size_t n) {
   if (!c || !out) return fail(c, PBS_ERR_ARG, "null output");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
   { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
-  const size_t nyz = (size_t)c->ny * c->nz;
-  if (n % nyz != 0 || n / nyz > (size_t)c->nx) return fail(c, PBS_ERR_ARG, "n must be n_slabs*ny*nz");
-  PBS_CUDA(c, cudaMemcpyAsync(out, at<void>(c, c->off_dose), n * 8, cudaMemcpyDeviceToHost, c->stream));
+  const size_t per = (size_t)c->B * c->ny * c->nz;
+  if (n == 0 || n % per != 0 || n / per > (size_t)c->nx) return fail(c, PBS_ERR_ARG, "n must be n_beams*n_slabs*ny*nz");
+  const size_t row = n / c->B * 8;  // bytes of one beam's slabs
+  PBS_CUDA(c, cudaMemcpy2DAsync(out, row, at<void>(c, c->off_dose), (size_t)c->nx * c->ny * c->nz * 8, row, c->B,
+                                cudaMemcpyDeviceToHost, c->stream));
   PBS_CUDA(c, cudaStreamSynchronize(c->stream));
   return check_device_status(c);
 }
@@ -651,15 +928,18 @@ pbs_status pbs_read_fluence(pbs_ctx *c, double *out, size_t n) {
   if (!c || !out) return fail(c, PBS_ERR_ARG, "null output");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
   { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
-  const size_t nyz = (size_t)c->ny * c->nz;
-  if (n % nyz != 0 || n / nyz > (size_t)c->steps_done + 1) return fail(c, PBS_ERR_ARG, "n must be n_planes*ny*nz");
-  PBS_CUDA(c, cudaMemcpyAsync(out, at<void>(c, c->off_flu), n * 8, cudaMemcpyDeviceToHost, c->stream));
+  const size_t per = (size_t)c->B * c->ny * c->nz;
+  if (n == 0 || n % per != 0 || n / per > (size_t)c->steps_done + 1)
+    return fail(c, PBS_ERR_ARG, "n must be n_beams*n_planes*ny*nz");
+  const size_t row = n / c->B * 8;
+  PBS_CUDA(c, cudaMemcpy2DAsync(out, row, at<void>(c, c->off_flu), (size_t)(c->nx + 1) * c->ny * c->nz * 8, row, c->B,
+                                cudaMemcpyDeviceToHost, c->stream));
   PBS_CUDA(c, cudaStreamSynchronize(c->stream));
   return check_device_status(c);
 }
 
 pbs_status pbs_read_psi(pbs_ctx *c, int k, double *out, size_t n) {
-  if (!c || !out || k < 0 || k > c->K) return fail(c, PBS_ERR_ARG, "bad component");
+  if (!c || !out || k < 0 || k >= c->d.ncomp) return fail(c, PBS_ERR_ARG, "bad component");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
   { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   if (n != (size_t)c->d.comp_elems) return fail(c, PBS_ERR_ARG, "n must be ng*2*nu*nv*ny*nz");
@@ -667,7 +947,7 @@ pbs_status pbs_read_psi(pbs_ctx *c, int k, double *out, size_t n) {
 }
 
 pbs_status pbs_write_psi(pbs_ctx *c, int k, const double *in, size_t n) {
-  if (!c || !in || k < 0 || k > c->K) return fail(c, PBS_ERR_ARG, "bad component");
+  if (!c || !in || k < 0 || k >= c->d.ncomp) return fail(c, PBS_ERR_ARG, "bad component");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
   { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   if (n != (size_t)c->d.comp_elems) return fail(c, PBS_ERR_ARG, "n must be ng*2*nu*nv*ny*nz");
@@ -697,7 +977,7 @@ pbs_status pbs_substep_angular(pbs_ctx *c, double h, int slab) {
 }
 
 pbs_status pbs_eval_source(pbs_ctx *c, int k_from, int slab, double *out, size_t n) {
-  if (!c || !out || k_from < 0 || k_from > c->K || slab < 0 || slab >= c->n_slabs)
+  if (!c || !out || k_from < 0 || k_from >= c->d.ncomp || slab < 0 || slab >= c->n_slabs)
     return fail(c, PBS_ERR_ARG, "bad arguments");
   if (c->K < 1) return fail(c, PBS_ERR_STATE, "the context has no scattered component (n_scatter = 0)");
   if (!c->ws || !c->have_tables || !c->have_material) return fail(c, PBS_ERR_STATE, "not set up");

@@ -38,7 +38,8 @@ struct GroupCoef {
 };
 
 struct Dims {
-  int ny, nz, ng, nu, nv, na, nyz, ncomp;  // ncomp = K + 1
+  int ny, nz, ng, nu, nv, na, nyz, ncomp;  // ncomp = n_beams * (K + 1): all components
+  int nbeam;                                // independent beams
   long long lanes;                          // na * nyz
   long long comp_elems;                     // ng * 2 * lanes
 };
@@ -143,6 +144,9 @@ struct LaunchCtx {
   int num_sms;
   long long *launches;  // host counter
   int *err = nullptr;   // device status word (bounded waits record timeouts here)
+  // launch shapes chosen by the autotuner (pbs_autotune)
+  int energy_angles = 8;   // energy: angles per block (4, 8 or 16) x 32 lateral points
+  int transport_ctas = 0;  // streaming transport: resident CTAs per SM (0 = as many as fit)
 };
 
 // One E substep's per-lane inputs and outputs: density of its slab, c = h/2,
@@ -157,12 +161,20 @@ struct EnergyHalf {
   double *dose;
 };
 
-// E substep on one component; with hb != NULL, two consecutive E substeps
-// (ha then hb) fused in one pass.  flu_yz receives the fluence after ha.
+// Per-beam strides of the pointers an energy launch receives (blockIdx.z =
+// beam): psi of the same component of the next beam, its source/R buffers,
+// its dose slab array and its fluence plane array.
+struct BeamStrides {
+  long long psi, src, dose, flu;
+};
+
+// E substep on one component of every beam; with hb != NULL, two consecutive
+// E substeps (ha then hb) fused in one pass.  flu_yz receives the fluence
+// after ha.
 template <typename real, typename st>
 cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
                           const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
-                          double dose_scale, double flu_scale);
+                          double dose_scale, double flu_scale, const BeamStrides &bs);
 
 template <typename real>
 cudaError_t launch_transport(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
@@ -183,8 +195,11 @@ bool angular_supported(int nu, int nv);
 // (synchronous; done once per context at creation).
 cudaError_t angular_init_tables();
 
+// src[b][g] = du dv P2_g R[b][g] for nbatch = n_beams source blocks of ng
+// groups each (R, src laid out [b][g][a][yz]).
 template <typename real, typename st>
-cudaError_t launch_source(const LaunchCtx &lc, const Dims &d, const st *p2, const st *r, st *src, double dudv);
+cudaError_t launch_source(const LaunchCtx &lc, const Dims &d, const st *p2, const st *r, st *src, double dudv,
+                          int nbatch = 1);
 
 // R of one state for pbs_eval_source; precision as pbs_precision.
 cudaError_t launch_source_input(const LaunchCtx &lc, const Dims &d, const void *psi_k, const void *rho_yz,
@@ -194,8 +209,9 @@ template <typename real>
 cudaError_t launch_init(const LaunchCtx &lc, const Dims &d, real *psi0, const double *fe, const double *fa,
                         const double *fy, const double *fz);
 
+// Fluence of one beam: ncomp_beam components starting at psi.
 template <typename real>
-cudaError_t launch_fluence(const LaunchCtx &lc, const Dims &d, const real *psi, const GroupCoef<real> *coef,
-                           double *flu_yz, double scale);
+cudaError_t launch_fluence(const LaunchCtx &lc, const Dims &d, const real *psi, int ncomp_beam,
+                           const GroupCoef<real> *coef, double *flu_yz, double scale);
 
 }  // namespace pbs

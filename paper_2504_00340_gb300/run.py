@@ -2,9 +2,13 @@
 
     python -m paper_2504_00340_gb300.run --workload water150_128x128_g256_a16x16 \
         [--ny 64 --nz 64] [--ng G] [--steps N] [--precision fp32|fp64|mixed]
+    python -m paper_2504_00340_gb300.run --spots 256 [--max-gb 48] [--no-graph] [--no-autotune]
 
 Sizes may be overridden to make reduced cases of the same kernels (e.g. for
-profiling).  Prints the per-kernel device times of the march.
+profiling).  Prints the per-kernel device times of the march.  --spots runs
+the first N spots of the seeded 256-spot batch (bucketed contexts, each
+marched as one CUDA graph); under torchrun the buckets are spread over the
+ranks and rank 0 prints the totals (device time: max over ranks).
 """
 from __future__ import annotations
 
@@ -13,6 +17,49 @@ import json
 import time
 
 import numpy as np
+
+
+def run_spots(a) -> dict:
+    import os
+
+    import torch
+
+    from . import spots as S
+    from .workloads import spot_batch
+    rank, world = int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sp = spot_batch()[:a.spots]
+    t0 = time.perf_counter()
+    doses, st = S.run_shard(sp, rank, world, max_bytes=int(a.max_gb * (1 << 30)), use_graph=not a.no_graph,
+                            autotune=not a.no_autotune)
+    wall = time.perf_counter() - t0
+    dev_ms = st["device_ms"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+        n = torch.tensor([st["cell_updates"]], device="cuda", dtype=torch.float64)
+        dist.all_reduce(n)
+        processed = float(n.item())
+        doses = S.gather_doses(doses, rank, world)
+    else:
+        processed = float(st["cell_updates"])
+    out = None
+    if rank == 0:
+        useful = float(S.useful_cost(sp))
+        out = {"spots": len(sp), "ranks": world, "buckets_rank0": st["buckets"], "device_ms": dev_ms,
+               "wall_s_rank0": wall, "cell_updates_processed": processed, "cell_updates_useful": useful,
+               "cell_updates_per_s": useful / (dev_ms * 1e-3), "kernels_rank0": st["kernels"],
+               "tuning_rank0": st["tuning"], "graph": not a.no_graph,
+               "max_dose": float(max(np.abs(d).max() for d in doses.values()))}
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
 
 
 def main(argv=None):
@@ -25,7 +72,16 @@ def main(argv=None):
     p.add_argument("--ng", type=int)
     p.add_argument("--steps", type=int)
     p.add_argument("--precision", choices=["fp64", "fp32", "mixed"])
+    p.add_argument("--spots", type=int, default=0, help="run the first N spots of the 256-spot batch")
+    p.add_argument("--max-gb", type=float, default=48.0, help="device workspace per spot bucket (GiB)")
+    p.add_argument("--no-graph", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
     a = p.parse_args(argv)
+    if a.spots:
+        out = run_spots(a)
+        if out is not None:
+            print(json.dumps(out))
+        return
     w = WORKLOADS[a.workload]
     kw = {k: getattr(a, k) for k in ("ny", "nz", "ng") if getattr(a, k)}
     if a.ng:
