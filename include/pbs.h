@@ -189,19 +189,37 @@ pbs_status pbs_set_beam_steps(pbs_ctx *ctx, const int *steps, int n);
  * work around it. */
 pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
 
-/* Launch-shape autotuner: times the candidate shapes of the energy pass
- * (angles per block: 4, 8, 16) and of the streaming transport (resident CTAs
- * per SM: 1, 2, 3, 4, as many as fit) on the launched beams with CUDA events,
- * best of reps trials each, and keeps the fastest.  The trials advance the
- * state, so the beams restart from their projections afterwards (depth 0).
- * Synchronises.  Results of psi do not depend on the shapes; the dose's
- * angle reduction order does (rounding only). */
+/* Launch shapes and kernel forms of the march.  Every setting computes the
+ * same method; forms differ in how the work maps onto the GPU, and the
+ * packed forms differ from the plain ones by rounding only.
+ *   energy_angles   angles per block of the energy pass: 4, 8 or 16
+ *   energy_form     FP32 energy pass: 0 one lane per thread, 1 two lateral
+ *                   points per thread on the packed FP32x2 datapath (needs
+ *                   ny*nz even, else form 0 runs)
+ *   transport_ctas  resident CTAs per SM of the streaming transport, 0..64
+ *                   (0 = as many as fit)
+ *   angular_form    angular substep: 0 direct, 1 TMA-staged persistent
+ *                   (needs a row pitch of ny*nz elements that is a multiple of
+ *                   16 bytes), 2 packed FP32x2 (FP32, ny*nz even); a form the
+ *                   grid does not allow falls back to 0 */
+typedef struct {
+  int energy_angles;
+  int energy_form;
+  int transport_ctas;
+  int angular_form;
+} pbs_tuning;
+
+/* Launch-shape autotuner: times the candidate energy forms and shapes (angles
+ * per block 4, 8, 16), transport residencies (1, 2, 3, 4, as many as fit) and
+ * angular forms on the launched beams with CUDA events, best of reps trials
+ * each, and keeps the fastest.  The trials advance the state, so the beams
+ * restart from their projections afterwards (depth 0).  Synchronises. */
 pbs_status pbs_autotune(pbs_ctx *ctx, int reps);
 
-/* Set / read the launch shapes directly: energy_angles in {4, 8, 16},
- * transport_ctas in [0, 64] (0 = as many as fit). */
-pbs_status pbs_set_tuning(pbs_ctx *ctx, int energy_angles, int transport_ctas);
-pbs_status pbs_get_tuning(const pbs_ctx *ctx, int *energy_angles, int *transport_ctas);
+/* Set / read the launch shapes directly (PBS_ERR_ARG for a value outside the
+ * ranges above). */
+pbs_status pbs_set_tuning(pbs_ctx *ctx, const pbs_tuning *tuning);
+pbs_status pbs_get_tuning(const pbs_ctx *ctx, pbs_tuning *tuning);
 
 /* Depth steps marched since pbs_launch_beam. */
 pbs_status pbs_get_depth(const pbs_ctx *ctx, int *steps_done);

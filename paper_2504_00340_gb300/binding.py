@@ -45,6 +45,13 @@ class PbsBeam(ctypes.Structure):
                                                "sigma_u", "sigma_v")]
 
 
+class PbsTuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in ("energy_angles", "energy_form", "transport_ctas", "angular_form")]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class PbsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -64,8 +71,8 @@ SIGNATURES = [
     ("pbs_set_beam_steps", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("pbs_run", ctypes.c_int, [_VP, ctypes.c_int]),
     ("pbs_autotune", ctypes.c_int, [_VP, ctypes.c_int]),
-    ("pbs_set_tuning", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
-    ("pbs_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("pbs_set_tuning", ctypes.c_int, [_VP, ctypes.POINTER(PbsTuning)]),
+    ("pbs_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(PbsTuning)]),
     ("pbs_step", ctypes.c_int, [_VP, ctypes.c_int]),
     ("pbs_flush", ctypes.c_int, [_VP]),
     ("pbs_get_depth", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
@@ -182,14 +189,14 @@ def pbs_autotune(ctx, reps: int = 3) -> None:
     _check(ctx, load_library().pbs_autotune(_VP(ctx), int(reps)))
 
 
-def pbs_set_tuning(ctx, energy_angles: int, transport_ctas: int) -> None:
-    _check(ctx, load_library().pbs_set_tuning(_VP(ctx), int(energy_angles), int(transport_ctas)))
+def pbs_set_tuning(ctx, tuning: PbsTuning) -> None:
+    _check(ctx, load_library().pbs_set_tuning(_VP(ctx), ctypes.byref(tuning)))
 
 
-def pbs_get_tuning(ctx):
-    a, b = ctypes.c_int(), ctypes.c_int()
-    _check(ctx, load_library().pbs_get_tuning(_VP(ctx), ctypes.byref(a), ctypes.byref(b)))
-    return a.value, b.value
+def pbs_get_tuning(ctx) -> PbsTuning:
+    t = PbsTuning()
+    _check(ctx, load_library().pbs_get_tuning(_VP(ctx), ctypes.byref(t)))
+    return t
 
 
 def pbs_step(ctx, n_steps: int) -> None:
@@ -377,11 +384,16 @@ class Solver:
         pbs_autotune(self.ctx, reps)
 
     @property
-    def tuning(self):
-        return pbs_get_tuning(self.ctx)
+    def tuning(self) -> dict:
+        """Launch shapes and kernel forms: energy_angles, energy_form,
+        transport_ctas, angular_form."""
+        return pbs_get_tuning(self.ctx).as_dict()
 
-    def set_tuning(self, energy_angles: int, transport_ctas: int):
-        pbs_set_tuning(self.ctx, energy_angles, transport_ctas)
+    def set_tuning(self, **kw):
+        t = pbs_get_tuning(self.ctx)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        pbs_set_tuning(self.ctx, t)
 
     def step(self, n: int):
         pbs_step(self.ctx, n)

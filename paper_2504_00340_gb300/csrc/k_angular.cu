@@ -16,9 +16,21 @@
 // transforms column m along v, scales by the mode factor, transforms back
 // along v; thread (x, j) transforms back along u and stores to global memory.
 // Sine and eigenvalue tables travel as kernel parameters (constant bank).
+//
+// Main form (k_angular_tma): a persistent CTA walks its tiles of
+// [all angles x 32 lateral points] of one (component, g, c); each tile comes
+// in by one 2-D TMA copy (cp.async.bulk.tensor, rows nyz apart in memory) into
+// one of three shared-memory buffers, is transformed in place (u, then v with
+// the mode factor, then u back) and leaves by one TMA store, while the next
+// two tiles load.  No per-element global address arithmetic remains; the
+// direct form (k_angular) serves grids whose row pitch breaks the TMA rules.
 #include "pbs_internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
+#include <mutex>
 
 namespace pbs {
 
@@ -29,23 +41,28 @@ template <typename real>
 __host__ __device__ constexpr int tile_w() { return sizeof(real) == 8 ? 16 : 32; }
 
 // Orthonormal DST-I matrices sqrt(2/(N+1)) sin(pi (m+1)(i+1)/(N+1)) for every
-// size N <= 16, row-major [m][i], in the constant bank (they depend on N
-// only).  Indexed with compile-time offsets, so the multiply-adds read them
-// as constant operands.
-__constant__ float c_dst_f[kMaxAngle + 1][kMaxAngle * kMaxAngle];
-__constant__ double c_dst_d[kMaxAngle + 1][kMaxAngle * kMaxAngle];
+// even size N <= 16, row-major [m][i], packed one after another (size N at
+// offset dst_off(N)) in the constant bank (they depend on N only).  Indexed
+// with compile-time offsets, so the multiply-adds read them as constant
+// operands.  c_dst_f2 holds each FP32 entry twice, as the pair operand of the
+// packed FP32x2 multiply-adds.
+__host__ __device__ constexpr int dst_off(int n) { return n <= 2 ? 0 : dst_off(n - 2) + (n - 2) * (n - 2); }
+constexpr int kDstEntries = dst_off(kMaxAngle + 2);
+__constant__ float c_dst_f[kDstEntries];
+__constant__ double c_dst_d[kDstEntries];
+__constant__ float2 c_dst_f2[kDstEntries];
 
 template <typename real>
 struct DstTab;
 template <>
 struct DstTab<float> {
   template <int N>
-  static __device__ __forceinline__ float at(int idx) { return c_dst_f[N][idx]; }
+  static __device__ __forceinline__ float at(int idx) { return c_dst_f[dst_off(N) + idx]; }
 };
 template <>
 struct DstTab<double> {
   template <int N>
-  static __device__ __forceinline__ double at(int idx) { return c_dst_d[N][idx]; }
+  static __device__ __forceinline__ double at(int idx) { return c_dst_d[dst_off(N) + idx]; }
 };
 
 template <typename real>
@@ -134,6 +151,296 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
   (void)NT;
 }
 
+// ---------------------------------------------------------------- packed FP32 form
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// dst_apply on pairs (two lateral points per register pair).
+template <int N>
+__device__ __forceinline__ void dst_apply2(const float2 (&x)[N], float2 (&y)[N]) {
+  constexpr int H = N / 2;
+  float2 e[H], o[H];
+#pragma unroll
+  for (int i = 0; i < H; i++) {
+    e[i] = add2(x[i], x[N - 1 - i]);
+    o[i] = fma2(x[N - 1 - i], make_float2(-1.f, -1.f), x[i]);
+  }
+#pragma unroll
+  for (int m = 0; m < N; m++) y[m] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < H; i++)
+#pragma unroll
+    for (int m = 0; m < N; m++) y[m] = fma2(c_dst_f2[dst_off(N) + m * N + i], (m & 1) ? o[i] : e[i], y[m]);
+}
+
+// As k_angular with each thread on two adjacent lateral points (one 8-byte
+// load per row) and the transforms on FP32x2 pairs; 64 lateral points per
+// CTA.  nyz must be even.
+template <int NU, int NV>
+__global__ void __launch_bounds__(32 * (NU > NV ? NU : NV), 1)
+    k_angular_f2(float *__restrict__ psi, const float *__restrict__ rho_yz, const float *__restrict__ ts, int nyz,
+                 int ng, float hq, long long kgc0, const __grid_constant__ AngTables<float> tb) {
+  constexpr int NA = NU * NV;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2(*tile)[32] = reinterpret_cast<float2(*)[32]>(smem_raw);
+  const int x = threadIdx.x;
+  const int t = threadIdx.y;
+  const long long kgc = kgc0 + blockIdx.y;  // (k * ng + g) * 2 + c
+  const int g = (int)((kgc / 2) % ng);
+  const int yz = (blockIdx.x * 32 + x) * 2;
+  const bool active = yz < nyz;
+  float *base = psi + kgc * (long long)NA * nyz + yz;
+  if (t < NV) {
+    float2 r[NU], y[NU];
+#pragma unroll
+    for (int i = 0; i < NU; i++)
+      r[i] = active ? *reinterpret_cast<const float2 *>(base + (long long)(t * NU + i) * nyz) : make_float2(0.f, 0.f);
+    dst_apply2<NU>(r, y);
+#pragma unroll
+    for (int i = 0; i < NU; i++) tile[t * NU + i][x] = y[i];
+  }
+  __syncthreads();
+  if (t < NU) {
+    float2 q = make_float2(0.f, 0.f);
+    if (active) {
+      const float2 rr = *reinterpret_cast<const float2 *>(rho_yz + yz);
+      const float w = hq * ts[g];
+      q = make_float2(w * rr.x, w * rr.y);  // h kappa / 4
+    }
+    float2 c[NV], y[NV];
+#pragma unroll
+    for (int j = 0; j < NV; j++) c[j] = tile[j * NU + t][x];
+    dst_apply2<NV>(c, y);
+#pragma unroll
+    for (int n = 0; n < NV; n++) {
+      const float l = tb.lam[n * NU + t];
+      y[n].x *= mode_factor(1.f - q.x * l);
+      y[n].y *= mode_factor(1.f - q.y * l);
+    }
+    dst_apply2<NV>(y, c);
+#pragma unroll
+    for (int j = 0; j < NV; j++) tile[j * NU + t][x] = c[j];
+  }
+  __syncthreads();
+  if (t < NV) {
+    float2 r[NU], y[NU];
+#pragma unroll
+    for (int i = 0; i < NU; i++) r[i] = tile[t * NU + i][x];
+    dst_apply2<NU>(r, y);
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < NU; i++) *reinterpret_cast<float2 *>(base + (long long)(t * NU + i) * nyz) = y[i];
+    }
+  }
+}
+
+template <int NU, int NV>
+cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
+                  const AngTables<float> &tb) {
+  constexpr int NT = NU > NV ? NU : NV;
+  const size_t smem = sizeof(float2) * NU * NV * 32;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_angular_f2<NU, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const long long total = (long long)d.ncomp * d.ng * 2;
+  for (long long k0 = 0; k0 < total; k0 += 65535) {
+    const long long cnt = total - k0 < 65535 ? total - k0 : 65535;
+    dim3 grid((d.nyz / 2 + 31) / 32, (unsigned)cnt);
+    k_angular_f2<NU, NV><<<grid, dim3(32, NT), smem, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng, (float)(0.25 * h),
+                                                                  k0, tb);
+    ++*lc.launches;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- TMA form
+
+constexpr int kAngBufs = 3;                        // tiles in flight per CTA
+constexpr long long kAngWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded waits
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+               "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Tile t covers rows [stack * NA, stack * NA + NA) and lateral points
+// [tx * TW, tx * TW + TW) with stack = t / ntx (= (k * ng + g) * 2 + c).
+template <typename real, int NU, int NV>
+__global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
+    k_angular_tma(const __grid_constant__ CUtensorMap map, const real *__restrict__ rho_yz,
+                  const real *__restrict__ ts, int nyz, int ng, int ntx, long long ntiles, real hq,
+                  const __grid_constant__ AngTables<real> tb, int *err) {
+  constexpr int NA = NU * NV;
+  constexpr int kTW = tile_w<real>();
+  constexpr unsigned kTileBytes = NA * kTW * sizeof(real);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  real(*buf)[NA][kTW] = reinterpret_cast<real(*)[NA][kTW]>(smem_raw);
+  __shared__ __align__(8) uint64_t full[kAngBufs];
+  const int x = threadIdx.x, t = threadIdx.y;
+  const bool leader = (x == 0 && t == 0);
+  const long long step = gridDim.x;
+  if (leader) {
+    for (int b = 0; b < kAngBufs; b++) mbar_init(&full[b], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  // prologue: the CTA's first kAngBufs - 1 tiles
+  if (leader) {
+    for (int j = 0; j < kAngBufs - 1; j++) {
+      const long long tile = blockIdx.x + j * step;
+      if (tile < ntiles) {
+        mbar_arrive_expect_tx(&full[j], kTileBytes);
+        tma_load_2d(buf[j], &map, (int)(tile % ntx) * kTW, (int)(tile / ntx) * NA, &full[j]);
+      }
+    }
+  }
+  long long i = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += step, i++) {
+    const int b = (int)(i % kAngBufs);
+    const bool ok = mbar_wait_bounded(&full[b], (unsigned)((i / kAngBufs) & 1), kAngWaitCycles);
+    if (__syncthreads_or(!ok)) {
+      // a copy never arrived: record it, let the copies in flight land, stop
+      if (leader) {
+        atomicAdd(err, 1);
+        err[1] = 3;
+        for (int j = 1; j < kAngBufs; j++) {
+          const long long ti = tile + j * step;
+          if (ti < ntiles && j < kAngBufs - 1)
+            mbar_wait_bounded(&full[(b + j) % kAngBufs], (unsigned)(((i + j) / kAngBufs) & 1), kAngWaitCycles);
+        }
+        bulk_wait_all();
+      }
+      return;
+    }
+    real(*tl)[kTW] = buf[b];
+    const long long stack = tile / ntx;
+    const int g = (int)((stack / 2) % ng);
+    const int yz = (int)(tile % ntx) * kTW + x;
+    constexpr int NT = NU > NV ? NU : NV;
+    // along u: row t of the slab, in place
+    if (t < NV) {
+      real r[NU], y[NU];
+#pragma unroll
+      for (int k = 0; k < NU; k++) r[k] = tl[t * NU + k][x];
+      dst_apply<real, NU>(r, y);
+#pragma unroll
+      for (int k = 0; k < NU; k++) tl[t * NU + k][x] = y[k];
+    }
+    __syncthreads();
+    // along v with the mode factor: column m = t
+    if (t < NU) {
+      const real q = (yz < nyz) ? hq * rho_yz[yz] * ts[g] : real(0);  // h kappa / 4
+      real c[NV], y[NV];
+#pragma unroll
+      for (int j = 0; j < NV; j++) c[j] = tl[j * NU + t][x];
+      dst_apply<real, NV>(c, y);
+#pragma unroll
+      for (int n = 0; n < NV; n++) y[n] *= mode_factor(real(1) - q * tb.lam[n * NU + t]);
+      dst_apply<real, NV>(y, c);
+#pragma unroll
+      for (int j = 0; j < NV; j++) tl[j * NU + t][x] = c[j];
+    }
+    __syncthreads();
+    // back along u
+    if (t < NV) {
+      real r[NU], y[NU];
+#pragma unroll
+      for (int k = 0; k < NU; k++) r[k] = tl[t * NU + k][x];
+      dst_apply<real, NU>(r, y);
+#pragma unroll
+      for (int k = 0; k < NU; k++) tl[t * NU + k][x] = y[k];
+    }
+    fence_proxy_async_smem();  // the generic-proxy writes become visible to the TMA store
+    __syncthreads();
+    if (leader) {
+      tma_store_2d(&map, (int)(tile % ntx) * kTW, (int)stack * NA, tl);
+      bulk_commit();
+      // buffer of tile i + kAngBufs - 1 last held tile i - 1: its store must have read it
+      const long long nt = tile + (kAngBufs - 1) * step;
+      if (nt < ntiles) {
+        bulk_wait_read<1>();
+        const int nb = (int)((i + kAngBufs - 1) % kAngBufs);
+        mbar_arrive_expect_tx(&full[nb], kTileBytes);
+        tma_load_2d(buf[nb], &map, (int)(nt % ntx) * kTW, (int)(nt / ntx) * NA, &full[nb]);
+      }
+    }
+    (void)NT;
+  }
+  if (leader) bulk_wait_all();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// TMA form usable: row pitch nyz * sizeof(real) a multiple of 16 bytes, rows
+// addressable by 32-bit coordinates, and the driver's encoder available.
+template <typename real>
+bool angular_tma_ok(const Dims &d, const real *psi) {
+  const long long rows = (long long)d.ncomp * d.ng * 2 * d.na;
+  return ((d.nyz * sizeof(real)) % 16 == 0) && rows < (1LL << 31) && d.na <= 256 &&
+         (reinterpret_cast<uintptr_t>(psi) % 16 == 0) && encode_fn() != nullptr;
+}
+
+template <typename real, int NU, int NV>
+cudaError_t go_tma(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts, double h,
+                   const AngTables<real> &tb) {
+  constexpr int NA = NU * NV;
+  constexpr int kTW = tile_w<real>();
+  constexpr int NT = NU > NV ? NU : NV;
+  const long long rows = (long long)d.ncomp * d.ng * 2 * NA;
+  CUtensorMap map;
+  cuuint64_t dims[2] = {(cuuint64_t)d.nyz, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)d.nyz * sizeof(real)};
+  cuuint32_t box[2] = {(cuuint32_t)kTW, (cuuint32_t)NA};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&map, sizeof(real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                           2, psi, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const int ntx = (d.nyz + kTW - 1) / kTW;
+  const long long ntiles = rows / NA * ntx;
+  const size_t smem = (size_t)kAngBufs * NA * kTW * sizeof(real);
+  auto kern = k_angular_tma<real, NU, NV>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTW * NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long blocks = (long long)per_sm * lc.num_sms;
+  if (blocks > ntiles) blocks = ntiles;
+  kern<<<(unsigned)blocks, dim3(kTW, NT), smem, lc.stream>>>(map, rho_yz, ts, d.nyz, d.ng, ntx, ntiles,
+                                                               (real)(0.25 * h), tb, lc.err);
+  ++*lc.launches;
+  return cudaGetLastError();
+}
+
 template <typename real>
 void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv) {
   const double pi = 3.14159265358979323846;
@@ -148,6 +455,11 @@ cudaError_t go(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz
                double dv) {
   AngTables<real> tb;
   fill_tables(tb, NU, NV, du, dv);
+  if constexpr (sizeof(real) == 4) {
+    if (lc.angular_form == 2 && (d.nyz % 2) == 0) return go_f2<NU, NV>(lc, d, psi, rho_yz, ts, h, tb);
+  }
+  if (lc.angular_form == 1 && lc.err && angular_tma_ok<real>(d, psi))
+    return go_tma<real, NU, NV>(lc, d, psi, rho_yz, ts, h, tb);
   constexpr int NT = NU > NV ? NU : NV;
   constexpr int kTW = tile_w<real>();
   dim3 block(kTW, NT);
@@ -178,18 +490,22 @@ cudaError_t launch_angular(const LaunchCtx &lc, const Dims &d, real *psi, const 
 }
 
 cudaError_t angular_init_tables() {
-  static float hf[kMaxAngle + 1][kMaxAngle * kMaxAngle];
-  static double hd[kMaxAngle + 1][kMaxAngle * kMaxAngle];
+  static float hf[kDstEntries];
+  static double hd[kDstEntries];
+  static float2 hf2[kDstEntries];
   const double pi = 3.14159265358979323846;
-  for (int n = 1; n <= kMaxAngle; n++)
+  for (int n = 2; n <= kMaxAngle; n += 2)
     for (int m = 0; m < n; m++)
       for (int i = 0; i < n; i++) {
         const double v = std::sqrt(2.0 / (n + 1)) * std::sin(pi * (m + 1) * (i + 1) / (n + 1));
-        hd[n][m * n + i] = v;
-        hf[n][m * n + i] = (float)v;
+        const int at = dst_off(n) + m * n + i;
+        hd[at] = v;
+        hf[at] = (float)v;
+        hf2[at] = make_float2((float)v, (float)v);
       }
   cudaError_t e = cudaMemcpyToSymbol(c_dst_f, hf, sizeof(hf));
   if (e != cudaSuccess) return e;
+  if ((e = cudaMemcpyToSymbol(c_dst_f2, hf2, sizeof(hf2))) != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_dst_d, hd, sizeof(hd));
 }
 

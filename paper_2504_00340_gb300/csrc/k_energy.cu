@@ -240,6 +240,10 @@ template <typename real, typename st>
 cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
                           const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
                           double dose_scale, double flu_scale, const BeamStrides &bs) {
+  if constexpr (sizeof(real) == 4) {
+    if (lc.energy_form == 1 && energy_f2_supported(d))
+      return launch_energy_f2<st>(lc, d, psi_k, ha, hb, coef, flu_yz, dose_scale, flu_scale, bs);
+  }
   const int ay = lc.energy_angles;
   dim3 block(kLanesX, ay);
   dim3 grid((d.nyz + kLanesX - 1) / kLanesX, (d.na + ay - 1) / ay, d.nbeam);
@@ -247,7 +251,7 @@ cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const
   const bool has_src = ha.src != nullptr, has_r = ha.r_out != nullptr;
   const EnergyHalf<real, st> &b = hb ? *hb : ha;
   auto go = [&](auto kern) -> cudaError_t {
-    if (smem > 48 * 1024) {
+    if (smem + sizeof(double) * 3 * 16 * kLanesX > 48 * 1024) {  // dynamic table + static reduction buffer
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }

@@ -53,7 +53,7 @@ struct pbs_ctx {
   size_t rsize, ssize;  // element sizes of real and of the source storage
   long long launches = 0;
   // launch shapes (pbs_autotune / pbs_set_tuning)
-  int tune_energy_angles = 8, tune_transport_ctas = 0;
+  pbs_tuning tune{8, 1, 0, 2};
   // whole-march CUDA graph (pbs_run with use_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -122,8 +122,10 @@ T *at(pbs_ctx *c, size_t off) { return reinterpret_cast<T *>(c->ws + off); }
 
 LaunchCtx lctx(pbs_ctx *c) {
   LaunchCtx lc{c->stream, c->num_sms, &c->launches, at<int>(c, c->off_err)};
-  lc.energy_angles = c->tune_energy_angles;
-  lc.transport_ctas = c->tune_transport_ctas;
+  lc.energy_angles = c->tune.energy_angles;
+  lc.energy_form = c->tune.energy_form;
+  lc.transport_ctas = c->tune.transport_ctas;
+  lc.angular_form = c->tune.angular_form;
   return lc;
 }
 
@@ -669,29 +671,46 @@ pbs_status autotune_impl(pbs_ctx *c, int reps) {
     return PBS_OK;
   };
   const int slab_b = c->n_slabs > 1 ? 1 : 0;
-  float best_e = 1e30f, best_t = 1e30f;
-  int pick_e = c->tune_energy_angles, pick_t = c->tune_transport_ctas;
-  for (int ay : {4, 8, 16}) {
-    c->tune_energy_angles = ay;
-    float ms;
-    r = time_best([&] { return energy_run<real, st>(c, 0.5 * c->dx, 0, slab_b, -1, 0, c->B); }, ms);
+  pbs_tuning pick = c->tune;
+  float best = 1e30f;
+  for (int form : {1, 0}) {
+    if (form == 1 && sizeof(real) != 4) continue;
+    for (int ay : {4, 8, 16}) {
+      c->tune.energy_form = form;
+      c->tune.energy_angles = ay;
+      float ms;
+      r = time_best([&] { return energy_run<real, st>(c, 0.5 * c->dx, 0, slab_b, -1, 0, c->B); }, ms);
+      if (r != PBS_OK) break;
+      if (ms < best) { best = ms; pick.energy_form = form; pick.energy_angles = ay; }
+    }
     if (r != PBS_OK) break;
-    if (ms < best_e) { best_e = ms; pick_e = ay; }
   }
+  c->tune = pick;
+  best = 1e30f;
   if (r == PBS_OK) {
     for (int ctas : {1, 2, 3, 4, 0}) {
-      c->tune_transport_ctas = ctas;
+      c->tune.transport_ctas = ctas;
       float ms;
       r = time_best([&] { return transport_run<real>(c, 0.5 * c->dx, c->B); }, ms);
       if (r != PBS_OK) break;
-      if (ms < best_t) { best_t = ms; pick_t = ctas; }
+      if (ms < best) { best = ms; pick.transport_ctas = ctas; }
+    }
+  }
+  c->tune = pick;
+  best = 1e30f;
+  if (r == PBS_OK) {
+    for (int form : {2, 1, 0}) {
+      c->tune.angular_form = form;
+      float ms;
+      r = time_best([&] { return angular_run<real>(c, c->dx, 0, c->B); }, ms);
+      if (r != PBS_OK) break;
+      if (ms < best) { best = ms; pick.angular_form = form; }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->profiling = prof;
-  c->tune_energy_angles = pick_e;
-  c->tune_transport_ctas = pick_t;
+  c->tune = pick;
   drop_graph(c);
   if (r != PBS_OK) return r;
   if ((r = reinit_impl<real, st>(c)) != PBS_OK) return r;
@@ -875,20 +894,20 @@ pbs_status pbs_autotune(pbs_ctx *c, int reps) {
   return PBS_DISPATCH(c, autotune_impl, c, reps);
 }
 
-pbs_status pbs_set_tuning(pbs_ctx *c, int energy_angles, int transport_ctas) {
-  if (!c) return PBS_ERR_ARG;
-  if ((energy_angles != 4 && energy_angles != 8 && energy_angles != 16) || transport_ctas < 0 || transport_ctas > 64)
-    return fail(c, PBS_ERR_ARG, "energy_angles must be 4, 8 or 16 and transport_ctas in [0, 64]");
-  c->tune_energy_angles = energy_angles;
-  c->tune_transport_ctas = transport_ctas;
+pbs_status pbs_set_tuning(pbs_ctx *c, const pbs_tuning *t) {
+  if (!c || !t) return fail(c, PBS_ERR_ARG, "null tuning");
+  if ((t->energy_angles != 4 && t->energy_angles != 8 && t->energy_angles != 16) || t->energy_form < 0 ||
+      t->energy_form > 1 || t->transport_ctas < 0 || t->transport_ctas > 64 || t->angular_form < 0 ||
+      t->angular_form > 2)
+    return fail(c, PBS_ERR_ARG, "tuning value out of range");
+  c->tune = *t;
   drop_graph(c);
   return PBS_OK;
 }
 
-pbs_status pbs_get_tuning(const pbs_ctx *c, int *energy_angles, int *transport_ctas) {
-  if (!c || !energy_angles || !transport_ctas) return PBS_ERR_ARG;
-  *energy_angles = c->tune_energy_angles;
-  *transport_ctas = c->tune_transport_ctas;
+pbs_status pbs_get_tuning(const pbs_ctx *c, pbs_tuning *t) {
+  if (!c || !t) return PBS_ERR_ARG;
+  *t = c->tune;
   return PBS_OK;
 }
 

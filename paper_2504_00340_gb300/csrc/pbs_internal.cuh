@@ -147,6 +147,10 @@ struct LaunchCtx {
   // launch shapes chosen by the autotuner (pbs_autotune)
   int energy_angles = 8;   // energy: angles per block (4, 8 or 16) x 32 lateral points
   int transport_ctas = 0;  // streaming transport: resident CTAs per SM (0 = as many as fit)
+  int angular_form = 2;    // angular substep: 0 direct, 1 TMA-staged persistent, 2 packed FP32x2
+                           // (forms 1 and 2 where the grid allows, else 0)
+  int energy_form = 1;     // FP32 energy substep: 0 one lane per thread, 1 packed FP32x2
+                           // (form 1 where the grid allows, else 0)
 };
 
 // One E substep's per-lane inputs and outputs: density of its slab, c = h/2,
@@ -167,6 +171,12 @@ struct EnergyHalf {
 struct BeamStrides {
   long long psi, src, dose, flu;
 };
+
+bool energy_f2_supported(const Dims &d);
+template <typename st>
+cudaError_t launch_energy_f2(const LaunchCtx &lc, const Dims &d, float *psi_k, const EnergyHalf<float, st> &ha,
+                             const EnergyHalf<float, st> *hb, const GroupCoef<float> *coef, double *flu_yz,
+                             double dose_scale, double flu_scale, const BeamStrides &bs);
 
 // E substep on one component of every beam; with hb != NULL, two consecutive
 // E substeps (ha then hb) fused in one pass.  flu_yz receives the fluence

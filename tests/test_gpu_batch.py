@@ -143,9 +143,10 @@ def test_graph_rerecords_after_depth_change():
     s.close()
 
 
-def test_autotune_keeps_results():
-    """The tuner picks shapes from its candidate sets, restarts the beams, and
-    every shape gives the same psi (bitwise) and dose (to rounding)."""
+def test_autotune_and_forms_keep_results():
+    """The tuner picks shapes and forms from its candidate sets and restarts
+    the beams.  Shapes within one kernel form give the same psi bit for bit;
+    the packed and TMA forms agree with the plain ones to FP32 rounding."""
     grid = _grid(16, 32, 8, 8, 20)
     nx, dx = 4, 0.05
     rho = np.random.default_rng(6).uniform(0.5, 1.5, size=(nx, 16, 32))
@@ -153,21 +154,33 @@ def test_autotune_keeps_results():
     s.set_material(rho)
     s.launch_beams(BEAMS[:2])
     s.autotune(2)
-    ea, tc = s.tuning
-    assert ea in (4, 8, 16) and tc in (0, 1, 2, 3, 4)
+    t = s.tuning
+    assert t["energy_angles"] in (4, 8, 16) and t["energy_form"] in (0, 1)
+    assert t["transport_ctas"] in (0, 1, 2, 3, 4) and t["angular_form"] in (0, 1, 2)
     assert s.depth == 0
-    out = {}
-    for shape in ((4, 1), (8, 0), (16, 3), (ea, tc)):
-        s.set_tuning(*shape)
+    plain = dict(energy_angles=8, energy_form=0, transport_ctas=0, angular_form=0)
+    shapes = [plain, dict(energy_angles=4, energy_form=0, transport_ctas=1, angular_form=0),
+              dict(energy_angles=16, energy_form=1, transport_ctas=3, angular_form=2),
+              dict(energy_angles=8, energy_form=1, transport_ctas=0, angular_form=1), t]
+    out = []
+    for shape in shapes:
+        s.set_tuning(**shape)
         s.launch_beams(BEAMS[:2])
         s.step(nx)
-        out[shape] = (s.read_dose(), s.read_psi(0), s.read_psi(1))
-    base = out[(8, 0)]
-    for shape, got in out.items():
-        assert np.array_equal(got[1], base[1]) and np.array_equal(got[2], base[2]), shape
-        assert _relerr(got[0], base[0]) < 1e-5, shape
+        out.append((s.read_dose(), s.read_psi(0), s.read_psi(1)))
+    base = out[0]
+    for shape, got in zip(shapes, out):
+        same_forms = shape["energy_form"] == 0 and shape["angular_form"] == 0
+        for j in (1, 2):
+            if same_forms:
+                assert np.array_equal(got[j], base[j]), shape
+            else:
+                assert _relerr(got[j], base[j]) < 2e-5, shape
+        assert _relerr(got[0], base[0]) < 2e-5, shape
     with pytest.raises(binding.PbsError):
-        s.set_tuning(6, 0)
+        s.set_tuning(energy_angles=6)
+    with pytest.raises(binding.PbsError):
+        s.set_tuning(energy_angles=8, angular_form=3)
     s.close()
 
 

@@ -47,18 +47,21 @@ def test_tables_match_oracle(orc):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
-def test_energy_substep_with_source_chain(orc, precision, tol):
-    grid = _grid(6, 7, 4, 4, 37)  # ragged: nyz = 42, 37 groups
+@pytest.mark.parametrize("ny,nz", [(6, 7), (5, 9)])
+def test_energy_substep_with_source_chain(orc, precision, tol, ny, nz):
+    """nyz = 42 (even: the packed FP32 form) and 45 (odd: one lane per
+    thread), 37 groups, components 0..2 chained by their sources."""
+    grid = _grid(ny, nz, 4, 4, 37)
     K = 2
     s, o, rho = _pair(orc, grid, 3, 0.05, K, precision)
-    states = [smooth_state(6, 7, 37, 4, 4, seed=10 + k) for k in range(K + 1)]
+    states = [smooth_state(ny, nz, 37, 4, 4, seed=10 + k) for k in range(K + 1)]
     for k in range(K + 1):
         s.write_psi(k, states[k])
     h, slab = 0.025, 1
     s.substep_energy(h, slab, fluence_plane=2)
     # oracle: components in order, source of k from k-1 at start and end (trapezoid)
     ref = [x.copy() for x in states]
-    edep = np.zeros((6, 7))
+    edep = np.zeros((ny, nz))
     src_sum = None
     for k in range(K + 1):
         src_a = o.source(rho[slab], ref[k]) if k < K else None
@@ -71,8 +74,15 @@ def test_energy_substep_with_source_chain(orc, precision, tol):
     dose = s.read_dose(3)[slab]
     dose_ref = edep / (rho[slab] * 0.05 * 0.1 * 0.1)
     assert _relerr(dose, dose_ref) < 10 * tol
-    flu = s.read_fluence(3)[2] if s.depth >= 2 else None
     s.close()
+    # the fluence plane receives the particle count of the new state of every component
+    s2, _, _ = _pair(orc, grid, 3, 0.05, K, precision)
+    for k in range(K + 1):
+        s2.write_psi(k, states[k])
+    s2.substep_energy(h, slab, fluence_plane=0)
+    flu_ref = sum(o.fluence(ref[k]) for k in range(K + 1))
+    assert _relerr(s2.read_fluence(1)[0], flu_ref) < 10 * tol
+    s2.close()
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
@@ -94,6 +104,25 @@ def test_angular_substep(orc, precision, tol, nu, nv):
     grid = _grid(5, 9, nu, nv, 3)  # nyz = 45: ragged against the 32/16-point tiles
     s, o, rho = _pair(orc, grid, 2, 0.05, 1, precision)
     psi = [random_state((3, 2, nv, nu, 5, 9), seed=7 + k) for k in range(2)]
+    for k in range(2):
+        s.write_psi(k, psi[k])
+    s.substep_angular(3.0, 1)
+    for k in range(2):
+        ref = o.angular_substep(3.0, rho[1], psi[k])
+        assert _relerr(s.read_psi(k), ref) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
+@pytest.mark.parametrize("ny,nz,nu,nv,ng", [(12, 16, 16, 16, 80), (6, 12, 8, 8, 150), (10, 10, 4, 6, 200)])
+def test_angular_substep_tma_pipeline(orc, precision, tol, ny, nz, nu, nv, ng):
+    """The TMA-staged persistent form: row pitch a multiple of 16 bytes, a
+    ragged last lateral tile (72 or 100 points) or full tiles (192), and
+    enough tiles per CTA (two components x 2 ng stacks) that every buffer is
+    reused and every barrier phase flips."""
+    grid = _grid(ny, nz, nu, nv, ng)
+    s, o, rho = _pair(orc, grid, 2, 0.05, 1, precision)
+    psi = [random_state((ng, 2, nv, nu, ny, nz), seed=17 + k) for k in range(2)]
     for k in range(2):
         s.write_psi(k, psi[k])
     s.substep_angular(3.0, 1)
