@@ -175,20 +175,23 @@ __device__ __forceinline__ void dst_apply2(const float2 (&x)[N], float2 (&y)[N])
 }
 
 // As k_angular with each thread on two adjacent lateral points (one 8-byte
-// load per row) and the transforms on FP32x2 pairs; 64 lateral points per
-// CTA.  nyz must be even.
+// load per row) and the transforms on FP32x2 pairs; kF2X threads (2 kF2X
+// lateral points) per slab row, so that a warp covers two rows of 128 bytes
+// and several CTAs fit an SM (one CTA's loads overlap another's transforms).
+// nyz must be even.
+constexpr int kF2X = 16;
 template <int NU, int NV>
-__global__ void __launch_bounds__(32 * (NU > NV ? NU : NV), 1)
+__global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV))
     k_angular_f2(float *__restrict__ psi, const float *__restrict__ rho_yz, const float *__restrict__ ts, int nyz,
                  int ng, float hq, long long kgc0, const __grid_constant__ AngTables<float> tb) {
   constexpr int NA = NU * NV;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2(*tile)[32] = reinterpret_cast<float2(*)[32]>(smem_raw);
+  float2(*tile)[kF2X] = reinterpret_cast<float2(*)[kF2X]>(smem_raw);
   const int x = threadIdx.x;
   const int t = threadIdx.y;
   const long long kgc = kgc0 + blockIdx.y;  // (k * ng + g) * 2 + c
   const int g = (int)((kgc / 2) % ng);
-  const int yz = (blockIdx.x * 32 + x) * 2;
+  const int yz = (blockIdx.x * kF2X + x) * 2;
   const bool active = yz < nyz;
   float *base = psi + kgc * (long long)NA * nyz + yz;
   if (t < NV) {
@@ -239,7 +242,7 @@ template <int NU, int NV>
 cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
                   const AngTables<float> &tb) {
   constexpr int NT = NU > NV ? NU : NV;
-  const size_t smem = sizeof(float2) * NU * NV * 32;
+  const size_t smem = sizeof(float2) * NU * NV * kF2X;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_angular_f2<NU, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -247,9 +250,9 @@ cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *r
   const long long total = (long long)d.ncomp * d.ng * 2;
   for (long long k0 = 0; k0 < total; k0 += 65535) {
     const long long cnt = total - k0 < 65535 ? total - k0 : 65535;
-    dim3 grid((d.nyz / 2 + 31) / 32, (unsigned)cnt);
-    k_angular_f2<NU, NV><<<grid, dim3(32, NT), smem, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng, (float)(0.25 * h),
-                                                                  k0, tb);
+    dim3 grid((d.nyz / 2 + kF2X - 1) / kF2X, (unsigned)cnt);
+    k_angular_f2<NU, NV><<<grid, dim3(kF2X, NT), smem, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng,
+                                                                    (float)(0.25 * h), k0, tb);
     ++*lc.launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -33,11 +33,6 @@ constexpr int kP = 6;        // rows in flight per lane
 constexpr int kR = kP + 1;   // ring slots
 constexpr int kWarps = 4;    // warps per CTA
 
-template <typename real>
-struct V4 {
-  real v[kV];
-};
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, unsigned src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
                : "memory");
@@ -82,15 +77,105 @@ __device__ __forceinline__ real face_value_d(real B, real d1, real d2) {
   return fma(real(0.5), copysign(m, d2), B);
 }
 
-template <typename real, bool VEC>
+// Four columns of one row.  Elementwise arithmetic goes through the helpers
+// below, which issue the packed FP32x2 instructions for float (two columns
+// per instruction) and plain ones for double.
+template <typename real>
+struct V4 {
+  real v[kV];
+};
+
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+
+template <typename real>
+__device__ __forceinline__ V4<real> add4(const V4<real> &a, const V4<real> &b) {
+  V4<real> r;
+#pragma unroll
+  for (int j = 0; j < kV; j++) r.v[j] = a.v[j] + b.v[j];
+  return r;
+}
+template <>
+__device__ __forceinline__ V4<float> add4<float>(const V4<float> &a, const V4<float> &b) {
+  V4<float> r;
+#pragma unroll
+  for (int j = 0; j < kV; j += 2) {
+    const float2 t = __fadd2_rn(pk(a.v[j], a.v[j + 1]), pk(b.v[j], b.v[j + 1]));
+    r.v[j] = t.x;
+    r.v[j + 1] = t.y;
+  }
+  return r;
+}
+// a - b
+template <typename real>
+__device__ __forceinline__ V4<real> sub4(const V4<real> &a, const V4<real> &b) {
+  V4<real> r;
+#pragma unroll
+  for (int j = 0; j < kV; j++) r.v[j] = a.v[j] - b.v[j];
+  return r;
+}
+template <>
+__device__ __forceinline__ V4<float> sub4<float>(const V4<float> &a, const V4<float> &b) {
+  V4<float> r;
+#pragma unroll
+  for (int j = 0; j < kV; j += 2) {
+    const float2 t = __ffma2_rn(pk(b.v[j], b.v[j + 1]), pk(-1.f, -1.f), pk(a.v[j], a.v[j + 1]));
+    r.v[j] = t.x;
+    r.v[j + 1] = t.y;
+  }
+  return r;
+}
+// s * (B + h * sl) with h = 1/2
+template <typename real>
+__device__ __forceinline__ V4<real> face4(real s, const V4<real> &B, const V4<real> &sl) {
+  V4<real> r;
+#pragma unroll
+  for (int j = 0; j < kV; j++) r.v[j] = s * fma(real(0.5), sl.v[j], B.v[j]);
+  return r;
+}
+template <>
+__device__ __forceinline__ V4<float> face4<float>(float s, const V4<float> &B, const V4<float> &sl) {
+  V4<float> r;
+#pragma unroll
+  for (int j = 0; j < kV; j += 2) {
+    const float2 t = __fmul2_rn(pk(s, s), __ffma2_rn(pk(0.5f, 0.5f), pk(sl.v[j], sl.v[j + 1]), pk(B.v[j], B.v[j + 1])));
+    r.v[j] = t.x;
+    r.v[j + 1] = t.y;
+  }
+  return r;
+}
+// a + (b - c) + e
+template <typename real>
+__device__ __forceinline__ V4<real> upd4(const V4<real> &a, const V4<real> &b, const V4<real> &c, const V4<real> &e) {
+  return add4(add4(a, sub4(b, c)), e);
+}
+
+// Superbee slopes of four columns from their differences d1 (behind) and d2
+// (ahead): the packed part (2x, 2|d2|) and the per-column limiter.
+template <typename real>
+__device__ __forceinline__ V4<real> slope4(const V4<real> &d1, const V4<real> &d2) {
+  V4<real> x, x2, t2, r;
+#pragma unroll
+  for (int j = 0; j < kV; j++) x.v[j] = flip_by(d1.v[j], d2.v[j]);
+  x2 = add4(x, x);
+  t2 = add4(d2, d2);
+#pragma unroll
+  for (int j = 0; j < kV; j++) {
+    const real m = max3(real(0), fmin(x2.v[j], fabs(d2.v[j])), fmin(x.v[j], fabs(t2.v[j])));
+    r.v[j] = copysign(m, d2.v[j]);
+  }
+  return r;
+}
+
+// Row I/O in the march frame.  FZ: columns in memory order; otherwise the
+// lane -> column map is mirrored (the row is read and written reversed).
+template <typename real, bool VEC, bool FZ>
 struct RowIO {
   // Copy row `row` of a plane into the lane's ring slot `dst`.  Mirrored
   // VEC rows land in physical order and are reversed on read.
-  static __device__ __forceinline__ void issue(real *dst, const real *plane_base, int row, int nz, int col0, bool fz,
-                                               bool on) {
+  static __device__ __forceinline__ void issue(real *dst, const real *plane_base, int row, int nz, int col0, bool on) {
     const real *rowp = plane_base + (long long)row * nz;
     if (VEC) {
-      const int pc = fz ? col0 : nz - kV - col0;  // physical first column of the lane's chunk
+      const int pc = FZ ? col0 : nz - kV - col0;  // physical first column of the lane's chunk
       const unsigned nb = on ? 16u : 0u;
 #pragma unroll
       for (int k = 0; k < (int)(kV * sizeof(real) / 16); k++)
@@ -100,7 +185,7 @@ struct RowIO {
       for (int k = 0; k < kV; k++) {
         const int q = col0 + k;
         const bool in = on && (q < nz);
-        const int pcol = fz ? q : nz - 1 - q;
+        const int pcol = FZ ? q : nz - 1 - q;
         if (sizeof(real) == 8)
           cp_async8(dst + k, in ? rowp + pcol : plane_base, in ? 8u : 0u);
         else
@@ -108,27 +193,18 @@ struct RowIO {
       }
     }
   }
-  static __device__ __forceinline__ void read(const real *src, bool fz, V4<real> &x) {
-    if (VEC) {
+  static __device__ __forceinline__ void read(const real *src, V4<real> &x) {
 #pragma unroll
-      for (int k = 0; k < kV; k++) {
-        const real a = src[k], b = src[kV - 1 - k];
-        x.v[k] = fz ? a : b;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < kV; k++) x.v[k] = src[k];
-    }
+    for (int k = 0; k < kV; k++) x.v[k] = (VEC && !FZ) ? src[kV - 1 - k] : src[k];
   }
-  static __device__ __forceinline__ void store(real *plane_base, int row, int nz, int col0, bool fz, bool on,
-                                               const V4<real> &x) {
+  static __device__ __forceinline__ void store(real *plane_base, int row, int nz, int col0, bool on, const V4<real> &x) {
     if (!on) return;
     real *rowp = plane_base + (long long)row * nz;
     if (VEC) {
-      const int pc = fz ? col0 : nz - kV - col0;
+      const int pc = FZ ? col0 : nz - kV - col0;
       real y[kV];
 #pragma unroll
-      for (int k = 0; k < kV; k++) y[k] = fz ? x.v[k] : x.v[kV - 1 - k];
+      for (int k = 0; k < kV; k++) y[k] = FZ ? x.v[k] : x.v[kV - 1 - k];
       if (sizeof(real) == 4) {
         *reinterpret_cast<float4 *>(rowp + pc) = make_float4((float)y[0], (float)y[1], (float)y[2], (float)y[3]);
       } else {
@@ -139,45 +215,43 @@ struct RowIO {
 #pragma unroll
       for (int k = 0; k < kV; k++) {
         const int q = col0 + k;
-        if (q < nz) rowp[fz ? q : nz - 1 - q] = x.v[k];
+        if (q < nz) rowp[FZ ? q : nz - 1 - q] = x.v[k];
       }
     }
   }
 };
 
 // z contribution (G_lo - G_hi) h/dz for the lane's 4 cells of one row in the
-// march frame (positive flow).  gz = |v| h / dz.
+// march frame (positive flow).  gz = |v| h / dz.  zl / zr: 0 for the first /
+// last lane of the plane (zero ghosts), else 1.
 template <typename real>
-__device__ __forceinline__ void z_delta(const V4<real> &c, real gz, int li, int lp, int gw, V4<real> &out) {
-  real lft = __shfl_up_sync(0xffffffffu, c.v[kV - 1], 1, gw);  // column 4l-1
-  real rgt = __shfl_down_sync(0xffffffffu, c.v[0], 1, gw);     // column 4l+4
-  if (li == 0) lft = real(0);
-  if (li >= lp - 1) rgt = real(0);
+__device__ __forceinline__ void z_delta(const V4<real> &c, real gz, real zl, real zr, int gw, V4<real> &out) {
+  const real lft = zl * __shfl_up_sync(0xffffffffu, c.v[kV - 1], 1, gw);  // column 4l-1
+  const real rgt = zr * __shfl_down_sync(0xffffffffu, c.v[0], 1, gw);     // column 4l+4
   // right faces 4l+k+1/2 of the lane's cells
-  real g[kV];
-  const real d0 = c.v[0] - lft;
-  const real d1 = c.v[1] - c.v[0];
-  const real d2 = c.v[2] - c.v[1];
-  const real d3 = c.v[3] - c.v[2];
-  const real d4 = rgt - c.v[3];
-  g[0] = gz * face_value_d(c.v[0], d0, d1);
-  g[1] = gz * face_value_d(c.v[1], d1, d2);
-  g[2] = gz * face_value_d(c.v[2], d2, d3);
-  g[3] = gz * face_value_d(c.v[3], d3, d4);
-  real glo = __shfl_up_sync(0xffffffffu, g[kV - 1], 1, gw);  // left face = neighbour's last right face
-  if (li == 0) glo = real(0);                                  // inflow edge: zero ghosts upstream
-  out.v[0] = glo - g[0];
+  V4<real> dl, dr;
+  dl.v[0] = c.v[0] - lft;
+  dr.v[0] = dl.v[1] = c.v[1] - c.v[0];
+  dr.v[1] = dl.v[2] = c.v[2] - c.v[1];
+  dr.v[2] = dl.v[3] = c.v[3] - c.v[2];
+  dr.v[3] = rgt - c.v[3];
+  const V4<real> g = face4(gz, c, slope4(dl, dr));
+  // left face = the left neighbour's last right face; inflow edge: zero ghosts upstream
+  const real glo = zl * __shfl_up_sync(0xffffffffu, g.v[kV - 1], 1, gw);
+  V4<real> gl;
+  gl.v[0] = glo;
 #pragma unroll
-  for (int j = 1; j < kV; j++) out.v[j] = g[j - 1] - g[j];
+  for (int j = 1; j < kV; j++) gl.v[j] = g.v[j - 1];
+  out = sub4(gl, g);
 }
 
-template <typename real, bool VEC>
+template <typename real, bool VEC, bool FZ>
 struct PlaneMarch {
   real *ring;  // this lane's ring base (slot stride 32*kV)
   real *pbase;
-  int ny, nz, col0, li, lp, gw;
-  bool fwd, fz, on;
-  real sy, gz;
+  int ny, nz, col0, gw;
+  bool fwd, on;
+  real sy, gz, zl, zr;
   int rd, wr;
   V4<real> w[4], st[4];  // psi rows i-3..i, psi* rows i-4..i-1 (march order)
   V4<real> f1, f2;       // carried y face fluxes of stage 1 and stage 2
@@ -190,7 +264,7 @@ struct PlaneMarch {
     rd = 0;
 #pragma unroll
     for (int j = 0; j < kP; j++) {
-      if (j < ny) RowIO<real, VEC>::issue(ring + wr * 32 * kV, pbase, prow(j), nz, col0, fz, on);
+      if (j < ny) RowIO<real, VEC, FZ>::issue(ring + wr * 32 * kV, pbase, prow(j), nz, col0, on);
       cp_async_commit();
       wr++;
     }
@@ -208,13 +282,13 @@ struct PlaneMarch {
     cp_async_wait<kP - 1>();
     V4<real> x;
     if (LOAD) {
-      RowIO<real, VEC>::read(ring + rd * 32 * kV, fz, x);
+      RowIO<real, VEC, FZ>::read(ring + rd * 32 * kV, x);
     } else {
 #pragma unroll
       for (int j = 0; j < kV; j++) x.v[j] = real(0);
     }
     rd = (rd + 1 == kR) ? 0 : rd + 1;
-    if (i + kP < ny) RowIO<real, VEC>::issue(ring + wr * 32 * kV, pbase, prow(i + kP), nz, col0, fz, on);
+    if (i + kP < ny) RowIO<real, VEC, FZ>::issue(ring + wr * 32 * kV, pbase, prow(i + kP), nz, col0, on);
     cp_async_commit();
     wr = (wr + 1 == kR) ? 0 : wr + 1;
 #pragma unroll
@@ -223,52 +297,86 @@ struct PlaneMarch {
 
     if (S1) {  // row m = i-1 needs psi(m-2..m+1) = w[0..3]
       if (FIRST1) {
-#pragma unroll
-        for (int j = 0; j < kV; j++) {
-          const real d0 = w[1].v[j] - w[0].v[j];
-          const real d = w[2].v[j] - w[1].v[j];
-          f1.v[j] = sy * face_value_d(w[1].v[j], d0, d);  // face m - 1/2
-          e1.v[j] = d;
-        }
+        const V4<real> d = sub4(w[2], w[1]);
+        f1 = face4(sy, w[1], slope4(sub4(w[1], w[0]), d));  // face m - 1/2
+        e1 = d;
       }
       V4<real> dz, s;
-      z_delta(w[2], gz, li, lp, gw, dz);
+      z_delta(w[2], gz, zl, zr, gw, dz);
+      const V4<real> d = sub4(w[3], w[2]);
+      const V4<real> fh = face4(sy, w[2], slope4(e1, d));  // face m + 1/2
+      e1 = d;
+      s = upd4(w[2], f1, fh, dz);
+      if (!IN1 || !VEC) {
 #pragma unroll
-      for (int j = 0; j < kV; j++) {
-        const real d = w[3].v[j] - w[2].v[j];
-        const real fh = sy * face_value_d(w[2].v[j], e1.v[j], d);  // face m + 1/2
-        e1.v[j] = d;
-        s.v[j] = (IN1 && (VEC || col0 + j < nz)) ? w[2].v[j] + (f1.v[j] - fh) + dz.v[j] : real(0);
-        f1.v[j] = fh;
+        for (int j = 0; j < kV; j++)
+          if (!(IN1 && (VEC || col0 + j < nz))) s.v[j] = real(0);
       }
+      f1 = fh;
 #pragma unroll
       for (int k = 0; k < 3; k++) st[k] = st[k + 1];
       st[3] = s;
     }
     if (S2) {  // row m' = i-2 needs psi*(m'-2..m'+1) = st[0..3] and psi(m') = w[1]
       if (FIRST2) {
-#pragma unroll
-        for (int j = 0; j < kV; j++) {
-          const real d0 = st[1].v[j] - st[0].v[j];
-          const real d = st[2].v[j] - st[1].v[j];
-          f2.v[j] = sy * face_value_d(st[1].v[j], d0, d);
-          e2.v[j] = d;
-        }
+        const V4<real> d = sub4(st[2], st[1]);
+        f2 = face4(sy, st[1], slope4(sub4(st[1], st[0]), d));
+        e2 = d;
       }
       V4<real> dz, o;
-      z_delta(st[2], gz, li, lp, gw, dz);
+      z_delta(st[2], gz, zl, zr, gw, dz);
+      const V4<real> d = sub4(st[3], st[2]);
+      const V4<real> fh = face4(sy, st[2], slope4(e2, d));
+      e2 = d;
+      o = upd4(add4(w[1], st[2]), f2, fh, dz);
 #pragma unroll
-      for (int j = 0; j < kV; j++) {
-        const real d = st[3].v[j] - st[2].v[j];
-        const real fh = sy * face_value_d(st[2].v[j], e2.v[j], d);
-        e2.v[j] = d;
-        o.v[j] = real(0.5) * (w[1].v[j] + st[2].v[j] + (f2.v[j] - fh) + dz.v[j]);
-        f2.v[j] = fh;
-      }
-      RowIO<real, VEC>::store(pbase, prow(i - 2), nz, col0, fz, on, o);
+      for (int j = 0; j < kV; j++) o.v[j] *= real(0.5);
+      f2 = fh;
+      RowIO<real, VEC, FZ>::store(pbase, prow(i - 2), nz, col0, on, o);
+    }
+  }
+
+  __device__ __forceinline__ void run() {
+    prologue();
+    if (ny >= 3) {
+      iter<true, false, false, true, false, false>(0);
+      iter<true, true, true, true, false, false>(1);
+      iter<true, true, false, true, true, true>(2);
+#pragma unroll 4
+      for (int i = 3; i < ny; i++) iter<true, true, false, true, true, false>(i);
+      iter<false, true, false, true, true, false>(ny);
+      iter<false, true, false, false, true, false>(ny + 1);
+    } else if (ny == 2) {
+      iter<true, false, false, true, false, false>(0);
+      iter<true, true, true, true, false, false>(1);
+      iter<false, true, false, true, true, true>(2);
+      iter<false, true, false, false, true, false>(3);
+    } else {  // ny == 1
+      iter<true, false, false, true, false, false>(0);
+      iter<false, true, true, true, false, false>(1);
+      iter<false, true, false, false, true, true>(2);
     }
   }
 };
+
+template <typename real, bool VEC, bool FZ>
+__device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int nz, int col0, int gw, bool fwd,
+                                            bool on, real sy, real gz, real zl, real zr) {
+  PlaneMarch<real, VEC, FZ> pm;
+  pm.ring = ring;
+  pm.pbase = pbase;
+  pm.ny = ny;
+  pm.nz = nz;
+  pm.col0 = col0;
+  pm.gw = gw;
+  pm.fwd = fwd;
+  pm.on = on;
+  pm.sy = sy;
+  pm.gz = gz;
+  pm.zl = zl;
+  pm.zr = zr;
+  pm.run();
+}
 
 template <typename real, bool VEC>
 __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict__ psi, long long nplanes, int ny, int nz,
@@ -281,48 +389,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
   const int gi = lane / gw;
   const long long gwarp = (long long)blockIdx.x * kWarps + warp;
   const long long nwarps = (long long)gridDim.x * kWarps;
-
-  PlaneMarch<real, VEC> pm;
-  pm.ring = reinterpret_cast<real *>(smem_raw) + ((size_t)warp * kR * 32 + lane) * kV;
-  pm.ny = ny;
-  pm.nz = nz;
-  pm.li = lane % gw;
-  pm.col0 = pm.li * kV;
-  pm.lp = lp;
-  pm.gw = gw;
-  const bool lane_on = pm.li < lp;
+  real *ring = reinterpret_cast<real *>(smem_raw) + ((size_t)warp * kR * 32 + lane) * kV;
+  const int li = lane % gw;
+  const int col0 = li * kV;
+  const bool lane_on = li < lp;
+  const real zl = li == 0 ? real(0) : real(1);
+  const real zr = li >= lp - 1 ? real(0) : real(1);
 
   for (long long base = gwarp * ngroups; base < nplanes; base += nwarps * ngroups) {
     const long long plane = base + gi;
     const bool valid = plane < nplanes;
-    pm.on = valid && lane_on;
     const int a = valid ? (int)(plane % na) : 0;
     const real uu = (real)((a % nu) - 0.5 * (nu - 1)) * du;
     const real vv = (real)((a / nu) - 0.5 * (nv - 1)) * dv;
-    pm.fwd = uu >= real(0);
-    pm.fz = vv >= real(0);
-    pm.sy = fabs(uu) * ky;
-    pm.gz = fabs(vv) * kz;
-    pm.pbase = psi + (valid ? plane : 0) * (long long)ny * nz;
-    pm.prologue();
-    if (ny >= 3) {
-      pm.template iter<true, false, false, true, false, false>(0);
-      pm.template iter<true, true, true, true, false, false>(1);
-      pm.template iter<true, true, false, true, true, true>(2);
-#pragma unroll 4
-      for (int i = 3; i < ny; i++) pm.template iter<true, true, false, true, true, false>(i);
-      pm.template iter<false, true, false, true, true, false>(ny);
-      pm.template iter<false, true, false, false, true, false>(ny + 1);
-    } else if (ny == 2) {
-      pm.template iter<true, false, false, true, false, false>(0);
-      pm.template iter<true, true, true, true, false, false>(1);
-      pm.template iter<false, true, false, true, true, true>(2);
-      pm.template iter<false, true, false, false, true, false>(3);
-    } else {  // ny == 1
-      pm.template iter<true, false, false, true, false, false>(0);
-      pm.template iter<false, true, true, true, false, false>(1);
-      pm.template iter<false, true, false, false, true, true>(2);
-    }
+    real *pbase = psi + (valid ? plane : 0) * (long long)ny * nz;
+    // both branches are taken only when the lane groups of a warp hold planes of opposite v
+    if (vv >= real(0))
+      march_plane<real, VEC, true>(ring, pbase, ny, nz, col0, gw, uu >= real(0), valid && lane_on, fabs(uu) * ky,
+                                   fabs(vv) * kz, zl, zr);
+    else
+      march_plane<real, VEC, false>(ring, pbase, ny, nz, col0, gw, uu >= real(0), valid && lane_on, fabs(uu) * ky,
+                                    fabs(vv) * kz, zl, zr);
   }
   cp_async_wait<0>();
 }
