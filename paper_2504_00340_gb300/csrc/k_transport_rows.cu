@@ -378,10 +378,13 @@ __device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int
   pm.run();
 }
 
-template <typename real, bool VEC>
+// Planes of one mirror class: FZ = the angles with v >= 0 (a >= a0, na_half
+// of them per stack), else those with v < 0 (a < a0).  The two classes run as
+// two launches so that each kernel holds one copy of the unrolled march.
+template <typename real, bool VEC, bool FZ>
 __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict__ psi, long long nplanes, int ny, int nz,
-                                                                int na, int nu, int nv, real du, real dv, real ky,
-                                                                real kz, int lp, int gw) {
+                                                                int na, int a0, int na_half, int nu, int nv, real du,
+                                                                real dv, real ky, real kz, int lp, int gw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -397,19 +400,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
   const real zr = li >= lp - 1 ? real(0) : real(1);
 
   for (long long base = gwarp * ngroups; base < nplanes; base += nwarps * ngroups) {
-    const long long plane = base + gi;
-    const bool valid = plane < nplanes;
-    const int a = valid ? (int)(plane % na) : 0;
+    const long long idx = base + gi;  // plane of this class
+    const bool valid = idx < nplanes;
+    const long long stack = valid ? idx / na_half : 0;
+    const int a = valid ? a0 + (int)(idx - stack * na_half) : a0;
+    const long long plane = stack * na + a;
     const real uu = (real)((a % nu) - 0.5 * (nu - 1)) * du;
     const real vv = (real)((a / nu) - 0.5 * (nv - 1)) * dv;
-    real *pbase = psi + (valid ? plane : 0) * (long long)ny * nz;
-    // both branches are taken only when the lane groups of a warp hold planes of opposite v
-    if (vv >= real(0))
-      march_plane<real, VEC, true>(ring, pbase, ny, nz, col0, gw, uu >= real(0), valid && lane_on, fabs(uu) * ky,
-                                   fabs(vv) * kz, zl, zr);
-    else
-      march_plane<real, VEC, false>(ring, pbase, ny, nz, col0, gw, uu >= real(0), valid && lane_on, fabs(uu) * ky,
-                                    fabs(vv) * kz, zl, zr);
+    real *pbase = psi + plane * (long long)ny * nz;
+    march_plane<real, VEC, FZ>(ring, pbase, ny, nz, col0, gw, uu >= real(0), valid && lane_on, fabs(uu) * ky,
+                               fabs(vv) * kz, zl, zr);
   }
   cp_async_wait<0>();
 }
@@ -421,26 +421,38 @@ bool transport_rows_supported(int nz) { return nz >= 1 && nz <= 32 * kV; }
 template <typename real>
 cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
                                   double dy, double dz) {
-  const long long nplanes = (long long)d.ncomp * d.ng * 2 * d.na;
+  const long long nstacks = (long long)d.ncomp * d.ng * 2;
+  // angles with v >= 0 (rows j >= nv / 2; for odd nv the middle row has v = 0)
+  const int a_split = (d.nv / 2) * d.nu;
   const int lp = (d.nz + kV - 1) / kV;
   int gw = 1;
   while (gw < lp) gw <<= 1;
   const bool vec = (d.nz % kV) == 0;
   const size_t smem = (size_t)kWarps * kR * 32 * kV * sizeof(real);
-  auto kern = vec ? k_transport_rows<real, true> : k_transport_rows<real, false>;
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  if (lc.transport_ctas > 0 && lc.transport_ctas < per_sm) per_sm = lc.transport_ctas;
-  const long long groups_per_block = (long long)kWarps * (32 / gw);
-  long long blocks = (long long)per_sm * lc.num_sms;
-  const long long need = (nplanes + groups_per_block - 1) / groups_per_block;
-  if (blocks > need) blocks = need;
-  kern<<<(unsigned)blocks, kWarps * 32, smem, lc.stream>>>(psi, nplanes, d.ny, d.nz, d.na, d.nu, d.nv, (real)du,
-                                                          (real)dv, (real)(tau / dy), (real)(tau / dz), lp, gw);
-  ++*lc.launches;
-  return cudaGetLastError();
+  for (int half = 0; half < 2; half++) {
+    const bool fz = half == 1;
+    const int a0 = fz ? a_split : 0;
+    const int na_half = fz ? d.na - a_split : a_split;
+    if (na_half == 0) continue;
+    const long long nplanes = nstacks * na_half;
+    auto kern = vec ? (fz ? k_transport_rows<real, true, true> : k_transport_rows<real, true, false>)
+                    : (fz ? k_transport_rows<real, false, true> : k_transport_rows<real, false, false>);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (lc.transport_ctas > 0 && lc.transport_ctas < per_sm) per_sm = lc.transport_ctas;
+    const long long groups_per_block = (long long)kWarps * (32 / gw);
+    long long blocks = (long long)per_sm * lc.num_sms;
+    const long long need = (nplanes + groups_per_block - 1) / groups_per_block;
+    if (blocks > need) blocks = need;
+    kern<<<(unsigned)blocks, kWarps * 32, smem, lc.stream>>>(psi, nplanes, d.ny, d.nz, d.na, a0, na_half, d.nu, d.nv,
+                                                            (real)du, (real)dv, (real)(tau / dy), (real)(tau / dz), lp,
+                                                            gw);
+    ++*lc.launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template cudaError_t launch_transport_rows<double>(const LaunchCtx &, const Dims &, double *, double, double, double,
