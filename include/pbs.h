@@ -136,6 +136,21 @@ pbs_status pbs_bind_workspace(pbs_ctx *ctx, void *dev_ptr, size_t bytes);
  * removal cross section, P^1 decay factors, P^2 matrices). */
 pbs_status pbs_set_physics(pbs_ctx *ctx, const pbs_physics *phys);
 
+/* Caller-supplied tables instead of the built-in physics (e.g. tabulated
+ * stopping powers): s_face[ng+1] mass stopping power at the group faces
+ * (MeV cm^2/g, > 0), ts[ng] group-averaged scattering power (rad^2 cm^2/g,
+ * >= 0: d<u^2>/dx per unit density, the rho sigma_tr of Eq. 0041-d),
+ * sig_ct[ng] catastrophic removal cross section of each emitting group
+ * (cm^2/g, >= 0), lambda_p1 (1/MeV, > 0) the rate of the exponential energy
+ * transfer P^1 (Appendix A.4; normalised to sum 1 over the receiving groups),
+ * and p2[ng*na*na] ([g][a][a'], the outgoing-angle density, normalised by
+ * the caller) or NULL to keep the P^2 of the previous pbs_set_physics /
+ * pbs_set_tables call.  Host arrays, copied during the call.  PBS_ERR_ARG
+ * for a value out of range; PBS_ERR_STATE for p2 = NULL with n_scatter > 0
+ * and no previous P^2. */
+pbs_status pbs_set_tables(pbs_ctx *ctx, const double *s_face, const double *ts, const double *sig_ct,
+                          double lambda_p1, const double *p2);
+
 /* Copy the FP64 host tables out (any pointer may be NULL):
  * s_face[ng+1] (MeV cm^2/g), ts[ng] (rad^2 cm^2/g), sig[ng] (cm^2/g),
  * p1[ng*ng] ([g'][g], probability g' -> g), p2[ng*na*na] ([g][a][a'],

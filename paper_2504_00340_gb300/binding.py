@@ -64,6 +64,7 @@ SIGNATURES = [
     ("pbs_workspace_size", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
     ("pbs_bind_workspace", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("pbs_set_physics", ctypes.c_int, [_VP, ctypes.POINTER(PbsPhysics)]),
+    ("pbs_set_tables", ctypes.c_int, [_VP, _D, _D, _D, ctypes.c_double, _D]),
     ("pbs_get_tables", ctypes.c_int, [_VP, _D, _D, _D, _D, _D, _D, _D]),
     ("pbs_set_material", ctypes.c_int, [_VP, _D, ctypes.c_int]),
     ("pbs_launch_beam", ctypes.c_int, [_VP, ctypes.POINTER(PbsBeam)]),
@@ -157,6 +158,11 @@ def pbs_bind_workspace(ctx, dev_ptr: int, nbytes: int) -> None:
 
 def pbs_set_physics(ctx, phys: PbsPhysics) -> None:
     _check(ctx, load_library().pbs_set_physics(_VP(ctx), ctypes.byref(phys)))
+
+
+def pbs_set_tables(ctx, s_face, ts, sig_ct, lambda_p1: float, p2=None) -> None:
+    _check(ctx, load_library().pbs_set_tables(_VP(ctx), _ptr(s_face), _ptr(ts), _ptr(sig_ct), float(lambda_p1),
+                                              _ptr(p2)))
 
 
 def pbs_get_tables(ctx, s_face, ts, sig, p1, p2, u, v) -> None:
@@ -347,6 +353,12 @@ class Solver:
         p = dict(DEFAULT_PHYSICS)
         p.update(kw)
         pbs_set_physics(self.ctx, PbsPhysics(**p))
+
+    def set_tables(self, s_face, ts, sig_ct, lambda_p1: float, p2=None):
+        """Caller-supplied tables (see pbs_set_tables): s_face[ng+1], ts[ng],
+        sig_ct[ng], lambda_p1, optional p2[ng][na][na]."""
+        f = lambda x: None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float64))  # noqa: E731
+        pbs_set_tables(self.ctx, f(s_face), f(ts), f(sig_ct), lambda_p1, f(p2))
 
     def tables(self) -> dict:
         G, na = self.ng, self.na

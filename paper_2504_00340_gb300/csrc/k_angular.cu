@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
       // a copy never arrived: record it, let the copies in flight land, stop
       if (leader) {
         atomicAdd(err, 1);
-        err[1] = 3;
+        err[1] = kErrTimeoutAngular;
         for (int j = 1; j < kAngBufs; j++) {
           const long long ti = tile + j * step;
           if (ti < ntiles && j < kAngBufs - 1)

@@ -1,12 +1,12 @@
 // k_transport_rows.cu -- lateral transport substep T(h) (Section 3.4, Eq.
-// distansport, Remark 3), warp-per-plane streaming form for nz <= 128.
+// distansport, Remark 3), warp-per-plane streaming form.
 //
-// Same scheme as the tiled kernel in k_transport.cu: flux-limited upwind
-// finite volumes with the superbee slope, zero ghost cells, and the explicit
-// trapezoid in depth  psi* = psi + h L(psi),  psi_new = (psi + psi* + h L(psi*))/2.
+// Flux-limited upwind finite volumes with the superbee slope, zero ghost
+// cells, and the explicit trapezoid in depth  psi* = psi + h L(psi),  psi_new = (psi + psi* + h L(psi*))/2.
 //
 // GB300 design.  A group of lanes owns one (component, g, c, u, v) plane; each
-// lane owns 4 adjacent z columns, so one row of up to 128 columns is one warp.
+// lane owns 4 adjacent z columns, so one row of up to 128 columns is one warp
+// (wider rows are cut into segments with one halo lane per inner side).
 //   * The scheme is symmetric under y -> -y and z -> -z, so each plane is
 //     processed in a "march frame" in which both speeds are >= 0: rows are
 //     visited from the last to the first when u < 0, and the lane -> column
@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kV = 4;        // columns per lane
 constexpr int kP = 6;        // rows in flight per lane
-constexpr int kR = kP + 1;   // ring slots
+constexpr int kR = 8;        // ring slots (a power of two >= kP + 1: slot indices wrap by a mask)
 constexpr int kWarps = 4;    // warps per CTA
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, unsigned src_bytes) {
@@ -249,10 +249,57 @@ template <typename real, bool VEC, bool FZ>
 struct PlaneMarch {
   real *ring;  // this lane's ring base (slot stride 32*kV)
   real *pbase;
-  int ny, nz, col0, gw;
-  bool fwd, on;
+  int ny, nz, col0, gw;  // col0: the lane's first column in the march frame
+  bool fwd, on, own;     // on: the lane's columns are loaded; own: they are stored
   real sy, gz, zl, zr;
   int rd, wr;
+  // VEC rows: the lane's first physical column of march row m sits at
+  // lrow0 + m * lstep (loads; a lane that is off re-reads its own plane base
+  // with zero fill: lstep = 0) and srow0 + m * sstep (stores)
+  const real *lrow0;
+  real *srow0;
+  long long lstep, sstep;
+  unsigned nbytes;
+
+  __device__ __forceinline__ void setup_rows() {
+    if (VEC) {
+      const int pc = FZ ? col0 : nz - kV - col0;
+      const long long r0 = fwd ? 0 : (long long)(ny - 1) * nz;
+      const long long st = fwd ? nz : -(long long)nz;
+      srow0 = pbase + r0 + pc;
+      sstep = st;
+      lrow0 = on ? srow0 : pbase;
+      lstep = on ? st : 0;
+      nbytes = on ? 16u : 0u;
+    }
+  }
+  __device__ __forceinline__ void issue_row(real *dst, int m) {
+    if (VEC) {
+      const real *src = lrow0 + m * lstep;
+#pragma unroll
+      for (int k = 0; k < (int)(kV * sizeof(real) / 16); k++)
+        cp_async16(dst + k * (16 / sizeof(real)), src + k * (16 / sizeof(real)), nbytes);
+    } else {
+      RowIO<real, VEC, FZ>::issue(dst, pbase, prow(m), nz, col0, on);
+    }
+  }
+  __device__ __forceinline__ void store_row(int m, const V4<real> &x) {
+    if (VEC) {
+      if (!own) return;
+      real *dst = srow0 + m * sstep;
+      real y[kV];
+#pragma unroll
+      for (int k = 0; k < kV; k++) y[k] = FZ ? x.v[k] : x.v[kV - 1 - k];
+      if (sizeof(real) == 4) {
+        *reinterpret_cast<float4 *>(dst) = make_float4((float)y[0], (float)y[1], (float)y[2], (float)y[3]);
+      } else {
+        reinterpret_cast<double2 *>(dst)[0] = make_double2((double)y[0], (double)y[1]);
+        reinterpret_cast<double2 *>(dst)[1] = make_double2((double)y[2], (double)y[3]);
+      }
+    } else {
+      RowIO<real, VEC, FZ>::store(pbase, prow(m), nz, col0, own, x);
+    }
+  }
   V4<real> w[4], st[4];  // psi rows i-3..i, psi* rows i-4..i-1 (march order)
   V4<real> f1, f2;       // carried y face fluxes of stage 1 and stage 2
   V4<real> e1, e2;       // carried y differences of stage 1 and stage 2
@@ -260,11 +307,12 @@ struct PlaneMarch {
   __device__ __forceinline__ int prow(int m) const { return fwd ? m : ny - 1 - m; }
 
   __device__ __forceinline__ void prologue() {
+    setup_rows();
     wr = 0;
     rd = 0;
 #pragma unroll
     for (int j = 0; j < kP; j++) {
-      if (j < ny) RowIO<real, VEC, FZ>::issue(ring + wr * 32 * kV, pbase, prow(j), nz, col0, on);
+      if (j < ny) issue_row(ring + wr * 32 * kV, j);
       cp_async_commit();
       wr++;
     }
@@ -287,10 +335,10 @@ struct PlaneMarch {
 #pragma unroll
       for (int j = 0; j < kV; j++) x.v[j] = real(0);
     }
-    rd = (rd + 1 == kR) ? 0 : rd + 1;
-    if (i + kP < ny) RowIO<real, VEC, FZ>::issue(ring + wr * 32 * kV, pbase, prow(i + kP), nz, col0, on);
+    rd = (rd + 1) & (kR - 1);
+    if (i + kP < ny) issue_row(ring + wr * 32 * kV, i + kP);
     cp_async_commit();
-    wr = (wr + 1 == kR) ? 0 : wr + 1;
+    wr = (wr + 1) & (kR - 1);
 #pragma unroll
     for (int k = 0; k < 3; k++) w[k] = w[k + 1];
     w[3] = x;
@@ -332,7 +380,7 @@ struct PlaneMarch {
 #pragma unroll
       for (int j = 0; j < kV; j++) o.v[j] *= real(0.5);
       f2 = fh;
-      RowIO<real, VEC, FZ>::store(pbase, prow(i - 2), nz, col0, on, o);
+      store_row(i - 2, o);
     }
   }
 
@@ -361,7 +409,7 @@ struct PlaneMarch {
 
 template <typename real, bool VEC, bool FZ>
 __device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int nz, int col0, int gw, bool fwd,
-                                            bool on, real sy, real gz, real zl, real zr) {
+                                            bool on, bool own, real sy, real gz, real zl, real zr) {
   PlaneMarch<real, VEC, FZ> pm;
   pm.ring = ring;
   pm.pbase = pbase;
@@ -371,6 +419,7 @@ __device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int
   pm.gw = gw;
   pm.fwd = fwd;
   pm.on = on;
+  pm.own = own;
   pm.sy = sy;
   pm.gz = gz;
   pm.zl = zl;
@@ -381,10 +430,17 @@ __device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int
 // Planes of one mirror class: FZ = the angles with v >= 0 (a >= a0, na_half
 // of them per stack), else those with v < 0 (a < a0).  The two classes run as
 // two launches so that each kernel holds one copy of the unrolled march.
+//
+// Rows wider than one warp's 32 lanes x 4 columns are cut into nseg segments
+// of seg_w owned columns (march frame).  A segment's lane group also loads one
+// lane of 4 columns on each inner side: the two Heun stages reach 4 columns
+// upstream and 2 downstream, so the owned columns come out exact while the halo
+// lanes' own results (their outer neighbours are missing) are discarded.  A
+// task is one (plane, segment).
 template <typename real, bool VEC, bool FZ>
 __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict__ psi, long long nplanes, int ny, int nz,
                                                                 int na, int a0, int na_half, int nu, int nv, real du,
-                                                                real dv, real ky, real kz, int lp, int gw) {
+                                                                real dv, real ky, real kz, int nseg, int seg_w, int gw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -394,29 +450,52 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
   const long long nwarps = (long long)gridDim.x * kWarps;
   real *ring = reinterpret_cast<real *>(smem_raw) + ((size_t)warp * kR * 32 + lane) * kV;
   const int li = lane % gw;
-  const int col0 = li * kV;
-  const bool lane_on = li < lp;
-  const real zl = li == 0 ? real(0) : real(1);
-  const real zr = li >= lp - 1 ? real(0) : real(1);
+  const long long ntasks = nplanes * nseg;
 
-  for (long long base = gwarp * ngroups; base < nplanes; base += nwarps * ngroups) {
-    const long long idx = base + gi;  // plane of this class
-    const bool valid = idx < nplanes;
-    const long long stack = valid ? idx / na_half : 0;
-    const int a = valid ? a0 + (int)(idx - stack * na_half) : a0;
+  for (long long base = gwarp * ngroups; base < ntasks; base += nwarps * ngroups) {
+    const long long task = base + gi;
+    const bool valid = task < ntasks;
+    const long long idx = valid ? task / nseg : 0;  // plane of this class
+    const int seg = valid ? (int)(task - idx * nseg) : 0;
+    const long long stack = idx / na_half;
+    const int a = a0 + (int)(idx - stack * na_half);
     const long long plane = stack * na + a;
+    // owned columns [s0, s1), loaded columns [s0 - left halo, hi)
+    const int s0 = seg * seg_w;
+    const int s1 = min(nz, s0 + seg_w);
+    const int c_lo = seg > 0 ? s0 - kV : 0;
+    const int hi = seg < nseg - 1 ? min(nz, s1 + kV) : nz;
+    const int lp = (hi - c_lo + kV - 1) / kV;  // lanes of this segment
+    const int col0 = c_lo + li * kV;
+    const bool on = valid && li < lp;
+    const bool own = on && col0 >= s0 && col0 < s1;
+    const real zl = li == 0 ? real(0) : real(1);
+    const real zr = li >= lp - 1 ? real(0) : real(1);
     const real uu = (real)((a % nu) - 0.5 * (nu - 1)) * du;
     const real vv = (real)((a / nu) - 0.5 * (nv - 1)) * dv;
     real *pbase = psi + plane * (long long)ny * nz;
-    march_plane<real, VEC, FZ>(ring, pbase, ny, nz, col0, gw, uu >= real(0), valid && lane_on, fabs(uu) * ky,
+    march_plane<real, VEC, FZ>(ring, pbase, ny, nz, col0, gw, uu >= real(0), on, own, fabs(uu) * ky,
                                fabs(vv) * kz, zl, zr);
   }
   cp_async_wait<0>();
 }
 
-}  // namespace
+// Segments of a row of nz columns: one if it fits a warp, else segments of at
+// most 120 owned columns (with both halo lanes, 32 lanes).
+void row_segments(int nz, int &nseg, int &seg_w, int &lanes) {
+  if (nz <= 32 * kV) {
+    nseg = 1;
+    seg_w = nz;
+    lanes = (nz + kV - 1) / kV;
+    return;
+  }
+  const int wmax = (32 - 2) * kV;
+  nseg = (nz + wmax - 1) / wmax;
+  seg_w = ((nz + nseg - 1) / nseg + kV - 1) / kV * kV;
+  lanes = seg_w / kV + 2;
+}
 
-bool transport_rows_supported(int nz) { return nz >= 1 && nz <= 32 * kV; }
+}  // namespace
 
 template <typename real>
 cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
@@ -424,7 +503,8 @@ cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi,
   const long long nstacks = (long long)d.ncomp * d.ng * 2;
   // angles with v >= 0 (rows j >= nv / 2; for odd nv the middle row has v = 0)
   const int a_split = (d.nv / 2) * d.nu;
-  const int lp = (d.nz + kV - 1) / kV;
+  int nseg, seg_w, lp;
+  row_segments(d.nz, nseg, seg_w, lp);
   int gw = 1;
   while (gw < lp) gw <<= 1;
   const bool vec = (d.nz % kV) == 0;
@@ -444,11 +524,11 @@ cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi,
     if (lc.transport_ctas > 0 && lc.transport_ctas < per_sm) per_sm = lc.transport_ctas;
     const long long groups_per_block = (long long)kWarps * (32 / gw);
     long long blocks = (long long)per_sm * lc.num_sms;
-    const long long need = (nplanes + groups_per_block - 1) / groups_per_block;
+    const long long need = (nplanes * nseg + groups_per_block - 1) / groups_per_block;
     if (blocks > need) blocks = need;
     kern<<<(unsigned)blocks, kWarps * 32, smem, lc.stream>>>(psi, nplanes, d.ny, d.nz, d.na, a0, na_half, d.nu, d.nv,
-                                                            (real)du, (real)dv, (real)(tau / dy), (real)(tau / dz), lp,
-                                                            gw);
+                                                            (real)du, (real)dv, (real)(tau / dy), (real)(tau / dz), nseg,
+                                                            seg_w, gw);
     ++*lc.launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -221,14 +221,29 @@ double gamma_density(double th, double al, double be) {
   return std::exp(al * std::log(be) + (al - 1.0) * std::log(th) - be * th - std::lgamma(al));
 }
 
+// Exponential energy transfer P^1(g' -> g) = lambda e^{-lambda (E_g' - E_g)},
+// normalised per emitting group g', and the source weights of the fused
+// recursion (q1 = lambda sigma_g' dE_g' / Z_g', decay = e^{-lambda (E_g+1 - E_g)}),
+// from the removal cross sections already in c->sig.
+void transfer_tables(pbs_ctx *c, double lambda) {
+  const int G = c->ng;
+  c->p1.assign((size_t)G * G, 0.0);
+  c->q1.assign(G, 0.0);
+  c->decay.assign(G, 0.0);
+  for (int gp = 0; gp < G; gp++) {
+    double z = 0.0;
+    for (int g = gp; g >= 0; g--) z += lambda * std::exp(-lambda * (c->e_c[gp] - c->e_c[g]));
+    for (int g = 0; g <= gp; g++) c->p1[(size_t)gp * G + g] = lambda * std::exp(-lambda * (c->e_c[gp] - c->e_c[g])) / z;
+    c->q1[gp] = lambda * c->sig[gp] * c->de[gp] / z;
+    c->decay[gp] = (gp + 1 < G) ? std::exp(-lambda * (c->e_c[gp + 1] - c->e_c[gp])) : 0.0;
+  }
+}
+
 void build_tables(pbs_ctx *c, const pbs_physics &ph) {
   const int G = c->ng, na = c->na;
   c->s_face.assign(G + 1, 0.0);
   c->ts.assign(G, 0.0);
   c->sig.assign(G, ph.sigma_ct);
-  c->p1.assign((size_t)G * G, 0.0);
-  c->q1.assign(G, 0.0);
-  c->decay.assign(G, 0.0);
   // a face at E <= 0 takes the stopping power at half the lowest group width
   const double floor_e = 0.5 * c->de[0];
   for (int f = 0; f <= G; f++) c->s_face[f] = stopping_bk(ph, std::max(c->e_faces[f], floor_e));
@@ -236,15 +251,7 @@ void build_tables(pbs_ctx *c, const pbs_physics &ph) {
     const double lo = std::max(c->e_faces[g], floor_e), hi = c->e_faces[g + 1];
     c->ts[g] = ph.ts_scale * (highland_primitive(ph, hi) - highland_primitive(ph, lo)) / (hi - lo);
   }
-  // exponential energy transfer, normalised per emitting group g'
-  for (int gp = 0; gp < G; gp++) {
-    double z = 0.0;
-    for (int g = gp; g >= 0; g--) z += ph.lambda_p1 * std::exp(-ph.lambda_p1 * (c->e_c[gp] - c->e_c[g]));
-    for (int g = 0; g <= gp; g++)
-      c->p1[(size_t)gp * G + g] = ph.lambda_p1 * std::exp(-ph.lambda_p1 * (c->e_c[gp] - c->e_c[g])) / z;
-    c->q1[gp] = ph.lambda_p1 * ph.sigma_ct * c->de[gp] / z;
-    c->decay[gp] = (gp + 1 < G) ? std::exp(-ph.lambda_p1 * (c->e_c[gp + 1] - c->e_c[gp])) : 0.0;
-  }
+  transfer_tables(c, ph.lambda_p1);
   // angular transfer: Gamma density of the angle between (1,u',v') and (1,u,v),
   // normalised so that sum_a P2 du dv = 1 for every incoming a'
   c->p2.assign((size_t)G * na * na, 0.0);
@@ -414,11 +421,7 @@ pbs_status transport_run(pbs_ctx *c, double h, int nb) {
   if (nb <= 0) return PBS_OK;
   const Dims d = dims_for(c, nb);
   ProfScope ps(c, PBS_KERNEL_TRANSPORT);
-  cudaError_t e =
-      transport_rows_supported(c->nz)
-          ? launch_transport_rows<real>(lctx(c), d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz)
-          : launch_transport<real>(lctx(c), d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz,
-                                   at<int>(c, c->off_err));
+  cudaError_t e = launch_transport_rows<real>(lctx(c), d, at<real>(c, c->off_psi), h, c->du, c->dv, c->dy, c->dz);
   return e == cudaSuccess ? PBS_OK : cuda_fail(c, e, "transport kernel");
 }
 
@@ -489,8 +492,10 @@ pbs_status step_impl(pbs_ctx *c, int n) {
 template <typename real, typename st>
 pbs_status reinit_impl(pbs_ctx *c) {
   const size_t nyz = (size_t)c->ny * c->nz;
-  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_psi), 0, (size_t)c->d.ncomp * c->d.comp_elems * sizeof(real),
-                              c->stream));
+  // the projection overwrites every primary component; only scattered ones need zeroing
+  if (c->K > 0)
+    PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_psi), 0, (size_t)c->d.ncomp * c->d.comp_elems * sizeof(real),
+                                c->stream));
   PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_dose), 0, (size_t)c->B * c->nx * nyz * 8, c->stream));
   PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_flu), 0, (size_t)c->B * (c->nx + 1) * nyz * 8, c->stream));
   PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_err), 0, 64, c->stream));
@@ -815,6 +820,35 @@ pbs_status pbs_set_physics(pbs_ctx *c, const pbs_physics *ph) {
     return fail(c, PBS_ERR_ARG, "physics parameters out of range");
   build_tables(c, *ph);
   c->have_tables = true;
+  if (!c->ws) return PBS_OK;  // uploaded at bind time
+  return PBS_DISPATCH(c, upload_tables, c);
+}
+
+pbs_status pbs_set_tables(pbs_ctx *c, const double *s_face, const double *ts, const double *sig_ct, double lambda_p1,
+                          const double *p2) {
+  if (!c || !s_face || !ts || !sig_ct) return fail(c, PBS_ERR_ARG, "null table");
+  const int G = c->ng;
+  if (!(lambda_p1 > 0) || !std::isfinite(lambda_p1)) return fail(c, PBS_ERR_ARG, "lambda_p1 must be > 0");
+  for (int f = 0; f <= G; f++)
+    if (!(s_face[f] > 0) || !std::isfinite(s_face[f])) return fail(c, PBS_ERR_ARG, "s_face must be finite and > 0");
+  for (int g = 0; g < G; g++)
+    if (!(ts[g] >= 0) || !(sig_ct[g] >= 0) || !std::isfinite(ts[g]) || !std::isfinite(sig_ct[g]))
+      return fail(c, PBS_ERR_ARG, "ts and sig_ct must be finite and >= 0");
+  const size_t np2 = (size_t)G * c->na * c->na;
+  if (p2) {
+    for (size_t e = 0; e < np2; e++)
+      if (!std::isfinite(p2[e])) return fail(c, PBS_ERR_ARG, "p2 must be finite");
+  } else if (c->K > 0 && c->p2.size() != np2) {
+    return fail(c, PBS_ERR_STATE, "no previous P^2: pass p2");
+  }
+  { pbs_status fr = c->ws ? PBS_DISPATCH(c, flush_impl, c) : PBS_OK; if (fr != PBS_OK) return fr; }
+  c->s_face.assign(s_face, s_face + G + 1);
+  c->ts.assign(ts, ts + G);
+  c->sig.assign(sig_ct, sig_ct + G);
+  if (p2) c->p2.assign(p2, p2 + np2);
+  transfer_tables(c, lambda_p1);
+  c->have_tables = true;
+  drop_graph(c);
   if (!c->ws) return PBS_OK;  // uploaded at bind time
   return PBS_DISPATCH(c, upload_tables, c);
 }

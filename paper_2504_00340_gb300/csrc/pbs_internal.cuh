@@ -45,7 +45,7 @@ struct Dims {
 };
 
 // Device status word: slot 0 counts timeouts, slot 1 records where.
-enum : int { kErrTimeoutTransport = 1, kErrTimeoutSourceMma = 2 };
+enum : int { kErrTimeoutSourceMma = 2, kErrTimeoutAngular = 3 };
 
 // ----------------------------------------------------------------------------
 // PTX helpers: shared-memory addresses, mbarriers, 1-D bulk (TMA) copies.
@@ -186,12 +186,7 @@ cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const
                           const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
                           double dose_scale, double flu_scale, const BeamStrides &bs);
 
-template <typename real>
-cudaError_t launch_transport(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
-                             double dy, double dz, int *err);
-
-// Warp-per-plane streaming transport for nz <= 128 (k_transport_rows.cu).
-bool transport_rows_supported(int nz);
+// Warp-per-plane streaming transport (k_transport_rows.cu).
 template <typename real>
 cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
                                   double dy, double dz);

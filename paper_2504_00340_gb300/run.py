@@ -1,7 +1,7 @@
 """Run one named workload through the C ABI and print a short summary.
 
     python -m paper_2504_00340_gb300.run --workload water150_128x128_g256_a16x16 \
-        [--ny 64 --nz 64] [--ng G] [--steps N] [--precision fp32|fp64|mixed]
+        [--ny 64 --nz 64] [--ng G] [--steps N] [--precision fp32|fp64|mixed] [--autotune] [--vs-fp64]
     python -m paper_2504_00340_gb300.run --spots 256 [--max-gb 48] [--no-graph] [--no-autotune]
 
 Sizes may be overridden to make reduced cases of the same kernels (e.g. for
@@ -76,6 +76,10 @@ def main(argv=None):
     p.add_argument("--max-gb", type=float, default=48.0, help="device workspace per spot bucket (GiB)")
     p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--autotune", action="store_true", help="autotune launch shapes before a workload march")
+    p.add_argument("--no-profile", action="store_true", help="no per-kernel event pairs in the timed march")
+    p.add_argument("--vs-fp64", action="store_true",
+                   help="also march the same workload in FP64 and report the dose and fluence error against it")
     a = p.parse_args(argv)
     if a.spots:
         out = run_spots(a)
@@ -92,21 +96,47 @@ def main(argv=None):
     prec = a.precision or w.precision
     import torch
     torch.cuda.set_device(0)
-    s = binding.Solver(w.grid(), nx=steps, dx=w.dx, n_scatter=w.n_scatter, precision=prec)
-    s.set_material(w.density(steps))
-    s.launch_beam(**w.beam)
-    s.set_profiling(True)
-    t0 = time.perf_counter()
-    s.step(steps)
-    dose = s.read_dose(steps)
-    t = time.perf_counter() - t0
-    prof = s.profile()
-    out = {"workload": w.name, "ny": w.ny, "nz": w.nz, "ng": w.ng, "steps": steps, "precision": prec,
-           "wall_s": t, "cell_updates_per_s": w.cell_updates_per_step * steps / t,
-           "max_dose": float(np.abs(dose).max()), "kernels": {k: list(v) for k, v in prof.items()}}
+    out, dose, flu = march(binding, w, steps, prec, autotune=a.autotune, profile=not a.no_profile)
+    out.update({"workload": w.name, "ny": w.ny, "nz": w.nz, "ng": w.ng, "n_scatter": w.n_scatter,
+                "medium": w.medium})
+    if a.vs_fp64 and prec != "fp64":
+        ref, dose64, flu64 = march(binding, w, steps, "fp64", autotune=False, profile=False)
+        out["fp64"] = {"cell_updates_per_s": ref["cell_updates_per_s"],
+                       "speedup": out["cell_updates_per_s"] / ref["cell_updates_per_s"],
+                       "dose_err_vs_fp64": float(np.abs(dose - dose64).max() / np.abs(dose64).max()),
+                       "fluence_err_vs_fp64": float(np.abs(flu - flu64).max() / np.abs(flu64).max())}
     print(json.dumps(out))
-    s.close()
 
+
+def march(binding, w, steps, prec, autotune=False, profile=True):
+    """The whole march of workload w (steps depth steps) in the given
+    precision: device time by CUDA events around step + flush on the
+    context's stream; per-kernel times when profiling."""
+    import torch
+    s = binding.Solver(w.grid(), nx=steps, dx=w.dx, n_scatter=w.n_scatter, precision=prec)
+    try:
+        s.set_material(w.density(steps))
+        s.launch_beam(**w.beam)
+        if autotune:
+            s.autotune(2)
+        s.set_profiling(profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s.stream)
+        s.step(steps)
+        s.flush()
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        dose, flu = s.read_dose(steps), s.read_fluence(steps + 1)
+        out = {"steps": steps, "precision": prec, "device_s": ms / 1e3,
+               "cell_updates_per_s": w.cell_updates_per_step * steps / (ms / 1e3),
+               "max_dose": float(np.abs(dose).max()), "tuning": s.tuning}
+        if profile:
+            out["kernels"] = {k: list(v) for k, v in s.profile().items()}
+        return out, dose, flu
+    finally:
+        s.close()
 
 if __name__ == "__main__":
     main()

@@ -1,0 +1,108 @@
+"""Degenerate and edge cases of the CUDA path against the oracle: one- and
+two-row planes, single-column rows, the smallest angle grid, a single energy
+group, vacuum slabs (rho = 0) inside the march, and empty calls."""
+import numpy as np
+import pytest
+
+from paper_2504_00340_gb300 import binding
+from paper_2504_00340_gb300.workloads import random_state
+
+pytestmark = pytest.mark.gpu
+
+
+def _grid(ny, nz, nu, nv, ng, e_max=60.0, d=0.1, u_max=0.15):
+    return dict(ny=ny, nz=nz, nu=nu, nv=nv, dy=d, dz=d, u_max=u_max, v_max=u_max,
+                e_faces=np.linspace(0.0, e_max, ng + 1))
+
+
+def _relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
+@pytest.mark.parametrize("ny,nz", [(1, 8), (2, 12), (4, 1), (1, 1), (2, 3)])
+def test_transport_tiny_planes(orc, precision, tol, ny, nz):
+    grid = _grid(ny, nz, 4, 4, 2)
+    s = binding.Solver(grid, nx=1, dx=0.05, precision=precision)
+    psi = random_state((2, 2, 4, 4, ny, nz), seed=ny * 31 + nz)
+    s.write_psi(0, psi)
+    s.substep_transport(0.3)
+    ref = orc.Oracle(grid).transport_substep(0.3, psi)
+    assert _relerr(s.read_psi(0), ref) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
+def test_angular_smallest_grid(orc, precision, tol):
+    grid = _grid(4, 6, 2, 2, 3)
+    s = binding.Solver(grid, nx=1, dx=0.05, precision=precision)
+    s.set_material(np.full((1, 4, 6), 1.3))
+    psi = random_state((3, 2, 2, 2, 4, 6), seed=5)
+    s.write_psi(0, psi)
+    s.substep_angular(2.0, 0)
+    ref = orc.Oracle(grid).angular_substep(2.0, np.full((4, 6), 1.3), psi)
+    assert _relerr(s.read_psi(0), ref) < tol
+    s.close()
+
+
+def test_single_group_march(orc):
+    grid = _grid(8, 8, 4, 4, 1, e_max=20.0)
+    nx, dx = 5, 0.05
+    rho = np.ones((nx, 8, 8))
+    beam = dict(e0=10.0, sigma_e=1.0, sigma_y=0.2, sigma_z=0.2)
+    s = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision="fp64")
+    s.set_material(rho)
+    s.launch_beam(**beam)
+    s.step(nx)
+    ref = orc.Oracle(grid).march(rho, nx, dx, beam=beam, n_scatter=1)
+    assert _relerr(s.read_dose(), ref["dose"]) < 1e-10
+    assert _relerr(s.read_fluence(), ref["fluence"]) < 1e-10
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_vacuum_gap(orc, precision, tol):
+    """Slabs of rho = 0 inside the march: no energy loss, no scattering, no
+    dose there; transport continues."""
+    grid = _grid(10, 12, 8, 8, 20)
+    nx, dx = 8, 0.05
+    rho = np.ones((nx, 10, 12))
+    rho[2:5] = 0.0
+    rho[6, :5] = 0.0  # a half-vacuum slab
+    beam = dict(e0=45.0, sigma_e=1.0, sigma_y=0.25, sigma_z=0.25)
+    s = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision=precision)
+    s.set_material(rho)
+    s.launch_beam(**beam)
+    s.step(nx)
+    d = s.read_dose()
+    ref = orc.Oracle(grid).march(rho, nx, dx, beam=beam, n_scatter=1)
+    assert not d[2:5].any() and not d[6, :5].any()
+    assert _relerr(d, ref["dose"]) < tol
+    assert _relerr(s.read_fluence(), ref["fluence"]) < tol
+    s.close()
+
+
+def test_empty_calls():
+    grid = _grid(6, 6, 4, 4, 8)
+    s = binding.Solver(grid, nx=3, dx=0.05, precision="fp32", n_beams=2)
+    s.set_material(np.ones((3, 6, 6)))
+    s.launch_beams([dict(e0=30.0), dict(e0=20.0)])
+    s.step(0)
+    assert s.depth == 0
+    assert not s.read_dose(3).any()  # no step marched: no dose
+    f = s.read_fluence(1)
+    assert f.shape == (2, 1, 6, 6) and np.all(f.sum(axis=(1, 2, 3)) > 0)  # the entrance plane of both beams
+    s.set_beam_steps([0, 0])
+    s.launch_beams([dict(e0=30.0), dict(e0=20.0)])
+    s.run(True)  # no beam marches: the graph holds only the restart
+    assert s.depth == 0 and not s.read_dose(3).any()
+    with pytest.raises(binding.PbsError):
+        s.step(4)  # past the material
+    s.close()
