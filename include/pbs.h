@@ -216,12 +216,17 @@ pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
  *   angular_form    angular substep: 0 direct, 1 TMA-staged persistent
  *                   (needs a row pitch of ny*nz elements that is a multiple of
  *                   16 bytes), 2 packed FP32x2 (FP32, ny*nz even); a form the
- *                   grid does not allow falls back to 0 */
+ *                   grid does not allow falls back to 0
+ *   source_form     BF16 source contraction on the tensor cores (mixed
+ *                   precision, n_scatter > 0): 0 tile by tile, 1 pipelined
+ *                   (TMA loads, MMAs and epilogue of consecutive tiles
+ *                   overlapped) */
 typedef struct {
   int energy_angles;
   int energy_form;
   int transport_ctas;
   int angular_form;
+  int source_form;
 } pbs_tuning;
 
 /* Launch-shape autotuner: times the candidate energy forms and shapes (angles

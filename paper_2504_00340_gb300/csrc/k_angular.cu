@@ -26,9 +26,6 @@
 // direct form (k_angular) serves grids whose row pitch breaks the TMA rules.
 #include "pbs_internal.cuh"
 
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <cmath>
 #include <mutex>
 
@@ -388,26 +385,13 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
   if (leader) bulk_wait_all();
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static std::once_flag once;
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  });
-  return fn;
-}
-
 // TMA form usable: row pitch nyz * sizeof(real) a multiple of 16 bytes, rows
 // addressable by 32-bit coordinates, and the driver's encoder available.
 template <typename real>
 bool angular_tma_ok(const Dims &d, const real *psi) {
   const long long rows = (long long)d.ncomp * d.ng * 2 * d.na;
   return ((d.nyz * sizeof(real)) % 16 == 0) && rows < (1LL << 31) && d.na <= 256 &&
-         (reinterpret_cast<uintptr_t>(psi) % 16 == 0) && encode_fn() != nullptr;
+         (reinterpret_cast<uintptr_t>(psi) % 16 == 0) && tensor_map_encoder() != nullptr;
 }
 
 template <typename real, int NU, int NV>
@@ -422,7 +406,7 @@ cudaError_t go_tma(const LaunchCtx &lc, const Dims &d, real *psi, const real *rh
   cuuint64_t strides[1] = {(cuuint64_t)d.nyz * sizeof(real)};
   cuuint32_t box[2] = {(cuuint32_t)kTW, (cuuint32_t)NA};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(&map, sizeof(real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+  CUresult r = tensor_map_encoder()(&map, sizeof(real) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                            2, psi, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
@@ -480,6 +464,19 @@ cudaError_t go(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz
 }
 
 }  // namespace
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
 
 template <typename real>
 cudaError_t launch_angular(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts,

@@ -235,6 +235,240 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ---------------------------------------------------------------- pipelined form
+//
+// Warp-specialised and pipelined: lane 0 of warp 0 issues the TMA loads and
+// the MMAs, warps 1-4 drain the accumulators.  P^2_g (all M rows, whole K) is
+// loaded once per group by one 5-D TMA copy straight into the canonical K-major
+// core-matrix layout; each R tile (whole K x 64 lateral points) by one 3-D TMA
+// copy into the canonical MN-major layout, kPipeMax stages ahead; the MMAs of a
+// tile go into one of two TMEM accumulators while the epilogue warps read the
+// other, so loads, MMAs and stores of consecutive tiles overlap.  Each CTA walks
+// a contiguous range of (group, N-tile) tiles; every wait is bounded.
+
+constexpr int kPipeMax = 4;                      // R stages (3 when na = 256: shared memory)
+constexpr int kPipeThreads = 160;                // warp 0: producer + MMA issue; warps 1-4: epilogue
+constexpr long long kPipeWait = 2000000000LL;    // ~1 s at 2 GHz
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    k_source_tc_pipe(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                     __nv_bfloat16 *__restrict__ src, int na, int nyz, int ng, int ngb, int nstages, float dudv,
+                     int *__restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const int mh = na / kTM;  // M halves
+  const int kcm = na / 8;
+  const unsigned a_bytes = (unsigned)na * na * 2u;
+  const unsigned b_bytes = (unsigned)na * kTN * 2u;
+  unsigned char *sA = smem_raw;
+  unsigned char *sB = smem_raw + a_bytes;  // stage s at sB + s * b_bytes
+  __shared__ __align__(8) uint64_t full_b[kPipeMax], empty_b[kPipeMax], acc_full[2], acc_empty[2], a_full;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int acc_cols = mh * kTN;  // columns of one accumulator (both M halves)
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(2 * kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kPipeMax; i++) {
+      mbar_init(&full_b[i], 1);
+      mbar_init(&empty_b[i], 1);
+    }
+    for (int i = 0; i < 2; i++) {
+      mbar_init(&acc_full[i], 1);
+      mbar_init(&acc_empty[i], 128);
+    }
+    mbar_init(&a_full, 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  const int ntn = (nyz + kTN - 1) / kTN;
+  const long long ntot = (long long)ngb * ntn;
+  const long long per = (ntot + gridDim.x - 1) / gridDim.x;
+  const long long t_beg = (long long)blockIdx.x * per;
+  const long long t_end = min(ntot, t_beg + per);
+  const int count = (int)max(0LL, t_end - t_beg);
+
+  if (warp == 0) {
+    if (lane == 0 && count > 0) {
+      const uint32_t idesc = idesc_bf16(kTM, kTN);
+      const uint32_t lbo = 128, sbo = (uint32_t)kcm * 128;
+      int issued = 0, cur_gb = -1, consumed = 0;
+      unsigned a_phase = 0;
+      bool ok = true, a_pending = false;
+      for (int i = 0; i < count && ok; i++) {
+        // keep the R loads nstages tiles ahead
+        while (ok && issued < count && issued < i + nstages) {
+          const int s = issued % nstages;
+          if (issued >= nstages)
+            ok = mbar_wait_bounded(&empty_b[s], (unsigned)((issued / nstages - 1) & 1), kPipeWait);
+          if (!ok) break;
+          const long long t = t_beg + issued;
+          const int gb = (int)(t / ntn), nt = (int)(t % ntn);
+          mbar_arrive_expect_tx(&full_b[s], b_bytes);
+          tma_load_3d(sB + (size_t)s * b_bytes, &mapB, 0, gb * na, nt * (kTN / 8), &full_b[s]);
+          issued++;
+        }
+        if (!ok) break;
+        const long long t = t_beg + i;
+        const int gb = (int)(t / ntn);
+        if (gb != cur_gb) {
+          // P^2 of the new group: every MMA reading the old one has completed
+          if (i > 0) ok = mbar_wait_bounded(&acc_full[(i - 1) & 1], (unsigned)(((i - 1) >> 1) & 1), kPipeWait);
+          if (!ok) break;
+          mbar_arrive_expect_tx(&a_full, a_bytes);
+          tma_load_5d(sA, &mapA, 0, 0, 0, 0, gb % ng, &a_full);
+          a_pending = true;
+          ok = mbar_wait_bounded(&a_full, a_phase, kPipeWait);
+          if (!ok) break;
+          a_pending = false;
+          a_phase ^= 1u;
+          cur_gb = gb;
+        }
+        const int s = i % nstages;
+        ok = mbar_wait_bounded(&full_b[s], (unsigned)((i / nstages) & 1), kPipeWait);
+        if (!ok) break;
+        consumed = i + 1;
+        const int acc = i & 1;
+        if (i >= 2) ok = mbar_wait_bounded(&acc_empty[acc], (unsigned)(((i >> 1) - 1) & 1), kPipeWait);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t b0 = smem_u32(sB + (size_t)s * b_bytes);
+        for (int h = 0; h < mh; h++) {
+          const uint32_t a0 = smem_u32(sA) + (uint32_t)h * (kTM / 8) * kcm * 128u;
+          const uint32_t d = tmem + (uint32_t)(acc * acc_cols + h * kTN);
+          for (int j = 0; j < na / 16; j++)
+            mma_bf16(d, smem_desc(a0 + (uint32_t)j * 256u, lbo, sbo), smem_desc(b0 + (uint32_t)j * 256u, lbo, sbo),
+                     idesc, j > 0);
+        }
+        mma_commit(&empty_b[s]);
+        mma_commit(&acc_full[acc]);
+      }
+      if (!ok) {
+        *reinterpret_cast<volatile int *>(&s_abort) = 1;
+        if (err) {
+          atomicAdd(err, 1);
+          atomicExch(err + 1, kErrTimeoutSourceMma);
+        }
+        // let the copies still in flight land (bounded) before the CTA exits
+        if (a_pending) mbar_wait_bounded(&a_full, a_phase, kPipeWait / 8);
+        for (int k = consumed; k < issued; k++)
+          mbar_wait_bounded(&full_b[k % nstages], (unsigned)((k / nstages) & 1), kPipeWait / 8);
+      }
+      // the last commit covers every MMA issued: wait for it before TMEM is released
+      if (count > 0) mbar_wait_bounded(&acc_full[(count - 1) & 1], (unsigned)(((count - 1) >> 1) & 1), kPipeWait);
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of each M half
+    const int q = warp & 3;
+    for (int i = 0; i < count; i++) {
+      const int acc = i & 1;
+      const bool ok = mbar_wait_bounded(&acc_full[acc], (unsigned)((i >> 1) & 1), kPipeWait);
+      // warp-uniform decision: the TMEM loads below are warp-collective
+      if (!__all_sync(0xffffffffu, ok && *reinterpret_cast<volatile int *>(&s_abort) == 0)) break;
+      tc_fence_after();
+      const long long t = t_beg + i;
+      const int gb = (int)(t / ntn), n0 = (int)(t % ntn) * kTN;
+      for (int h = 0; h < mh; h++) {
+        const int m = h * kTM + q * 32 + lane;
+        __nv_bfloat16 *out = src + ((long long)gb * na + m) * nyz + n0;
+#pragma unroll
+        for (int half = 0; half < kTN / 32; half++) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + h * kTN + half * 32), v);
+          const int nb = half * 32;
+          if (n0 + nb + 32 <= nyz) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+              uint4 pk;
+              __nv_bfloat162 h0 = __floats2bfloat162_rn(v[c * 8 + 0] * dudv, v[c * 8 + 1] * dudv);
+              __nv_bfloat162 h1 = __floats2bfloat162_rn(v[c * 8 + 2] * dudv, v[c * 8 + 3] * dudv);
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[c * 8 + 4] * dudv, v[c * 8 + 5] * dudv);
+              __nv_bfloat162 h3 = __floats2bfloat162_rn(v[c * 8 + 6] * dudv, v[c * 8 + 7] * dudv);
+              pk.x = *reinterpret_cast<uint32_t *>(&h0);
+              pk.y = *reinterpret_cast<uint32_t *>(&h1);
+              pk.z = *reinterpret_cast<uint32_t *>(&h2);
+              pk.w = *reinterpret_cast<uint32_t *>(&h3);
+              *reinterpret_cast<uint4 *>(out + nb + c * 8) = pk;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; e++)
+              if (n0 + nb + e < nyz) out[nb + e] = __float2bfloat16_rn(v[e] * dudv);
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[acc]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
+}
+
+// Tensor maps of the pipelined form: P^2 as [g][m8][kc][m7][k8] (5-D box = one
+// group) and R as [chunk][row][n8] (3-D box = whole K x 64 lateral points).
+bool source_pipe_maps(const Dims &d, const __nv_bfloat16 *p2, const __nv_bfloat16 *r, int nbatch, CUtensorMap &ma,
+                      CUtensorMap &mb) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t na = (cuuint64_t)d.na, nyz = (cuuint64_t)d.nyz;
+  {
+    cuuint64_t dims[5] = {8, 8, na / 8, na / 8, (cuuint64_t)d.ng};
+    cuuint64_t strides[4] = {na * 2, 16, 8 * na * 2, na * na * 2};
+    cuuint32_t box[5] = {8, 8, (cuuint32_t)(na / 8), (cuuint32_t)(na / 8), 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    if (enc(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(p2), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  {
+    cuuint64_t dims[3] = {8, (cuuint64_t)d.ng * nbatch * na, nyz / 8};
+    cuuint64_t strides[2] = {nyz * 2, 16};
+    cuuint32_t box[3] = {8, (cuuint32_t)na, kTN / 8};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(r), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
+
 }  // namespace
 
 bool source_tc_supported(int na, int nyz) { return na % kTM == 0 && na <= 256 && nyz % 8 == 0; }
@@ -242,6 +476,20 @@ bool source_tc_supported(int na, int nyz) { return na % kTM == 0 && na <= 256 &&
 cudaError_t launch_source_tc(const LaunchCtx &lc, const Dims &d, const __nv_bfloat16 *p2, const __nv_bfloat16 *r,
                              __nv_bfloat16 *src, double dudv, int nbatch) {
   if (!source_tc_supported(d.na, d.nyz)) return launch_source_bf16_cc(lc, d, p2, r, src, dudv, nbatch);
+  CUtensorMap ma, mb;
+  if (lc.source_form == 1 && source_pipe_maps(d, p2, r, nbatch, ma, mb)) {
+    const int nstages = d.na == 256 ? 3 : kPipeMax;
+    const size_t smem = (size_t)d.na * d.na * 2 + (size_t)nstages * d.na * kTN * 2;
+    cudaError_t e = cudaFuncSetAttribute(k_source_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long ntot = (long long)d.ng * nbatch * ((d.nyz + kTN - 1) / kTN);
+    long long blocks = lc.num_sms;  // one CTA per SM (shared memory; TMEM 256 columns)
+    if (blocks > ntot) blocks = ntot;
+    k_source_tc_pipe<<<(unsigned)blocks, kPipeThreads, smem, lc.stream>>>(ma, mb, src, d.na, d.nyz, d.ng,
+                                                                          d.ng * nbatch, nstages, (float)dudv, lc.err);
+    ++*lc.launches;
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)(kTM / 8 + kTN / 8) * (d.na / 8) * 128;
   cudaError_t e = cudaFuncSetAttribute(k_source_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

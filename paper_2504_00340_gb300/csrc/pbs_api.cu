@@ -53,7 +53,7 @@ struct pbs_ctx {
   size_t rsize, ssize;  // element sizes of real and of the source storage
   long long launches = 0;
   // launch shapes (pbs_autotune / pbs_set_tuning)
-  pbs_tuning tune{8, 1, 0, 2};
+  pbs_tuning tune{8, 1, 0, 2, 1};
   // whole-march CUDA graph (pbs_run with use_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -126,6 +126,7 @@ LaunchCtx lctx(pbs_ctx *c) {
   lc.energy_form = c->tune.energy_form;
   lc.transport_ctas = c->tune.transport_ctas;
   lc.angular_form = c->tune.angular_form;
+  lc.source_form = c->tune.source_form;
   return lc;
 }
 
@@ -712,6 +713,21 @@ pbs_status autotune_impl(pbs_ctx *c, int reps) {
       if (ms < best) { best = ms; pick.angular_form = form; }
     }
   }
+  c->tune = pick;
+  best = 1e30f;
+  if (r == PBS_OK && c->K > 0 && c->precision == PBS_MIXED) {
+    for (int form : {1, 0}) {
+      c->tune.source_form = form;
+      float ms;
+      r = time_best([&] {
+        cudaError_t e = launch_source<real, st>(lctx(c), dims_for(c, c->B), at<st>(c, c->off_p2), at<st>(c, c->off_r),
+                                                at<st>(c, c->off_s), c->du * c->dv, c->B);
+        return e == cudaSuccess ? PBS_OK : cuda_fail(c, e, "source kernel");
+      }, ms);
+      if (r != PBS_OK) break;
+      if (ms < best) { best = ms; pick.source_form = form; }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->profiling = prof;
@@ -932,7 +948,7 @@ pbs_status pbs_set_tuning(pbs_ctx *c, const pbs_tuning *t) {
   if (!c || !t) return fail(c, PBS_ERR_ARG, "null tuning");
   if ((t->energy_angles != 4 && t->energy_angles != 8 && t->energy_angles != 16) || t->energy_form < 0 ||
       t->energy_form > 1 || t->transport_ctas < 0 || t->transport_ctas > 64 || t->angular_form < 0 ||
-      t->angular_form > 2)
+      t->angular_form > 2 || t->source_form < 0 || t->source_form > 1)
     return fail(c, PBS_ERR_ARG, "tuning value out of range");
   c->tune = *t;
   drop_graph(c);

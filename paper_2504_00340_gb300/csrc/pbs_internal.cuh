@@ -14,6 +14,8 @@
 //   err   int[4]                  device status word (timeouts)
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -151,6 +153,7 @@ struct LaunchCtx {
                            // (forms 1 and 2 where the grid allows, else 0)
   int energy_form = 1;     // FP32 energy substep: 0 one lane per thread, 1 packed FP32x2
                            // (form 1 where the grid allows, else 0)
+  int source_form = 1;     // BF16 source contraction: 0 tile by tile, 1 TMA/MMA/epilogue pipeline
 };
 
 // One E substep's per-lane inputs and outputs: density of its slab, c = h/2,
@@ -185,6 +188,10 @@ template <typename real, typename st>
 cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
                           const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
                           double dose_scale, double flu_scale, const BeamStrides &bs);
+
+// The driver's tensor-map encoder (cuTensorMapEncodeTiled), looked up once
+// through the runtime; NULL when the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 
 // Warp-per-plane streaming transport (k_transport_rows.cu).
 template <typename real>

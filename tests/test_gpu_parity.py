@@ -176,6 +176,24 @@ def test_source_contraction(orc, precision, tol, ny, nz, nu, nv):
     s.close()
 
 
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("ny,nz,nu,nv,ng", [(24, 24, 16, 16, 40), (16, 20, 8, 16, 60), (12, 12, 16, 16, 7)])
+def test_source_contraction_tensor_core_forms(orc, form, ny, nz, nu, nv, ng):
+    """The tile-by-tile and the pipelined tcgen05 contraction (source_form 0 /
+    1) on many groups per CTA (P^2 reloads at group boundaries, every R stage
+    and both TMEM accumulators reused) and a ragged last N tile, against the
+    oracle in BF16 tolerance."""
+    grid = _grid(ny, nz, nu, nv, ng)
+    s, o, rho = _pair(orc, grid, 1, 0.05, 1, "mixed")
+    s.set_tuning(source_form=form)
+    psi = smooth_state(ny, nz, ng, nv, nu, seed=4)
+    s.write_psi(0, psi)
+    got = s.eval_source(0, 0)
+    ref = o.source(rho[0], psi)
+    assert _relerr(got, ref) < 8e-3
+    s.close()
+
+
 def test_full_march_fp64(orc):
     grid = _grid(18, 14, 8, 8, 24, e_max=60.0)
     nx, dx = 12, 0.05
