@@ -213,6 +213,9 @@ pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
  *                   ny*nz even, else form 0 runs)
  *   transport_ctas  resident CTAs per SM of the streaming transport, 0..64
  *                   (0 = as many as fit)
+ *   transport_cols  columns of a row per lane of the streaming transport: 4,
+ *                   6 or 0 (chosen by the row width nz: 6 where nz is a
+ *                   multiple of 6 and that fills the warps better)
  *   angular_form    angular substep: 0 direct, 1 TMA-staged persistent
  *                   (needs a row pitch of ny*nz elements that is a multiple of
  *                   16 bytes), 2 packed FP32x2 (FP32, ny*nz even); a form the
@@ -225,6 +228,7 @@ typedef struct {
   int energy_angles;
   int energy_form;
   int transport_ctas;
+  int transport_cols;
   int angular_form;
   int source_form;
 } pbs_tuning;

@@ -46,8 +46,8 @@ class PbsBeam(ctypes.Structure):
 
 
 class PbsTuning(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int) for n in ("energy_angles", "energy_form", "transport_ctas", "angular_form",
-                                            "source_form")]
+    _fields_ = [(n, ctypes.c_int) for n in ("energy_angles", "energy_form", "transport_ctas", "transport_cols",
+                                            "angular_form", "source_form")]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -399,7 +399,7 @@ class Solver:
     @property
     def tuning(self) -> dict:
         """Launch shapes and kernel forms: energy_angles, energy_form,
-        transport_ctas, angular_form, source_form."""
+        transport_ctas, transport_cols, angular_form, source_form."""
         return pbs_get_tuning(self.ctx).as_dict()
 
     def set_tuning(self, **kw):

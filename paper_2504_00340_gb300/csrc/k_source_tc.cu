@@ -238,16 +238,19 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
 // ---------------------------------------------------------------- pipelined form
 //
 // Warp-specialised and pipelined: lane 0 of warp 0 issues the TMA loads and
-// the MMAs, warps 1-4 drain the accumulators.  P^2_g (all M rows, whole K) is
+// the MMAs, warps 1-8 drain the accumulators.  P^2_g (all M rows, whole K) is
 // loaded once per group by one 5-D TMA copy straight into the canonical K-major
 // core-matrix layout; each R tile (whole K x 64 lateral points) by one 3-D TMA
 // copy into the canonical MN-major layout, kPipeMax stages ahead; the MMAs of a
 // tile go into one of two TMEM accumulators while the epilogue warps read the
-// other, so loads, MMAs and stores of consecutive tiles overlap.  Each CTA walks
-// a contiguous range of (group, N-tile) tiles; every wait is bounded.
+// other, so loads, MMAs and stores of consecutive tiles overlap.  Two epilogue
+// warps share each TMEM lane quadrant, one per 32-column half of the tile.
+// Each CTA walks a contiguous range of (group, N-tile) tiles; every wait is
+// bounded.
 
 constexpr int kPipeMax = 4;                      // R stages (3 when na = 256: shared memory)
-constexpr int kPipeThreads = 160;                // warp 0: producer + MMA issue; warps 1-4: epilogue
+constexpr int kPipeThreads = 288;                // warp 0: producer + MMA issue; warps 1-8: epilogue
+constexpr int kEpiThreads = kPipeThreads - 32;
 constexpr long long kPipeWait = 2000000000LL;    // ~1 s at 2 GHz
 
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     }
     for (int i = 0; i < 2; i++) {
       mbar_init(&acc_full[i], 1);
-      mbar_init(&acc_empty[i], 128);
+      mbar_init(&acc_empty[i], kEpiThreads);
     }
     mbar_init(&a_full, 1);
     fence_mbar_init();
@@ -389,8 +392,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       if (count > 0) mbar_wait_bounded(&acc_full[(count - 1) & 1], (unsigned)(((count - 1) >> 1) & 1), kPipeWait);
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of each M half
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of each M half,
+    // columns 32 half .. +31 of the tile
     const int q = warp & 3;
+    const int half = (warp - 1) >> 2;
     for (int i = 0; i < count; i++) {
       const int acc = i & 1;
       const bool ok = mbar_wait_bounded(&acc_full[acc], (unsigned)((i >> 1) & 1), kPipeWait);
@@ -402,8 +407,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       for (int h = 0; h < mh; h++) {
         const int m = h * kTM + q * 32 + lane;
         __nv_bfloat16 *out = src + ((long long)gb * na + m) * nyz + n0;
-#pragma unroll
-        for (int half = 0; half < kTN / 32; half++) {
+        {
           float v[32];
           tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + h * kTN + half * 32), v);
           const int nb = half * 32;

@@ -28,7 +28,8 @@ namespace pbs {
 
 namespace {
 
-constexpr int kV = 4;        // columns per lane
+// Columns per lane: KV = 4 or 6 (a template parameter; 6 fills a warp with
+// rows of 96 or 192 columns).
 constexpr int kP = 6;        // rows in flight per lane
 constexpr int kR = 8;        // ring slots (a power of two >= kP + 1: slot indices wrap by a mask)
 constexpr int kWarps = 4;    // warps per CTA
@@ -77,112 +78,120 @@ __device__ __forceinline__ real face_value_d(real B, real d1, real d2) {
   return fma(real(0.5), copysign(m, d2), B);
 }
 
-// Four columns of one row.  Elementwise arithmetic goes through the helpers
+// KV columns of one row.  Elementwise arithmetic goes through the helpers
 // below, which issue the packed FP32x2 instructions for float (two columns
 // per instruction) and plain ones for double.
-template <typename real>
-struct V4 {
-  real v[kV];
+template <typename real, int KV>
+struct Vk {
+  real v[KV];
 };
 
 __device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
 
-template <typename real>
-__device__ __forceinline__ V4<real> add4(const V4<real> &a, const V4<real> &b) {
-  V4<real> r;
+template <typename real, int KV>
+__device__ __forceinline__ Vk<real, KV> add4(const Vk<real, KV> &a, const Vk<real, KV> &b) {
+  Vk<real, KV> r;
+  if constexpr (sizeof(real) == 4) {
 #pragma unroll
-  for (int j = 0; j < kV; j++) r.v[j] = a.v[j] + b.v[j];
-  return r;
-}
-template <>
-__device__ __forceinline__ V4<float> add4<float>(const V4<float> &a, const V4<float> &b) {
-  V4<float> r;
+    for (int j = 0; j < KV; j += 2) {
+      const float2 t = __fadd2_rn(pk(a.v[j], a.v[j + 1]), pk(b.v[j], b.v[j + 1]));
+      r.v[j] = t.x;
+      r.v[j + 1] = t.y;
+    }
+  } else {
 #pragma unroll
-  for (int j = 0; j < kV; j += 2) {
-    const float2 t = __fadd2_rn(pk(a.v[j], a.v[j + 1]), pk(b.v[j], b.v[j + 1]));
-    r.v[j] = t.x;
-    r.v[j + 1] = t.y;
+    for (int j = 0; j < KV; j++) r.v[j] = a.v[j] + b.v[j];
   }
   return r;
 }
 // a - b
-template <typename real>
-__device__ __forceinline__ V4<real> sub4(const V4<real> &a, const V4<real> &b) {
-  V4<real> r;
+template <typename real, int KV>
+__device__ __forceinline__ Vk<real, KV> sub4(const Vk<real, KV> &a, const Vk<real, KV> &b) {
+  Vk<real, KV> r;
+  if constexpr (sizeof(real) == 4) {
 #pragma unroll
-  for (int j = 0; j < kV; j++) r.v[j] = a.v[j] - b.v[j];
-  return r;
-}
-template <>
-__device__ __forceinline__ V4<float> sub4<float>(const V4<float> &a, const V4<float> &b) {
-  V4<float> r;
+    for (int j = 0; j < KV; j += 2) {
+      const float2 t = __ffma2_rn(pk(b.v[j], b.v[j + 1]), pk(-1.f, -1.f), pk(a.v[j], a.v[j + 1]));
+      r.v[j] = t.x;
+      r.v[j + 1] = t.y;
+    }
+  } else {
 #pragma unroll
-  for (int j = 0; j < kV; j += 2) {
-    const float2 t = __ffma2_rn(pk(b.v[j], b.v[j + 1]), pk(-1.f, -1.f), pk(a.v[j], a.v[j + 1]));
-    r.v[j] = t.x;
-    r.v[j + 1] = t.y;
+    for (int j = 0; j < KV; j++) r.v[j] = a.v[j] - b.v[j];
   }
   return r;
 }
 // s * (B + h * sl) with h = 1/2
-template <typename real>
-__device__ __forceinline__ V4<real> face4(real s, const V4<real> &B, const V4<real> &sl) {
-  V4<real> r;
+template <typename real, int KV>
+__device__ __forceinline__ Vk<real, KV> face4(real s, const Vk<real, KV> &B, const Vk<real, KV> &sl) {
+  Vk<real, KV> r;
+  if constexpr (sizeof(real) == 4) {
 #pragma unroll
-  for (int j = 0; j < kV; j++) r.v[j] = s * fma(real(0.5), sl.v[j], B.v[j]);
-  return r;
-}
-template <>
-__device__ __forceinline__ V4<float> face4<float>(float s, const V4<float> &B, const V4<float> &sl) {
-  V4<float> r;
+    for (int j = 0; j < KV; j += 2) {
+      const float2 t =
+          __fmul2_rn(pk(s, s), __ffma2_rn(pk(0.5f, 0.5f), pk(sl.v[j], sl.v[j + 1]), pk(B.v[j], B.v[j + 1])));
+      r.v[j] = t.x;
+      r.v[j + 1] = t.y;
+    }
+  } else {
 #pragma unroll
-  for (int j = 0; j < kV; j += 2) {
-    const float2 t = __fmul2_rn(pk(s, s), __ffma2_rn(pk(0.5f, 0.5f), pk(sl.v[j], sl.v[j + 1]), pk(B.v[j], B.v[j + 1])));
-    r.v[j] = t.x;
-    r.v[j + 1] = t.y;
+    for (int j = 0; j < KV; j++) r.v[j] = s * fma(real(0.5), sl.v[j], B.v[j]);
   }
   return r;
 }
 // a + (b - c) + e
-template <typename real>
-__device__ __forceinline__ V4<real> upd4(const V4<real> &a, const V4<real> &b, const V4<real> &c, const V4<real> &e) {
+template <typename real, int KV>
+__device__ __forceinline__ Vk<real, KV> upd4(const Vk<real, KV> &a, const Vk<real, KV> &b, const Vk<real, KV> &c,
+                                             const Vk<real, KV> &e) {
   return add4(add4(a, sub4(b, c)), e);
 }
 
-// Superbee slopes of four columns from their differences d1 (behind) and d2
-// (ahead): the packed part (2x, 2|d2|) and the per-column limiter.
-template <typename real>
-__device__ __forceinline__ V4<real> slope4(const V4<real> &d1, const V4<real> &d2) {
-  V4<real> x, x2, t2, r;
+// Superbee slopes of the lane's columns from their differences d1 (behind)
+// and d2 (ahead): the packed part (2x, 2|d2|) and the per-column limiter.
+template <typename real, int KV>
+__device__ __forceinline__ Vk<real, KV> slope4(const Vk<real, KV> &d1, const Vk<real, KV> &d2) {
+  Vk<real, KV> x, x2, t2, r;
 #pragma unroll
-  for (int j = 0; j < kV; j++) x.v[j] = flip_by(d1.v[j], d2.v[j]);
+  for (int j = 0; j < KV; j++) x.v[j] = flip_by(d1.v[j], d2.v[j]);
   x2 = add4(x, x);
   t2 = add4(d2, d2);
 #pragma unroll
-  for (int j = 0; j < kV; j++) {
+  for (int j = 0; j < KV; j++) {
     const real m = max3(real(0), fmin(x2.v[j], fabs(d2.v[j])), fmin(x.v[j], fabs(t2.v[j])));
     r.v[j] = copysign(m, d2.v[j]);
   }
   return r;
 }
 
+// Bytes per cp.async chunk of a lane's KV columns (16 when every lane's chunk
+// starts 16-byte aligned, else 8).
+template <typename real, int KV>
+__host__ __device__ constexpr int row_chunk() {
+  return (KV * sizeof(real)) % 16 == 0 ? 16 : 8;
+}
+
 // Row I/O in the march frame.  FZ: columns in memory order; otherwise the
 // lane -> column map is mirrored (the row is read and written reversed).
-template <typename real, bool VEC, bool FZ>
+template <typename real, bool VEC, bool FZ, int KV>
 struct RowIO {
   // Copy row `row` of a plane into the lane's ring slot `dst`.  Mirrored
   // VEC rows land in physical order and are reversed on read.
   static __device__ __forceinline__ void issue(real *dst, const real *plane_base, int row, int nz, int col0, bool on) {
     const real *rowp = plane_base + (long long)row * nz;
     if (VEC) {
-      const int pc = FZ ? col0 : nz - kV - col0;  // physical first column of the lane's chunk
-      const unsigned nb = on ? 16u : 0u;
+      constexpr int CB = row_chunk<real, KV>(), CE = CB / (int)sizeof(real);
+      const int pc = FZ ? col0 : nz - KV - col0;  // physical first column of the lane's chunk
+      const unsigned nb = on ? (unsigned)CB : 0u;
 #pragma unroll
-      for (int k = 0; k < (int)(kV * sizeof(real) / 16); k++)
-        cp_async16(dst + k * (16 / sizeof(real)), on ? rowp + pc + k * (16 / sizeof(real)) : plane_base, nb);
+      for (int k = 0; k < KV / CE; k++) {
+        if (CB == 16)
+          cp_async16(dst + k * CE, on ? rowp + pc + k * CE : plane_base, nb);
+        else
+          cp_async8(dst + k * CE, on ? rowp + pc + k * CE : plane_base, nb);
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < kV; k++) {
+      for (int k = 0; k < KV; k++) {
         const int q = col0 + k;
         const bool in = on && (q < nz);
         const int pcol = FZ ? q : nz - 1 - q;
@@ -193,27 +202,35 @@ struct RowIO {
       }
     }
   }
-  static __device__ __forceinline__ void read(const real *src, V4<real> &x) {
+  static __device__ __forceinline__ void read(const real *src, Vk<real, KV> &x) {
 #pragma unroll
-    for (int k = 0; k < kV; k++) x.v[k] = (VEC && !FZ) ? src[kV - 1 - k] : src[k];
+    for (int k = 0; k < KV; k++) x.v[k] = (VEC && !FZ) ? src[KV - 1 - k] : src[k];
   }
-  static __device__ __forceinline__ void store(real *plane_base, int row, int nz, int col0, bool on, const V4<real> &x) {
+  // VEC store of a lane's KV columns at dst (physical order)
+  static __device__ __forceinline__ void store_vec(real *dst, const Vk<real, KV> &x) {
+    real y[KV];
+#pragma unroll
+    for (int k = 0; k < KV; k++) y[k] = FZ ? x.v[k] : x.v[KV - 1 - k];
+    if (sizeof(real) == 4 && KV == 4) {
+      *reinterpret_cast<float4 *>(dst) = make_float4((float)y[0], (float)y[1], (float)y[2], (float)y[3]);
+    } else if (sizeof(real) == 4) {
+#pragma unroll
+      for (int k = 0; k < KV; k += 2) *reinterpret_cast<float2 *>(dst + k) = make_float2((float)y[k], (float)y[k + 1]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < KV; k += 2)
+        *reinterpret_cast<double2 *>(dst + k) = make_double2((double)y[k], (double)y[k + 1]);
+    }
+  }
+  static __device__ __forceinline__ void store(real *plane_base, int row, int nz, int col0, bool on,
+                                               const Vk<real, KV> &x) {
     if (!on) return;
     real *rowp = plane_base + (long long)row * nz;
     if (VEC) {
-      const int pc = FZ ? col0 : nz - kV - col0;
-      real y[kV];
-#pragma unroll
-      for (int k = 0; k < kV; k++) y[k] = FZ ? x.v[k] : x.v[kV - 1 - k];
-      if (sizeof(real) == 4) {
-        *reinterpret_cast<float4 *>(rowp + pc) = make_float4((float)y[0], (float)y[1], (float)y[2], (float)y[3]);
-      } else {
-        reinterpret_cast<double2 *>(rowp + pc)[0] = make_double2((double)y[0], (double)y[1]);
-        reinterpret_cast<double2 *>(rowp + pc)[1] = make_double2((double)y[2], (double)y[3]);
-      }
+      store_vec(rowp + (FZ ? col0 : nz - KV - col0), x);
     } else {
 #pragma unroll
-      for (int k = 0; k < kV; k++) {
+      for (int k = 0; k < KV; k++) {
         const int q = col0 + k;
         if (q < nz) rowp[FZ ? q : nz - 1 - q] = x.v[k];
       }
@@ -221,33 +238,33 @@ struct RowIO {
   }
 };
 
-// z contribution (G_lo - G_hi) h/dz for the lane's 4 cells of one row in the
+// z contribution (G_lo - G_hi) h/dz for the lane's KV cells of one row in the
 // march frame (positive flow).  gz = |v| h / dz.  zl / zr: 0 for the first /
 // last lane of the plane (zero ghosts), else 1.
-template <typename real>
-__device__ __forceinline__ void z_delta(const V4<real> &c, real gz, real zl, real zr, int gw, V4<real> &out) {
-  const real lft = zl * __shfl_up_sync(0xffffffffu, c.v[kV - 1], 1, gw);  // column 4l-1
-  const real rgt = zr * __shfl_down_sync(0xffffffffu, c.v[0], 1, gw);     // column 4l+4
-  // right faces 4l+k+1/2 of the lane's cells
-  V4<real> dl, dr;
+template <typename real, int KV>
+__device__ __forceinline__ void z_delta(const Vk<real, KV> &c, real gz, real zl, real zr, int gw, Vk<real, KV> &out) {
+  const real lft = zl * __shfl_up_sync(0xffffffffu, c.v[KV - 1], 1, gw);  // the column left of the lane's first
+  const real rgt = zr * __shfl_down_sync(0xffffffffu, c.v[0], 1, gw);     // the column right of the lane's last
+  // right faces of the lane's cells
+  Vk<real, KV> dl, dr;
   dl.v[0] = c.v[0] - lft;
-  dr.v[0] = dl.v[1] = c.v[1] - c.v[0];
-  dr.v[1] = dl.v[2] = c.v[2] - c.v[1];
-  dr.v[2] = dl.v[3] = c.v[3] - c.v[2];
-  dr.v[3] = rgt - c.v[3];
-  const V4<real> g = face4(gz, c, slope4(dl, dr));
+#pragma unroll
+  for (int j = 0; j + 1 < KV; j++) dr.v[j] = dl.v[j + 1] = c.v[j + 1] - c.v[j];
+  dr.v[KV - 1] = rgt - c.v[KV - 1];
+  const Vk<real, KV> g = face4(gz, c, slope4(dl, dr));
   // left face = the left neighbour's last right face; inflow edge: zero ghosts upstream
-  const real glo = zl * __shfl_up_sync(0xffffffffu, g.v[kV - 1], 1, gw);
-  V4<real> gl;
+  const real glo = zl * __shfl_up_sync(0xffffffffu, g.v[KV - 1], 1, gw);
+  Vk<real, KV> gl;
   gl.v[0] = glo;
 #pragma unroll
-  for (int j = 1; j < kV; j++) gl.v[j] = g.v[j - 1];
+  for (int j = 1; j < KV; j++) gl.v[j] = g.v[j - 1];
   out = sub4(gl, g);
 }
 
-template <typename real, bool VEC, bool FZ>
+template <typename real, bool VEC, bool FZ, int KV>
 struct PlaneMarch {
-  real *ring;  // this lane's ring base (slot stride 32*kV)
+  using IO = RowIO<real, VEC, FZ, KV>;
+  real *ring;  // this lane's ring base (slot stride 32*KV)
   real *pbase;
   int ny, nz, col0, gw;  // col0: the lane's first column in the march frame
   bool fwd, on, own;     // on: the lane's columns are loaded; own: they are stored
@@ -263,46 +280,42 @@ struct PlaneMarch {
 
   __device__ __forceinline__ void setup_rows() {
     if (VEC) {
-      const int pc = FZ ? col0 : nz - kV - col0;
+      const int pc = FZ ? col0 : nz - KV - col0;
       const long long r0 = fwd ? 0 : (long long)(ny - 1) * nz;
       const long long st = fwd ? nz : -(long long)nz;
       srow0 = pbase + r0 + pc;
       sstep = st;
       lrow0 = on ? srow0 : pbase;
       lstep = on ? st : 0;
-      nbytes = on ? 16u : 0u;
+      nbytes = on ? (unsigned)row_chunk<real, KV>() : 0u;
     }
   }
   __device__ __forceinline__ void issue_row(real *dst, int m) {
     if (VEC) {
       const real *src = lrow0 + m * lstep;
+      constexpr int CB = row_chunk<real, KV>(), CE = CB / (int)sizeof(real);
 #pragma unroll
-      for (int k = 0; k < (int)(kV * sizeof(real) / 16); k++)
-        cp_async16(dst + k * (16 / sizeof(real)), src + k * (16 / sizeof(real)), nbytes);
-    } else {
-      RowIO<real, VEC, FZ>::issue(dst, pbase, prow(m), nz, col0, on);
-    }
-  }
-  __device__ __forceinline__ void store_row(int m, const V4<real> &x) {
-    if (VEC) {
-      if (!own) return;
-      real *dst = srow0 + m * sstep;
-      real y[kV];
-#pragma unroll
-      for (int k = 0; k < kV; k++) y[k] = FZ ? x.v[k] : x.v[kV - 1 - k];
-      if (sizeof(real) == 4) {
-        *reinterpret_cast<float4 *>(dst) = make_float4((float)y[0], (float)y[1], (float)y[2], (float)y[3]);
-      } else {
-        reinterpret_cast<double2 *>(dst)[0] = make_double2((double)y[0], (double)y[1]);
-        reinterpret_cast<double2 *>(dst)[1] = make_double2((double)y[2], (double)y[3]);
+      for (int k = 0; k < KV / CE; k++) {
+        if (CB == 16)
+          cp_async16(dst + k * CE, src + k * CE, nbytes);
+        else
+          cp_async8(dst + k * CE, src + k * CE, nbytes);
       }
     } else {
-      RowIO<real, VEC, FZ>::store(pbase, prow(m), nz, col0, own, x);
+      IO::issue(dst, pbase, prow(m), nz, col0, on);
     }
   }
-  V4<real> w[4], st[4];  // psi rows i-3..i, psi* rows i-4..i-1 (march order)
-  V4<real> f1, f2;       // carried y face fluxes of stage 1 and stage 2
-  V4<real> e1, e2;       // carried y differences of stage 1 and stage 2
+  __device__ __forceinline__ void store_row(int m, const Vk<real, KV> &x) {
+    if (VEC) {
+      if (!own) return;
+      IO::store_vec(srow0 + m * sstep, x);
+    } else {
+      IO::store(pbase, prow(m), nz, col0, own, x);
+    }
+  }
+  Vk<real, KV> w[4], st[4];  // psi rows i-3..i, psi* rows i-4..i-1 (march order)
+  Vk<real, KV> f1, f2;       // carried y face fluxes of stage 1 and stage 2
+  Vk<real, KV> e1, e2;       // carried y differences of stage 1 and stage 2
 
   __device__ __forceinline__ int prow(int m) const { return fwd ? m : ny - 1 - m; }
 
@@ -312,14 +325,14 @@ struct PlaneMarch {
     rd = 0;
 #pragma unroll
     for (int j = 0; j < kP; j++) {
-      if (j < ny) issue_row(ring + wr * 32 * kV, j);
+      if (j < ny) issue_row(ring + wr * 32 * KV, j);
       cp_async_commit();
       wr++;
     }
 #pragma unroll
     for (int k = 0; k < 4; k++)
 #pragma unroll
-      for (int j = 0; j < kV; j++) w[k].v[j] = st[k].v[j] = real(0);
+      for (int j = 0; j < KV; j++) w[k].v[j] = st[k].v[j] = real(0);
   }
 
   // One march iteration i.  LOAD: row i exists (i < ny).  S1: stage 1 for
@@ -328,15 +341,15 @@ struct PlaneMarch {
   template <bool LOAD, bool S1, bool FIRST1, bool IN1, bool S2, bool FIRST2>
   __device__ __forceinline__ void iter(int i) {
     cp_async_wait<kP - 1>();
-    V4<real> x;
+    Vk<real, KV> x;
     if (LOAD) {
-      RowIO<real, VEC, FZ>::read(ring + rd * 32 * kV, x);
+      IO::read(ring + rd * 32 * KV, x);
     } else {
 #pragma unroll
-      for (int j = 0; j < kV; j++) x.v[j] = real(0);
+      for (int j = 0; j < KV; j++) x.v[j] = real(0);
     }
     rd = (rd + 1) & (kR - 1);
-    if (i + kP < ny) issue_row(ring + wr * 32 * kV, i + kP);
+    if (i + kP < ny) issue_row(ring + wr * 32 * KV, i + kP);
     cp_async_commit();
     wr = (wr + 1) & (kR - 1);
 #pragma unroll
@@ -345,19 +358,19 @@ struct PlaneMarch {
 
     if (S1) {  // row m = i-1 needs psi(m-2..m+1) = w[0..3]
       if (FIRST1) {
-        const V4<real> d = sub4(w[2], w[1]);
+        const Vk<real, KV> d = sub4(w[2], w[1]);
         f1 = face4(sy, w[1], slope4(sub4(w[1], w[0]), d));  // face m - 1/2
         e1 = d;
       }
-      V4<real> dz, s;
+      Vk<real, KV> dz, s;
       z_delta(w[2], gz, zl, zr, gw, dz);
-      const V4<real> d = sub4(w[3], w[2]);
-      const V4<real> fh = face4(sy, w[2], slope4(e1, d));  // face m + 1/2
+      const Vk<real, KV> d = sub4(w[3], w[2]);
+      const Vk<real, KV> fh = face4(sy, w[2], slope4(e1, d));  // face m + 1/2
       e1 = d;
       s = upd4(w[2], f1, fh, dz);
       if (!IN1 || !VEC) {
 #pragma unroll
-        for (int j = 0; j < kV; j++)
+        for (int j = 0; j < KV; j++)
           if (!(IN1 && (VEC || col0 + j < nz))) s.v[j] = real(0);
       }
       f1 = fh;
@@ -367,18 +380,18 @@ struct PlaneMarch {
     }
     if (S2) {  // row m' = i-2 needs psi*(m'-2..m'+1) = st[0..3] and psi(m') = w[1]
       if (FIRST2) {
-        const V4<real> d = sub4(st[2], st[1]);
+        const Vk<real, KV> d = sub4(st[2], st[1]);
         f2 = face4(sy, st[1], slope4(sub4(st[1], st[0]), d));
         e2 = d;
       }
-      V4<real> dz, o;
+      Vk<real, KV> dz, o;
       z_delta(st[2], gz, zl, zr, gw, dz);
-      const V4<real> d = sub4(st[3], st[2]);
-      const V4<real> fh = face4(sy, st[2], slope4(e2, d));
+      const Vk<real, KV> d = sub4(st[3], st[2]);
+      const Vk<real, KV> fh = face4(sy, st[2], slope4(e2, d));
       e2 = d;
       o = upd4(add4(w[1], st[2]), f2, fh, dz);
 #pragma unroll
-      for (int j = 0; j < kV; j++) o.v[j] *= real(0.5);
+      for (int j = 0; j < KV; j++) o.v[j] *= real(0.5);
       f2 = fh;
       store_row(i - 2, o);
     }
@@ -407,10 +420,10 @@ struct PlaneMarch {
   }
 };
 
-template <typename real, bool VEC, bool FZ>
+template <typename real, bool VEC, bool FZ, int KV>
 __device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int nz, int col0, int gw, bool fwd,
                                             bool on, bool own, real sy, real gz, real zl, real zr) {
-  PlaneMarch<real, VEC, FZ> pm;
+  PlaneMarch<real, VEC, FZ, KV> pm;
   pm.ring = ring;
   pm.pbase = pbase;
   pm.ny = ny;
@@ -437,7 +450,7 @@ __device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int
 // upstream and 2 downstream, so the owned columns come out exact while the halo
 // lanes' own results (their outer neighbours are missing) are discarded.  A
 // task is one (plane, segment).
-template <typename real, bool VEC, bool FZ>
+template <typename real, bool VEC, bool FZ, int KV>
 __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict__ psi, long long nplanes, int ny, int nz,
                                                                 int na, int a0, int na_half, int nu, int nv, real du,
                                                                 real dv, real ky, real kz, int nseg, int seg_w, int gw) {
@@ -448,7 +461,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
   const int gi = lane / gw;
   const long long gwarp = (long long)blockIdx.x * kWarps + warp;
   const long long nwarps = (long long)gridDim.x * kWarps;
-  real *ring = reinterpret_cast<real *>(smem_raw) + ((size_t)warp * kR * 32 + lane) * kV;
+  real *ring = reinterpret_cast<real *>(smem_raw) + ((size_t)warp * kR * 32 + lane) * KV;
   const int li = lane % gw;
   const long long ntasks = nplanes * nseg;
 
@@ -463,10 +476,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
     // owned columns [s0, s1), loaded columns [s0 - left halo, hi)
     const int s0 = seg * seg_w;
     const int s1 = min(nz, s0 + seg_w);
-    const int c_lo = seg > 0 ? s0 - kV : 0;
-    const int hi = seg < nseg - 1 ? min(nz, s1 + kV) : nz;
-    const int lp = (hi - c_lo + kV - 1) / kV;  // lanes of this segment
-    const int col0 = c_lo + li * kV;
+    const int c_lo = seg > 0 ? s0 - KV : 0;
+    const int hi = seg < nseg - 1 ? min(nz, s1 + KV) : nz;
+    const int lp = (hi - c_lo + KV - 1) / KV;  // lanes of this segment
+    const int col0 = c_lo + li * KV;
     const bool on = valid && li < lp;
     const bool own = on && col0 >= s0 && col0 < s1;
     const real zl = li == 0 ? real(0) : real(1);
@@ -474,49 +487,63 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
     const real uu = (real)((a % nu) - 0.5 * (nu - 1)) * du;
     const real vv = (real)((a / nu) - 0.5 * (nv - 1)) * dv;
     real *pbase = psi + plane * (long long)ny * nz;
-    march_plane<real, VEC, FZ>(ring, pbase, ny, nz, col0, gw, uu >= real(0), on, own, fabs(uu) * ky,
+    march_plane<real, VEC, FZ, KV>(ring, pbase, ny, nz, col0, gw, uu >= real(0), on, own, fabs(uu) * ky,
                                fabs(vv) * kz, zl, zr);
   }
   cp_async_wait<0>();
 }
 
 // Segments of a row of nz columns: one if it fits a warp, else segments of at
-// most 120 owned columns (with both halo lanes, 32 lanes).
-void row_segments(int nz, int &nseg, int &seg_w, int &lanes) {
-  if (nz <= 32 * kV) {
+// most 30 KV owned columns (with both halo lanes, 32 lanes).
+void row_segments(int nz, int kv, int &nseg, int &seg_w, int &lanes) {
+  if (nz <= 32 * kv) {
     nseg = 1;
     seg_w = nz;
-    lanes = (nz + kV - 1) / kV;
+    lanes = (nz + kv - 1) / kv;
     return;
   }
-  const int wmax = (32 - 2) * kV;
+  const int wmax = (32 - 2) * kv;
   nseg = (nz + wmax - 1) / wmax;
-  seg_w = ((nz + nseg - 1) / nseg + kV - 1) / kV * kV;
-  lanes = seg_w / kV + 2;
+  seg_w = ((nz + nseg - 1) / nseg + kv - 1) / kv * kv;
+  lanes = seg_w / kv + 2;
 }
 
-}  // namespace
+// Fraction of the lane columns of the launched warps that hold owned columns.
+double lane_use(int nz, int kv) {
+  int nseg, seg_w, lanes;
+  row_segments(nz, kv, nseg, seg_w, lanes);
+  int gw = 1;
+  while (gw < lanes) gw <<= 1;
+  return (double)nz / ((double)nseg * gw * kv);
+}
 
-template <typename real>
-cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
-                                  double dy, double dz) {
+// Columns per lane: 6 where rows split evenly into 6-column lanes and that
+// fills the warps better than 4 (rows of 48, 96 or 192 columns), else 4.
+int pick_kv(int nz) {
+  if (nz % 6 == 0 && lane_use(nz, 6) > lane_use(nz, 4) + 0.05) return 6;
+  return 4;
+}
+
+template <typename real, int KV>
+cudaError_t launch_kv(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv, double dy,
+                      double dz) {
   const long long nstacks = (long long)d.ncomp * d.ng * 2;
   // angles with v >= 0 (rows j >= nv / 2; for odd nv the middle row has v = 0)
   const int a_split = (d.nv / 2) * d.nu;
   int nseg, seg_w, lp;
-  row_segments(d.nz, nseg, seg_w, lp);
+  row_segments(d.nz, KV, nseg, seg_w, lp);
   int gw = 1;
   while (gw < lp) gw <<= 1;
-  const bool vec = (d.nz % kV) == 0;
-  const size_t smem = (size_t)kWarps * kR * 32 * kV * sizeof(real);
+  const bool vec = (d.nz % KV) == 0;
+  const size_t smem = (size_t)kWarps * kR * 32 * KV * sizeof(real);
   for (int half = 0; half < 2; half++) {
     const bool fz = half == 1;
     const int a0 = fz ? a_split : 0;
     const int na_half = fz ? d.na - a_split : a_split;
     if (na_half == 0) continue;
     const long long nplanes = nstacks * na_half;
-    auto kern = vec ? (fz ? k_transport_rows<real, true, true> : k_transport_rows<real, true, false>)
-                    : (fz ? k_transport_rows<real, false, true> : k_transport_rows<real, false, false>);
+    auto kern = vec ? (fz ? k_transport_rows<real, true, true, KV> : k_transport_rows<real, true, false, KV>)
+                    : (fz ? k_transport_rows<real, false, true, KV> : k_transport_rows<real, false, false, KV>);
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
     if (e != cudaSuccess) return e;
@@ -533,6 +560,16 @@ cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+}  // namespace
+
+template <typename real>
+cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
+                                  double dy, double dz) {
+  const int kv = lc.transport_cols ? lc.transport_cols : pick_kv(d.nz);
+  if (kv == 6) return launch_kv<real, 6>(lc, d, psi, tau, du, dv, dy, dz);
+  return launch_kv<real, 4>(lc, d, psi, tau, du, dv, dy, dz);
 }
 
 template cudaError_t launch_transport_rows<double>(const LaunchCtx &, const Dims &, double *, double, double, double,

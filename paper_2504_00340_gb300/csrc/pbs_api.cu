@@ -53,7 +53,7 @@ struct pbs_ctx {
   size_t rsize, ssize;  // element sizes of real and of the source storage
   long long launches = 0;
   // launch shapes (pbs_autotune / pbs_set_tuning)
-  pbs_tuning tune{8, 1, 0, 2, 1};
+  pbs_tuning tune{8, 1, 0, 0, 2, 1};
   // whole-march CUDA graph (pbs_run with use_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -125,6 +125,7 @@ LaunchCtx lctx(pbs_ctx *c) {
   lc.energy_angles = c->tune.energy_angles;
   lc.energy_form = c->tune.energy_form;
   lc.transport_ctas = c->tune.transport_ctas;
+  lc.transport_cols = c->tune.transport_cols;
   lc.angular_form = c->tune.angular_form;
   lc.source_form = c->tune.source_form;
   return lc;
@@ -694,12 +695,17 @@ pbs_status autotune_impl(pbs_ctx *c, int reps) {
   c->tune = pick;
   best = 1e30f;
   if (r == PBS_OK) {
-    for (int ctas : {1, 2, 3, 4, 0}) {
-      c->tune.transport_ctas = ctas;
-      float ms;
-      r = time_best([&] { return transport_run<real>(c, 0.5 * c->dx, c->B); }, ms);
+    for (int cols : {4, 6}) {
+      if (cols == 6 && c->nz % 6 != 0) continue;
+      for (int ctas : {1, 2, 3, 4, 0}) {
+        c->tune.transport_cols = cols;
+        c->tune.transport_ctas = ctas;
+        float ms;
+        r = time_best([&] { return transport_run<real>(c, 0.5 * c->dx, c->B); }, ms);
+        if (r != PBS_OK) break;
+        if (ms < best) { best = ms; pick.transport_ctas = ctas; pick.transport_cols = cols; }
+      }
       if (r != PBS_OK) break;
-      if (ms < best) { best = ms; pick.transport_ctas = ctas; }
     }
   }
   c->tune = pick;
@@ -947,7 +953,8 @@ pbs_status pbs_autotune(pbs_ctx *c, int reps) {
 pbs_status pbs_set_tuning(pbs_ctx *c, const pbs_tuning *t) {
   if (!c || !t) return fail(c, PBS_ERR_ARG, "null tuning");
   if ((t->energy_angles != 4 && t->energy_angles != 8 && t->energy_angles != 16) || t->energy_form < 0 ||
-      t->energy_form > 1 || t->transport_ctas < 0 || t->transport_ctas > 64 || t->angular_form < 0 ||
+      t->energy_form > 1 || t->transport_ctas < 0 || t->transport_ctas > 64 ||
+      (t->transport_cols != 0 && t->transport_cols != 4 && t->transport_cols != 6) || t->angular_form < 0 ||
       t->angular_form > 2 || t->source_form < 0 || t->source_form > 1)
     return fail(c, PBS_ERR_ARG, "tuning value out of range");
   c->tune = *t;

@@ -111,12 +111,18 @@ def test_energy_substep_with_source_chain(orc, precision, tol, ny, nz):
     s2.close()
 
 
+@pytest.mark.parametrize("cols", [0, 4, 6])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("ny,nz", [(21, 12), (9, 5), (40, 32), (24, 128), (13, 100), (7, 144), (3, 64),
-                                   (5, 150), (6, 192), (3, 260)])
-def test_transport_substep(orc, precision, tol, ny, nz):
+                                   (5, 150), (6, 192), (3, 260), (4, 96), (5, 198)])
+def test_transport_substep(orc, precision, tol, ny, nz, cols):
+    """Rows of every width class: one lane group, several groups per warp,
+    segments with halo lanes, ragged (non-vector) rows; 4 or 6 columns per
+    lane (0: chosen by the row width; rows that are not a multiple of the
+    lane width take the per-column path)."""
     grid = _grid(ny, nz, 4, 6, 3)
     s, o, _ = _pair(orc, grid, 1, 0.05, 0, precision)
+    s.set_tuning(transport_cols=cols)
     psi = random_state((3, 2, 6, 4, ny, nz), seed=ny * nz)
     s.write_psi(0, psi)
     s.substep_transport(0.37)
