@@ -33,7 +33,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "phase-space cell-updates/s (mixed vs FP64, same GB300, dose err<=1e-3); % HBM peak"
+METRIC = "phase-space cell-updates/s (mixed vs FP64, same GB300, dose err\u22641e-3); % HBM peak"
 UNIT = "cell-updates/s"
 
 
