@@ -214,8 +214,8 @@ pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
  *   transport_ctas  resident CTAs per SM of the streaming transport, 0..64
  *                   (0 = as many as fit)
  *   transport_cols  columns of a row per lane of the streaming transport: 4,
- *                   6 or 0 (chosen by the row width nz: 6 where nz is a
- *                   multiple of 6 and that fills the warps better)
+ *                   6, 8 or 0 (chosen by the row width nz: 6 where nz is a
+ *                   multiple of 6 and that fills the warps better, else 4)
  *   angular_form    angular substep: 0 direct, 1 TMA-staged persistent
  *                   (needs a row pitch of ny*nz elements that is a multiple of
  *                   16 bytes), 2 packed FP32x2 (FP32, ny*nz even); a form the

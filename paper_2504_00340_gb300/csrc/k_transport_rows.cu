@@ -28,8 +28,9 @@ namespace pbs {
 
 namespace {
 
-// Columns per lane: KV = 4 or 6 (a template parameter; 6 fills a warp with
-// rows of 96 or 192 columns).
+// Columns per lane: KV = 4, 6 or 8 (a template parameter; 6 fills a warp with
+// rows of 96 or 192 columns; 8 spreads the per-row overheads over more
+// columns at the cost of registers).
 constexpr int kP = 6;        // rows in flight per lane
 constexpr int kR = 8;        // ring slots (a power of two >= kP + 1: slot indices wrap by a mask)
 constexpr int kWarps = 4;    // warps per CTA
@@ -544,8 +545,12 @@ cudaError_t launch_kv(const LaunchCtx &lc, const Dims &d, real *psi, double tau,
     const long long nplanes = nstacks * na_half;
     auto kern = vec ? (fz ? k_transport_rows<real, true, true, KV> : k_transport_rows<real, true, false, KV>)
                     : (fz ? k_transport_rows<real, false, true, KV> : k_transport_rows<real, false, false, KV>);
+    cudaError_t e;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (lc.transport_ctas > 0 && lc.transport_ctas < per_sm) per_sm = lc.transport_ctas;
@@ -569,6 +574,7 @@ cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi,
                                   double dy, double dz) {
   const int kv = lc.transport_cols ? lc.transport_cols : pick_kv(d.nz);
   if (kv == 6) return launch_kv<real, 6>(lc, d, psi, tau, du, dv, dy, dz);
+  if (kv == 8) return launch_kv<real, 8>(lc, d, psi, tau, du, dv, dy, dz);
   return launch_kv<real, 4>(lc, d, psi, tau, du, dv, dy, dz);
 }
 

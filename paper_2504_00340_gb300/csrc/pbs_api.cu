@@ -695,8 +695,8 @@ pbs_status autotune_impl(pbs_ctx *c, int reps) {
   c->tune = pick;
   best = 1e30f;
   if (r == PBS_OK) {
-    for (int cols : {4, 6}) {
-      if (cols == 6 && c->nz % 6 != 0) continue;
+    for (int cols : {4, 6, 8}) {
+      if (c->nz % cols != 0) continue;
       for (int ctas : {1, 2, 3, 4, 0}) {
         c->tune.transport_cols = cols;
         c->tune.transport_ctas = ctas;
@@ -954,7 +954,8 @@ pbs_status pbs_set_tuning(pbs_ctx *c, const pbs_tuning *t) {
   if (!c || !t) return fail(c, PBS_ERR_ARG, "null tuning");
   if ((t->energy_angles != 4 && t->energy_angles != 8 && t->energy_angles != 16) || t->energy_form < 0 ||
       t->energy_form > 1 || t->transport_ctas < 0 || t->transport_ctas > 64 ||
-      (t->transport_cols != 0 && t->transport_cols != 4 && t->transport_cols != 6) || t->angular_form < 0 ||
+      (t->transport_cols != 0 && t->transport_cols != 4 && t->transport_cols != 6 && t->transport_cols != 8) ||
+      t->angular_form < 0 ||
       t->angular_form > 2 || t->source_form < 0 || t->source_form > 1)
     return fail(c, PBS_ERR_ARG, "tuning value out of range");
   c->tune = *t;

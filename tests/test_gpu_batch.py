@@ -157,7 +157,7 @@ def test_autotune_and_forms_keep_results():
     t = s.tuning
     assert t["energy_angles"] in (4, 8, 16) and t["energy_form"] in (0, 1)
     assert t["transport_ctas"] in (0, 1, 2, 3, 4) and t["angular_form"] in (0, 1, 2)
-    assert t["transport_cols"] in (4, 6)
+    assert t["transport_cols"] in (4, 6, 8)
     assert s.depth == 0
     plain = dict(energy_angles=8, energy_form=0, transport_ctas=0, angular_form=0)
     shapes = [plain, dict(energy_angles=4, energy_form=0, transport_ctas=1, angular_form=0),

@@ -111,7 +111,7 @@ def test_energy_substep_with_source_chain(orc, precision, tol, ny, nz):
     s2.close()
 
 
-@pytest.mark.parametrize("cols", [0, 4, 6])
+@pytest.mark.parametrize("cols", [0, 4, 6, 8])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("ny,nz", [(21, 12), (9, 5), (40, 32), (24, 128), (13, 100), (7, 144), (3, 64),
                                    (5, 150), (6, 192), (3, 260), (4, 96), (5, 198)])
