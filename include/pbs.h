@@ -204,6 +204,20 @@ pbs_status pbs_set_beam_steps(pbs_ctx *ctx, const int *steps, int n);
  * work around it. */
 pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
 
+/* Method options (each changes the computed result, unlike pbs_tuning):
+ *   angular_integrator  time integration of each sine mode of the angular
+ *                       diffusion (Section 3.4): 0 Crank-Nicolson (Section
+ *                       3.3, the default), 1 the mode's exact exponential
+ *                       exp(h kappa lam / 2) (the "ODE solver" reading). */
+typedef struct {
+  int angular_integrator;
+} pbs_options;
+
+/* Set / read the method options; PBS_ERR_ARG for an unknown value.  The
+ * deferred closing E(h/2) of the march, if any, is applied first. */
+pbs_status pbs_set_options(pbs_ctx *ctx, const pbs_options *options);
+pbs_status pbs_get_options(const pbs_ctx *ctx, pbs_options *options);
+
 /* Launch shapes and kernel forms of the march.  Every setting computes the
  * same method; forms differ in how the work maps onto the GPU, and the
  * packed forms differ from the plain ones by rounding only.
@@ -244,6 +258,19 @@ pbs_status pbs_autotune(pbs_ctx *ctx, int reps);
  * ranges above). */
 pbs_status pbs_set_tuning(pbs_ctx *ctx, const pbs_tuning *tuning);
 pbs_status pbs_get_tuning(const pbs_ctx *ctx, pbs_tuning *tuning);
+
+/* Checkpoint / resume of the march state: psi of every component of every
+ * beam (working precision), dose, fluence, the beam projection factors, the
+ * per-beam depth ranges, the depth counter and a deferred closing E(h/2)
+ * (kept deferred, not applied).  The material and the tables are inputs,
+ * not state: set them on the restoring context as before.  pbs_checkpoint_size
+ * gives the bytes of the host buffer; save copies the state into it
+ * (synchronises); load restores a checkpoint written by a context with the
+ * same grid, precision, n_scatter and n_beams (PBS_ERR_ARG otherwise, or for
+ * a buffer that is not a checkpoint).  Host buffers are the caller's. */
+pbs_status pbs_checkpoint_size(const pbs_ctx *ctx, size_t *bytes);
+pbs_status pbs_checkpoint_save(pbs_ctx *ctx, void *host, size_t bytes);
+pbs_status pbs_checkpoint_load(pbs_ctx *ctx, const void *host, size_t bytes);
 
 /* Depth steps marched since pbs_launch_beam. */
 pbs_status pbs_get_depth(const pbs_ctx *ctx, int *steps_done);

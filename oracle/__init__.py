@@ -87,6 +87,7 @@ def _load():
             lib.orc_source.argtypes = [ctypes.c_void_p, _D, _D, _D]
             lib.orc_transport_substep.argtypes = [ctypes.c_void_p, ctypes.c_double, _D]
             lib.orc_angular_substep.argtypes = [ctypes.c_void_p, ctypes.c_double, _D, _D]
+            lib.orc_set_angular_exact.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_init_beam.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Beam), _D]
             lib.orc_march.restype = ctypes.c_int
             lib.orc_march.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Opts), ctypes.POINTER(_Beam), _D,
@@ -218,6 +219,11 @@ class Oracle:
         assert psi.shape == self.comp_shape
         self.lib.orc_transport_substep(self.ctx, float(h), _ptr(psi))
         return psi
+
+    def set_angular_exact(self, exact: bool):
+        """Angular time integrator: False = Crank-Nicolson (default), True =
+        the exact exponential of each sine mode."""
+        self.lib.orc_set_angular_exact(self.ctx, int(bool(exact)))
 
     def angular_substep(self, h: float, rho_yz, psi):
         psi = _f64(psi).copy()

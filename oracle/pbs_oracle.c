@@ -53,7 +53,13 @@ struct orc_ctx {
   double *p1;       /* [gp][g] probability of gp -> g */
   double *p2;       /* [g][a][ap] density in (u,v) of ap -> a */
   double *u, *v;    /* angle nodes */
+  int angular_exact; /* angular time integrator: 0 Crank-Nicolson, 1 exact exponential */
 };
+
+/* Angular time integrator (Section 3.4: the paper integrates each sine mode
+ * with "an ODE solver"; Section 3.3 prescribes Crank-Nicolson): 0 keeps CN,
+ * 1 takes each mode's exact solution exp(h kappa lam / 2). */
+void orc_set_angular_exact(orc_ctx *c, int exact) { c->angular_exact = exact != 0; }
 
 /* ------------------------------------------------------------------ */
 /* Physics tables (Appendix A with the Bragg-Kleeman and Highland      */
@@ -490,7 +496,7 @@ void orc_angular_substep(const orc_ctx *c, double h, const double *rho_yz, doubl
         double acc = 0.0;
         for (int j = 0; j < nv; j++) acc += sv[n * nv + j] * w[j * nu + m];
         double q = 0.25 * h * kappa * lam[n * nu + m];
-        t[n * nu + m] = acc * (1.0 + q) / (1.0 - q);
+        t[n * nu + m] = acc * (c->angular_exact ? exp(2.0 * q) : (1.0 + q) / (1.0 - q));
       }
     /* inverse (the orthonormal DST-I is its own inverse), same two sums */
     for (int j = 0; j < nv; j++)

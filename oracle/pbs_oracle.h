@@ -54,6 +54,7 @@ void orc_energy_substep(const orc_ctx *c, double h, const double *rho_yz, double
 void orc_source(const orc_ctx *c, const double *rho_yz, const double *prev, double *out);
 void orc_transport_substep(const orc_ctx *c, double h, double *psi);
 void orc_angular_substep(const orc_ctx *c, double h, const double *rho_yz, double *psi);
+void orc_set_angular_exact(orc_ctx *c, int exact);
 void orc_init_beam(const orc_ctx *c, const orc_beam *b, double *psi);
 int orc_march(const orc_ctx *c, const orc_march_opts *o, const orc_beam *b, const double *rho, int n_steps,
               double dx, double *psi, double *dose, double *edep_w, double *fluence);

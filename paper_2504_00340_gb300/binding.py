@@ -53,6 +53,10 @@ class PbsTuning(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class PbsOptions(ctypes.Structure):
+    _fields_ = [("angular_integrator", ctypes.c_int)]
+
+
 class PbsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -73,11 +77,16 @@ SIGNATURES = [
     ("pbs_set_beam_steps", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     ("pbs_run", ctypes.c_int, [_VP, ctypes.c_int]),
     ("pbs_autotune", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("pbs_set_options", ctypes.c_int, [_VP, ctypes.POINTER(PbsOptions)]),
+    ("pbs_get_options", ctypes.c_int, [_VP, ctypes.POINTER(PbsOptions)]),
     ("pbs_set_tuning", ctypes.c_int, [_VP, ctypes.POINTER(PbsTuning)]),
     ("pbs_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(PbsTuning)]),
     ("pbs_step", ctypes.c_int, [_VP, ctypes.c_int]),
     ("pbs_flush", ctypes.c_int, [_VP]),
     ("pbs_get_depth", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    ("pbs_checkpoint_size", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    ("pbs_checkpoint_save", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    ("pbs_checkpoint_load", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("pbs_read_dose", ctypes.c_int, [_VP, _D, ctypes.c_size_t]),
     ("pbs_read_fluence", ctypes.c_int, [_VP, _D, ctypes.c_size_t]),
     ("pbs_read_psi", ctypes.c_int, [_VP, ctypes.c_int, _D, ctypes.c_size_t]),
@@ -196,6 +205,16 @@ def pbs_autotune(ctx, reps: int = 3) -> None:
     _check(ctx, load_library().pbs_autotune(_VP(ctx), int(reps)))
 
 
+def pbs_set_options(ctx, options: PbsOptions) -> None:
+    _check(ctx, load_library().pbs_set_options(_VP(ctx), ctypes.byref(options)))
+
+
+def pbs_get_options(ctx) -> PbsOptions:
+    o = PbsOptions()
+    _check(ctx, load_library().pbs_get_options(_VP(ctx), ctypes.byref(o)))
+    return o
+
+
 def pbs_set_tuning(ctx, tuning: PbsTuning) -> None:
     _check(ctx, load_library().pbs_set_tuning(_VP(ctx), ctypes.byref(tuning)))
 
@@ -212,6 +231,22 @@ def pbs_step(ctx, n_steps: int) -> None:
 
 def pbs_flush(ctx) -> None:
     _check(ctx, load_library().pbs_flush(_VP(ctx)))
+
+
+def pbs_checkpoint_size(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(ctx, load_library().pbs_checkpoint_size(_VP(ctx), ctypes.byref(n)))
+    return n.value
+
+
+def pbs_checkpoint_save(ctx, buf: np.ndarray) -> None:
+    assert buf.dtype == np.uint8 and buf.flags["C_CONTIGUOUS"]
+    _check(ctx, load_library().pbs_checkpoint_save(_VP(ctx), _VP(buf.ctypes.data), buf.size))
+
+
+def pbs_checkpoint_load(ctx, buf: np.ndarray) -> None:
+    assert buf.dtype == np.uint8 and buf.flags["C_CONTIGUOUS"]
+    _check(ctx, load_library().pbs_checkpoint_load(_VP(ctx), _VP(buf.ctypes.data), buf.size))
 
 
 def pbs_get_depth(ctx) -> int:
@@ -402,6 +437,11 @@ class Solver:
         transport_ctas, transport_cols, angular_form, source_form."""
         return pbs_get_tuning(self.ctx).as_dict()
 
+    def set_options(self, angular_integrator: str = "cn"):
+        """Method options: angular_integrator 'cn' (Crank-Nicolson, default)
+        or 'exact' (exact exponential of each sine mode)."""
+        pbs_set_options(self.ctx, PbsOptions({"cn": 0, "exact": 1}[angular_integrator]))
+
     def set_tuning(self, **kw):
         t = pbs_get_tuning(self.ctx)
         for k, v in kw.items():
@@ -413,6 +453,15 @@ class Solver:
 
     def flush(self):
         pbs_flush(self.ctx)
+
+    def checkpoint(self) -> np.ndarray:
+        """The march state as a host byte array (pbs_checkpoint_save)."""
+        buf = np.empty(pbs_checkpoint_size(self.ctx), dtype=np.uint8)
+        pbs_checkpoint_save(self.ctx, buf)
+        return buf
+
+    def restore(self, buf: np.ndarray):
+        pbs_checkpoint_load(self.ctx, np.ascontiguousarray(buf, dtype=np.uint8))
 
     @property
     def depth(self) -> int:

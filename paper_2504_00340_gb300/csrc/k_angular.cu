@@ -65,6 +65,7 @@ struct DstTab<double> {
 template <typename real>
 struct AngTables {
   real lam[kMaxAngle * kMaxAngle];  // eigenvalues [n][m]
+  int exact;                        // 0: Crank-Nicolson factor, 1: exact exponential
 };
 
 // y[m] = sum_i S[m][i] x[i] for an orthonormal DST-I of even length N.
@@ -87,6 +88,12 @@ __device__ __forceinline__ void dst_apply(const real (&x)[N], real (&y)[N]) {
 
 __device__ __forceinline__ double mode_factor(double den) { return 2.0 / den - 1.0; }
 __device__ __forceinline__ float mode_factor(float den) { return __fdividef(2.0f, den) - 1.0f; }
+
+// Factor of one sine mode over the step, ql = (h kappa / 4) lam <= 0:
+// Crank-Nicolson (1 + ql) / (1 - ql) = -1 + 2 / (1 - ql), or the exact
+// solution exp(2 ql) of the mode's ODE.
+__device__ __forceinline__ double mode_scale(double ql, int exact) { return exact ? exp(2.0 * ql) : mode_factor(1.0 - ql); }
+__device__ __forceinline__ float mode_scale(float ql, int exact) { return exact ? expf(2.0f * ql) : mode_factor(1.0f - ql); }
 
 template <typename real, int NU, int NV>
 __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
@@ -124,11 +131,7 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
     for (int j = 0; j < NV; j++) c[j] = tile[j * NU + t][x];
     dst_apply<real, NV>(c, y);
 #pragma unroll
-    for (int n = 0; n < NV; n++) {
-      // (1 + q lam) / (1 - q lam) = -1 + 2 / (1 - q lam); lam <= 0, so 1 - q lam >= 1
-      const real den = real(1) - q * tb.lam[n * NU + t];
-      y[n] *= mode_factor(den);
-    }
+    for (int n = 0; n < NV; n++) y[n] *= mode_scale(q * tb.lam[n * NU + t], tb.exact);  // lam <= 0
     dst_apply<real, NV>(y, c);
 #pragma unroll
     for (int j = 0; j < NV; j++) tile[j * NU + t][x] = c[j];
@@ -215,8 +218,8 @@ __global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV))
 #pragma unroll
     for (int n = 0; n < NV; n++) {
       const float l = tb.lam[n * NU + t];
-      y[n].x *= mode_factor(1.f - q.x * l);
-      y[n].y *= mode_factor(1.f - q.y * l);
+      y[n].x *= mode_scale(q.x * l, tb.exact);
+      y[n].y *= mode_scale(q.y * l, tb.exact);
     }
     dst_apply2<NV>(y, c);
 #pragma unroll
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
       for (int j = 0; j < NV; j++) c[j] = tl[j * NU + t][x];
       dst_apply<real, NV>(c, y);
 #pragma unroll
-      for (int n = 0; n < NV; n++) y[n] *= mode_factor(real(1) - q * tb.lam[n * NU + t]);
+      for (int n = 0; n < NV; n++) y[n] *= mode_scale(q * tb.lam[n * NU + t], tb.exact);
       dst_apply<real, NV>(y, c);
 #pragma unroll
       for (int j = 0; j < NV; j++) tl[j * NU + t][x] = c[j];
@@ -429,7 +432,8 @@ cudaError_t go_tma(const LaunchCtx &lc, const Dims &d, real *psi, const real *rh
 }
 
 template <typename real>
-void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv) {
+void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv, int exact) {
+  tb.exact = exact;
   const double pi = 3.14159265358979323846;
   for (int n = 0; n < nv; n++)
     for (int m = 0; m < nu; m++)
@@ -441,7 +445,7 @@ template <typename real, int NU, int NV>
 cudaError_t go(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts, double h, double du,
                double dv) {
   AngTables<real> tb;
-  fill_tables(tb, NU, NV, du, dv);
+  fill_tables(tb, NU, NV, du, dv, lc.angular_exact);
   if constexpr (sizeof(real) == 4) {
     if (lc.angular_form == 2 && (d.nyz % 2) == 0) return go_f2<NU, NV>(lc, d, psi, rho_yz, ts, h, tb);
   }

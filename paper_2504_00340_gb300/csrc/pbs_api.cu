@@ -54,6 +54,7 @@ struct pbs_ctx {
   long long launches = 0;
   // launch shapes (pbs_autotune / pbs_set_tuning)
   pbs_tuning tune{8, 1, 0, 0, 2, 1};
+  pbs_options opts{0};
   // whole-march CUDA graph (pbs_run with use_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -128,6 +129,7 @@ LaunchCtx lctx(pbs_ctx *c) {
   lc.transport_cols = c->tune.transport_cols;
   lc.angular_form = c->tune.angular_form;
   lc.source_form = c->tune.source_form;
+  lc.angular_exact = c->opts.angular_integrator;
   return lc;
 }
 
@@ -747,6 +749,22 @@ pbs_status autotune_impl(pbs_ctx *c, int reps) {
 
 }  // namespace
 
+// Checkpoint layout: CkptHeader, then psi (ncomp * comp_elems * rsize), dose
+// (B * nx * nyz doubles), fluence (B * (nx + 1) * nyz doubles), beam factors
+// (B * init_stride doubles), beam depth ranges (B ints).
+struct CkptHeader {
+  char magic[8];
+  int version, precision, ny, nz, ng, nu, nv, nx, K, B, steps_done, pending, have_beam, n_slabs_at_save;
+};
+
+namespace {
+size_t ckpt_bytes(const pbs_ctx *c) {
+  const size_t nyz = (size_t)c->ny * c->nz;
+  return sizeof(CkptHeader) + (size_t)c->d.ncomp * c->d.comp_elems * c->rsize + (size_t)c->B * c->nx * nyz * 8 +
+         (size_t)c->B * (c->nx + 1) * nyz * 8 + (size_t)c->B * init_stride(c) * 8 + (size_t)c->B * sizeof(int);
+}
+}  // namespace
+
 #define PBS_DISPATCH(c, FN, ...)                                                    \
   ((c)->precision == PBS_FP64    ? FN<double, double>(__VA_ARGS__)                  \
    : (c)->precision == PBS_FP32 ? FN<float, float>(__VA_ARGS__)                     \
@@ -963,6 +981,21 @@ pbs_status pbs_set_tuning(pbs_ctx *c, const pbs_tuning *t) {
   return PBS_OK;
 }
 
+pbs_status pbs_set_options(pbs_ctx *c, const pbs_options *o) {
+  if (!c || !o) return fail(c, PBS_ERR_ARG, "null options");
+  if (o->angular_integrator < 0 || o->angular_integrator > 1) return fail(c, PBS_ERR_ARG, "unknown angular integrator");
+  { pbs_status fr = c->ws ? PBS_DISPATCH(c, flush_impl, c) : PBS_OK; if (fr != PBS_OK) return fr; }
+  c->opts = *o;
+  drop_graph(c);
+  return PBS_OK;
+}
+
+pbs_status pbs_get_options(const pbs_ctx *c, pbs_options *o) {
+  if (!c || !o) return PBS_ERR_ARG;
+  *o = c->opts;
+  return PBS_OK;
+}
+
 pbs_status pbs_get_tuning(const pbs_ctx *c, pbs_tuning *t) {
   if (!c || !t) return PBS_ERR_ARG;
   *t = c->tune;
@@ -980,6 +1013,80 @@ pbs_status pbs_flush(pbs_ctx *c) {
   if (!c) return PBS_ERR_ARG;
   if (!c->ws) return PBS_OK;
   return PBS_DISPATCH(c, flush_impl, c);
+}
+
+pbs_status pbs_checkpoint_size(const pbs_ctx *c, size_t *bytes) {
+  if (!c || !bytes) return PBS_ERR_ARG;
+  *bytes = ckpt_bytes(c);
+  return PBS_OK;
+}
+
+pbs_status pbs_checkpoint_save(pbs_ctx *c, void *host, size_t bytes) {
+  if (!c || !host) return fail(c, PBS_ERR_ARG, "null buffer");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  if (bytes < ckpt_bytes(c)) return fail(c, PBS_ERR_ARG, "buffer smaller than pbs_checkpoint_size");
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "PBSCKPT1", 8);
+  h.version = 1;
+  h.precision = c->precision;
+  h.ny = c->ny; h.nz = c->nz; h.ng = c->ng; h.nu = c->nu; h.nv = c->nv; h.nx = c->nx; h.K = c->K; h.B = c->B;
+  h.steps_done = c->steps_done;
+  h.pending = c->pending ? 1 : 0;
+  h.have_beam = c->have_beam ? 1 : 0;
+  h.n_slabs_at_save = c->n_slabs;
+  unsigned char *p = static_cast<unsigned char *>(host);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const size_t nyz = (size_t)c->ny * c->nz;
+  const size_t parts[4][2] = {{c->off_psi, (size_t)c->d.ncomp * c->d.comp_elems * c->rsize},
+                              {c->off_dose, (size_t)c->B * c->nx * nyz * 8},
+                              {c->off_flu, (size_t)c->B * (c->nx + 1) * nyz * 8},
+                              {c->off_init, (size_t)c->B * init_stride(c) * 8}};
+  for (auto &q : parts) {
+    PBS_CUDA(c, cudaMemcpyAsync(p, at<void>(c, q[0]), q[1], cudaMemcpyDeviceToHost, c->stream));
+    p += q[1];
+  }
+  std::memcpy(p, c->beam_steps.data(), (size_t)c->B * sizeof(int));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  return check_device_status(c);
+}
+
+pbs_status pbs_checkpoint_load(pbs_ctx *c, const void *host, size_t bytes) {
+  if (!c || !host) return fail(c, PBS_ERR_ARG, "null buffer");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  if (bytes < sizeof(CkptHeader)) return fail(c, PBS_ERR_ARG, "not a checkpoint");
+  CkptHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (std::memcmp(h.magic, "PBSCKPT1", 8) != 0 || h.version != 1) return fail(c, PBS_ERR_ARG, "not a checkpoint");
+  if (h.precision != c->precision || h.ny != c->ny || h.nz != c->nz || h.ng != c->ng || h.nu != c->nu ||
+      h.nv != c->nv || h.nx != c->nx || h.K != c->K || h.B != c->B)
+    return fail(c, PBS_ERR_ARG, "checkpoint of another grid, precision or batch");
+  if (bytes < ckpt_bytes(c)) return fail(c, PBS_ERR_ARG, "truncated checkpoint");
+  const int *steps = reinterpret_cast<const int *>(static_cast<const unsigned char *>(host) + ckpt_bytes(c) -
+                                                   (size_t)c->B * sizeof(int));
+  for (int b = 0; b < c->B; b++)
+    if (steps[b] < 0 || steps[b] > c->nx || (b > 0 && steps[b] > steps[b - 1]))
+      return fail(c, PBS_ERR_ARG, "corrupt checkpoint (beam depths)");
+  if (h.steps_done < 0 || h.steps_done > c->nx) return fail(c, PBS_ERR_ARG, "corrupt checkpoint (depth)");
+  const unsigned char *p = static_cast<const unsigned char *>(host) + sizeof(h);
+  const size_t nyz = (size_t)c->ny * c->nz;
+  const size_t parts[4][2] = {{c->off_psi, (size_t)c->d.ncomp * c->d.comp_elems * c->rsize},
+                              {c->off_dose, (size_t)c->B * c->nx * nyz * 8},
+                              {c->off_flu, (size_t)c->B * (c->nx + 1) * nyz * 8},
+                              {c->off_init, (size_t)c->B * init_stride(c) * 8}};
+  for (auto &q : parts) {
+    PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, q[0]), p, q[1], cudaMemcpyHostToDevice, c->stream));
+    p += q[1];
+  }
+  PBS_CUDA(c, cudaMemsetAsync(at<void>(c, c->off_err), 0, 64, c->stream));
+  PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->beam_steps.assign(steps, steps + c->B);
+  c->steps_done = h.steps_done;
+  c->pending = h.pending != 0;
+  c->have_beam = h.have_beam != 0;
+  drop_graph(c);
+  return PBS_OK;
 }
 
 pbs_status pbs_get_depth(const pbs_ctx *c, int *s) {

@@ -155,6 +155,7 @@ struct LaunchCtx {
   int energy_form = 1;     // FP32 energy substep: 0 one lane per thread, 1 packed FP32x2
                            // (form 1 where the grid allows, else 0)
   int source_form = 1;     // BF16 source contraction: 0 tile by tile, 1 TMA/MMA/epilogue pipeline
+  int angular_exact = 0;   // angular time integrator: 0 Crank-Nicolson, 1 exact exponential per mode
 };
 
 // One E substep's per-lane inputs and outputs: density of its slab, c = h/2,

@@ -106,3 +106,47 @@ def test_empty_calls():
     with pytest.raises(binding.PbsError):
         s.step(4)  # past the material
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume(orc, precision):
+    """March 3 steps, checkpoint (with the closing half still deferred),
+    march 3 more; a fresh context restored from the checkpoint and marched
+    the same 3 steps gives the same dose, fluence and psi; both equal the
+    oracle's 6-step march (FP64)."""
+    grid = _grid(10, 12, 8, 8, 20)
+    nx, dx = 6, 0.05
+    rho = np.random.default_rng(11).uniform(0.5, 1.5, size=(nx, 10, 12))
+    beams = [dict(e0=45.0, sigma_e=1.0, sigma_y=0.25, sigma_z=0.25), dict(e0=38.0, sigma_e=1.0, sigma_y=0.3)]
+
+    def make():
+        s = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision=precision, n_beams=2)
+        s.set_material(rho)
+        return s
+
+    a = make()
+    a.set_beam_steps([6, 5])
+    a.launch_beams(beams)
+    a.step(3)
+    ck = a.checkpoint()
+    a.step(3)
+    ref = (a.read_dose(), a.read_fluence(), a.read_psi(0), a.read_psi(3))
+    b = make()
+    b.restore(ck)
+    assert b.depth == 3
+    b.step(3)
+    got = (b.read_dose(), b.read_fluence(), b.read_psi(0), b.read_psi(3))
+    for x, y in zip(got, ref):
+        assert _relerr(x, y) < (1e-12 if precision == "fp64" else 1e-6)
+    if precision == "fp64":
+        o = orc.Oracle(grid).march(rho, nx, dx, beam=beams[0], n_scatter=1)
+        assert _relerr(got[0][0], o["dose"]) < 1e-10
+    bad = ck.copy()
+    bad[:8] = 0
+    with pytest.raises(binding.PbsError):
+        b.restore(bad)
+    other = binding.Solver(grid, nx=nx, dx=dx, n_scatter=0, precision=precision, n_beams=2)
+    with pytest.raises(binding.PbsError):
+        other.restore(ck)  # another scattering order
+    for s in (a, b, other):
+        s.close()

@@ -146,6 +146,43 @@ def test_angular_substep(orc, precision, tol, nu, nv):
     s.close()
 
 
+@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
+@pytest.mark.parametrize("nu,nv", [(16, 16), (8, 8)])
+def test_angular_exact_integrator(orc, precision, tol, form, nu, nv):
+    """The exact-exponential angular integrator in every kernel form (direct,
+    TMA-staged, packed) against the oracle's."""
+    grid = _grid(12, 16, nu, nv, 5)
+    s, o, rho = _pair(orc, grid, 2, 0.05, 1, precision)
+    s.set_options("exact")
+    s.set_tuning(angular_form=form)
+    o.set_angular_exact(True)
+    psi = [random_state((5, 2, nv, nu, 12, 16), seed=27 + k) for k in range(2)]
+    for k in range(2):
+        s.write_psi(k, psi[k])
+    s.substep_angular(3.0, 1)
+    for k in range(2):
+        assert _relerr(s.read_psi(k), o.angular_substep(3.0, rho[1], psi[k])) < tol
+    s.close()
+
+
+def test_full_march_exact_angular_fp64(orc):
+    grid = _grid(14, 12, 8, 8, 24)
+    nx, dx = 8, 0.05
+    s, o, rho = _pair(orc, grid, nx, dx, 1, "fp64")
+    s.set_options("exact")
+    o.set_angular_exact(True)
+    beam = dict(e0=50.0, sigma_e=1.0, sigma_y=0.3, sigma_z=0.25)
+    s.launch_beam(**beam)
+    s.step(nx)
+    ref = o.march(rho, nx, dx, beam=beam, n_scatter=1)
+    assert _relerr(s.read_dose(), ref["dose"]) < 1e-10
+    o.set_angular_exact(False)
+    cn = o.march(rho, nx, dx, beam=beam, n_scatter=1)
+    assert _relerr(cn["dose"], ref["dose"]) > 1e-9  # the option changes the result
+    s.close()
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("ny,nz,nu,nv,ng", [(12, 16, 16, 16, 80), (6, 12, 8, 8, 150), (10, 10, 4, 6, 200)])
 def test_angular_substep_tma_pipeline(orc, precision, tol, ny, nz, nu, nv, ng):

@@ -170,6 +170,37 @@ def test_angular_dst_equals_dense_cn_solve(oracle_mod, nu, nv):
                     assert np.allclose(out[g, c, :, :, p, q].reshape(-1), ref, rtol=1e-11, atol=1e-13)
 
 
+@pytest.mark.parametrize("nu,nv", [(4, 4), (6, 3), (8, 8)])
+def test_angular_exact_integrator_equals_matrix_exponential(oracle_mod, nu, nv):
+    """The exact-exponential angular integrator (the paper's "ODE solver"
+    reading) equals the exact solution of the semi-discrete system,
+    expm(h kappa/2 L) psi with L the dense Kronecker five-point Laplacian
+    (scipy's expm), and it is a semigroup: two steps h/2 = one step h."""
+    from scipy.linalg import expm
+    o = oracle_mod.Oracle(_grid(3, 2, nu, nv, ng=2))
+    o.set_angular_exact(True)
+    ts = o.tables()["ts"]
+    rng = np.random.default_rng(3)
+    psi = rng.random(o.comp_shape)
+    rho = np.array([[1.0, 1.85], [0.26, 1.0], [0.7, 1.3]])
+    h = 2.5
+    out = o.angular_substep(h, rho, psi)
+    lap = np.kron(np.eye(nv), _dense_laplacian(nu, o.du)) + np.kron(_dense_laplacian(nv, o.dv), np.eye(nu))
+    for g in range(2):
+        for c in range(2):
+            for p in range(3):
+                for q in range(2):
+                    k = rho[p, q] * ts[g]
+                    ref = expm(0.5 * h * k * lap) @ psi[g, c, :, :, p, q].reshape(-1)
+                    assert np.allclose(out[g, c, :, :, p, q].reshape(-1), ref, rtol=1e-10, atol=1e-13)
+    half = o.angular_substep(0.5 * h, rho, o.angular_substep(0.5 * h, rho, psi))
+    assert np.allclose(half, out, rtol=1e-12, atol=1e-14)
+    # Crank-Nicolson is not a semigroup: the two integrators differ at this step
+    o.set_angular_exact(False)
+    cn = o.angular_substep(h, rho, psi)
+    assert np.abs(cn - out).max() > 1e-6 * np.abs(out).max()
+
+
 def test_angular_mass_change_is_wall_flux(oracle_mod):
     """d/dx sum psi = (kappa/2) [sum of -(psi_1 + psi_N)/du^2 over rows and
     columns]; CN makes the change the trapezoid of that wall term."""
