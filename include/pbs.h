@@ -89,13 +89,21 @@ typedef struct {
   const double *e_faces;   /* ng+1 ascending group faces (MeV), borrowed    */
 } pbs_grid;
 
-/* Physics of water-equivalent media (Appendix A with substitutes): mass
- * stopping power from the Bragg-Kleeman range law R = bk_alpha E^bk_p,
- * multiple-scattering power (Highland form) T = (es / pv)^2 / x0 used as
- * rho * sigma_tr, catastrophic removal sigma_ct (cm^2/g), exponential energy
- * transfer P^1 with rate lambda_p1 (1/MeV) and Gamma(g_alpha, g_beta)
- * angular deflection P^2 (Section 4 and Appendix A.4).  s_scale and ts_scale
- * multiply S and the scattering power (0 switches a process off). */
+/* Physics of water-equivalent media.  model = 0 (Appendix A with
+ * substitutes): mass stopping power from the Bragg-Kleeman range law
+ * R = bk_alpha E^bk_p, multiple-scattering power (Highland form)
+ * T = (es / pv)^2 / x0 used as rho * sigma_tr.  model = 1 (Appendix A as
+ * printed, for water): Bethe-Bloch stopping power per element with the
+ * piecewise I-value rule, combined by Bragg additivity over the mass
+ * fractions of H and O (density correction 0; held constant below
+ * max(dE_1 / 2, 0.5 MeV)), and the screened-Rutherford momentum-transfer
+ * cross section summed over the atoms of a gram (group-averaged by 8-point
+ * Gauss-Legendre); bk_*, x0 and es are then unused.  Both: catastrophic
+ * removal sigma_ct (cm^2/g), exponential energy transfer P^1 with rate
+ * lambda_p1 (1/MeV) and Gamma(g_alpha, g_beta) angular deflection P^2
+ * (Section 4 and Appendix A.4); s_scale and ts_scale multiply S and the
+ * scattering power (0 switches a process off); mp is the proton rest
+ * energy (MeV). */
 typedef struct {
   double bk_alpha, bk_p;
   double x0;
@@ -105,6 +113,7 @@ typedef struct {
   double lambda_p1;
   double g_alpha, g_beta;
   double s_scale, ts_scale;
+  int model;
 } pbs_physics;
 
 /* Pencil beam of Eq. (bdy): Gaussian in y, z (cm), u, v and E (MeV). */

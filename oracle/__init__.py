@@ -40,7 +40,7 @@ class _Grid(ctypes.Structure):
 class _Phys(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("bk_alpha", "bk_p", "x0", "mp", "es", "sigma_ct", "lambda_p1",
-                 "g_alpha", "g_beta", "s_scale", "ts_scale")]
+                 "g_alpha", "g_beta", "s_scale", "ts_scale")] + [("model", ctypes.c_int)]
 
 
 class _Beam(ctypes.Structure):
@@ -79,6 +79,13 @@ def _load():
             lib.orc_get_tables.argtypes = [ctypes.c_void_p] + [_D] * 7
             lib.orc_highland.restype = ctypes.c_double
             lib.orc_highland.argtypes = [ctypes.POINTER(_Phys), ctypes.c_double]
+            for fn in ("orc_bethe_water", "orc_scat_power_water"):
+                getattr(lib, fn).restype = ctypes.c_double
+                getattr(lib, fn).argtypes = [ctypes.POINTER(_Phys), ctypes.c_double]
+            for fn in ("orc_bethe_element", "orc_sigma_tr_element"):
+                getattr(lib, fn).restype = ctypes.c_double
+                getattr(lib, fn).argtypes = [ctypes.POINTER(_Phys), ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double]
             lib.orc_energy_blocks.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D, _D]
             lib.orc_energy_apply.argtypes = [ctypes.c_void_p, ctypes.c_double, _D, _D]
             lib.orc_energy_cn_lane.restype = ctypes.c_double
@@ -111,7 +118,7 @@ def _f64(a):
 
 
 DEFAULT_PHYS = dict(bk_alpha=0.0022, bk_p=1.77, x0=36.08, mp=938.272, es=13.6, sigma_ct=0.012,
-                    lambda_p1=0.05, g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0)
+                    lambda_p1=0.05, g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0, model=0)
 
 
 def num_threads() -> int:
@@ -126,6 +133,30 @@ def highland(e: float, **phys) -> float:
     p = dict(DEFAULT_PHYS)
     p.update(phys)
     return _load().orc_highland(ctypes.byref(_Phys(**p)), float(e))
+
+
+def _phys(phys):
+    p = dict(DEFAULT_PHYS)
+    p.update(phys)
+    return ctypes.byref(_Phys(**p))
+
+
+def bethe_water(e: float, **phys) -> float:
+    """Mass stopping power of water (MeV cm^2/g), Bethe-Bloch + Bragg additivity."""
+    return _load().orc_bethe_water(_phys(phys), float(e))
+
+
+def bethe_element(z: float, a: float, e: float, **phys) -> float:
+    return _load().orc_bethe_element(_phys(phys), float(z), float(a), float(e))
+
+
+def sigma_tr_element(z: float, a: float, e: float, **phys) -> float:
+    """Screened-Rutherford momentum-transfer cross section per atom (cm^2)."""
+    return _load().orc_sigma_tr_element(_phys(phys), float(z), float(a), float(e))
+
+
+def scat_power_water(e: float, **phys) -> float:
+    return _load().orc_scat_power_water(_phys(phys), float(e))
 
 
 class Oracle:

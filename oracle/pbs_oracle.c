@@ -88,6 +88,58 @@ double orc_highland(const orc_phys *ph, double e) {
   return ph->ts_scale * (ph->es / pv) * (ph->es / pv) / ph->x0;
 }
 
+/* The paper's own tables (Appendix A), for water as the paper's examples.
+ * Stopping power: Bethe-Bloch per element with the density correction taken
+ * as 0 (protons of at most a few hundred MeV) and the piecewise I-value rule
+ * of Appendix A.1, combined by Bragg additivity over the mass fractions.
+ * Scattering: the screened-Rutherford momentum-transfer cross section of
+ * Appendix A.3 per atom, summed over the atoms of one gram; with
+ * (rho sigma_tr / 2)(d_uu + d_vv) it is the growth of <u^2> per unit
+ * density and length, the same role as the Highland power. */
+#define ORC_ME 0.51099895   /* electron rest energy, MeV */
+#define ORC_KB 0.307075     /* 4 pi N_A r_e^2 m_e c^2, MeV cm^2 / mol */
+#define ORC_E2 1.439964e-13 /* e^2 / (4 pi eps0), MeV cm */
+#define ORC_FS (1.0 / 137.035999)
+#define ORC_NA 6.02214076e23
+#define ORC_AMU 931.494     /* MeV per atomic mass unit */
+
+/* Z, A (g/mol), mass fraction of water */
+static const double orc_water[2][3] = {{1.0, 1.00794, 0.111894}, {8.0, 15.9994, 0.888106}};
+
+static double i_value_mev(double z) {
+  double ev = (z < 1.5) ? 19.0 : (z <= 13.0 ? 11.2 + 11.7 * z : 52.8 + 8.71 * z);
+  return ev * 1e-6;
+}
+
+double orc_bethe_element(const orc_phys *ph, double z, double a, double e) {
+  double gam = 1.0 + e / ph->mp, b2 = 1.0 - 1.0 / (gam * gam);
+  return ORC_KB * z / a / b2 * (log(2.0 * ORC_ME * b2 * gam * gam / i_value_mev(z)) - b2);
+}
+
+double orc_bethe_water(const orc_phys *ph, double e) {
+  double s = 0.0;
+  for (int k = 0; k < 2; k++) s += orc_water[k][2] * orc_bethe_element(ph, orc_water[k][0], orc_water[k][1], e);
+  return s;
+}
+
+double orc_sigma_tr_element(const orc_phys *ph, double z, double a, double e) {
+  double gam = 1.0 + e / ph->mp, b2 = 1.0 - 1.0 / (gam * gam);
+  double mt = a * ORC_AMU;                 /* target nucleus */
+  double m0 = ph->mp * mt / (ph->mp + mt); /* reduced mass */
+  double r = z * ORC_E2 / (m0 * b2);       /* z_i Z e^2 / (4 pi eps0 m0 v^2), z_i = 1 */
+  double p = sqrt(e * (e + 2.0 * ph->mp)); /* MeV / c */
+  double th = cbrt(z) * ORC_FS * ORC_ME / p;
+  double eta = th * th;
+  return 2.0 * 3.14159265358979323846 * r * r * (log((eta + 1.0) / eta) - 1.0 / (eta + 1.0));
+}
+
+double orc_scat_power_water(const orc_phys *ph, double e) {
+  double s = 0.0;
+  for (int k = 0; k < 2; k++)
+    s += ORC_NA * orc_water[k][2] / orc_water[k][1] * orc_sigma_tr_element(ph, orc_water[k][0], orc_water[k][1], e);
+  return s;
+}
+
 /* Gamma density of the catastrophic deflection angle (Appendix A.4). */
 static double gamma_pdf(double th, double al, double be) {
   if (th <= 0.0) return (al == 1.0) ? be : 0.0;
@@ -126,11 +178,14 @@ orc_ctx *orc_create(const orc_grid *gr, const orc_phys *ph) {
   for (int j = 0; j < gr->nv; j++) c->v[j] = (j - 0.5 * (gr->nv - 1)) * c->dv;
 
   /* Reading (energy floor): a face at E <= 0 has no finite Bragg-Kleeman
-   * stopping power; it is evaluated at half the lowest group width instead. */
+   * stopping power; it is evaluated at half the lowest group width instead.
+   * The Bethe-Bloch tables hold their values below 0.5 MeV (where the
+   * formula's logarithm loses its meaning). */
   double e_floor = 0.5 * c->de[0];
+  if (ph->model == 1 && e_floor < 0.5) e_floor = 0.5;
   for (int f = 0; f <= G; f++) {
     double e = c->e_faces[f] > e_floor ? c->e_faces[f] : e_floor;
-    c->s_face[f] = bk_stopping(ph, e);
+    c->s_face[f] = ph->model == 1 ? ph->s_scale * orc_bethe_water(ph, e) : bk_stopping(ph, e);
   }
   /* sigma_tr,g is the group average of the scattering coefficient
    * (after Eq. (0041-d)); here rho*sigma_tr is the Highland scattering power,
@@ -138,7 +193,19 @@ orc_ctx *orc_create(const orc_grid *gr, const orc_phys *ph) {
   for (int g = 0; g < G; g++) {
     double lo = c->e_faces[g] > e_floor ? c->e_faces[g] : e_floor;
     double hi = c->e_faces[g + 1];
-    c->ts[g] = ph->ts_scale * (highland_primitive(ph, hi) - highland_primitive(ph, lo)) / (hi - lo);
+    if (ph->model == 1) {
+      /* group average by 8-point Gauss-Legendre (no closed-form primitive) */
+      static const double x8[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267,
+                                   0.9602898564975363};
+      static const double w8[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745,
+                                   0.1012285362903763};
+      double acc = 0.0, mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+      for (int q = 0; q < 4; q++)
+        acc += w8[q] * (orc_scat_power_water(ph, mid - half * x8[q]) + orc_scat_power_water(ph, mid + half * x8[q]));
+      c->ts[g] = ph->ts_scale * 0.5 * acc;
+    } else {
+      c->ts[g] = ph->ts_scale * (highland_primitive(ph, hi) - highland_primitive(ph, lo)) / (hi - lo);
+    }
     c->sig[g] = ph->sigma_ct;
   }
   /* P^1(g'->g) = lambda exp(-lambda (E_g' - E_g)) for g <= g' (protons only

@@ -26,6 +26,8 @@ typedef struct {
   double g_alpha, g_beta;  /* Gamma angular-deflection parameters */
   double s_scale;          /* multiplies S (0 switches energy loss off) */
   double ts_scale;         /* multiplies the scattering power */
+  int model;               /* 0: Bragg-Kleeman + Highland; 1: the paper's Appendix A
+                              (Bethe-Bloch with Bragg additivity, screened Rutherford) */
 } orc_phys;
 
 typedef struct {
@@ -45,6 +47,10 @@ void orc_destroy(orc_ctx *c);
 void orc_get_tables(const orc_ctx *c, double *s_face, double *ts, double *sig, double *p1, double *p2,
                     double *u, double *v);
 double orc_highland(const orc_phys *ph, double e);
+double orc_bethe_water(const orc_phys *ph, double e);
+double orc_bethe_element(const orc_phys *ph, double z, double a, double e);
+double orc_sigma_tr_element(const orc_phys *ph, double z, double a, double e);
+double orc_scat_power_water(const orc_phys *ph, double e);
 void orc_energy_blocks(const orc_ctx *c, int g, double rho, double agg[2][2], double aup[2][2]);
 void orc_energy_apply(const orc_ctx *c, double rho, const double *x, double *out);
 double orc_energy_cn_lane(const orc_ctx *c, double rho, double h, double *x, const double *src_sum,

@@ -37,7 +37,7 @@ class PbsGrid(ctypes.Structure):
 
 class PbsPhysics(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("bk_alpha", "bk_p", "x0", "mp", "es", "sigma_ct", "lambda_p1",
-                                               "g_alpha", "g_beta", "s_scale", "ts_scale")]
+                                               "g_alpha", "g_beta", "s_scale", "ts_scale")] + [("model", ctypes.c_int)]
 
 
 class PbsBeam(ctypes.Structure):
@@ -331,7 +331,7 @@ def pbs_destroy(ctx) -> None:
 # ---------------------------------------------------------------- convenience
 
 DEFAULT_PHYSICS = dict(bk_alpha=0.0022, bk_p=1.77, x0=36.08, mp=938.272, es=13.6, sigma_ct=0.012, lambda_p1=0.05,
-                       g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0)
+                       g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0, model=0)
 _BEAM_DEFAULTS = dict(e0=100.0, sigma_e=1.0, y0=0.0, z0=0.0, sigma_y=0.3, sigma_z=0.3, u0=0.0, v0=0.0,
                       sigma_u=1e-6, sigma_v=1e-6)
 

@@ -220,6 +220,52 @@ double highland_primitive(const pbs_physics &ph, double e) {
   return ph.es * ph.es / ph.x0 * (std::log(e / (e + 2.0 * m)) / (4.0 * m) - (e + m) / (2.0 * e * (e + 2.0 * m)));
 }
 
+// The paper's own physics for water (Appendix A.1, A.3): Bethe-Bloch per
+// element (density correction 0) with the piecewise I-value rule, Bragg
+// additivity over the mass fractions, and the screened-Rutherford
+// momentum-transfer cross section per atom.
+struct Element {
+  double z, a, w;  // atomic number, molar mass (g/mol), mass fraction in water
+};
+constexpr Element kWater[2] = {{1.0, 1.00794, 0.111894}, {8.0, 15.9994, 0.888106}};
+constexpr double kMeC2 = 0.51099895;      // MeV
+constexpr double kBetheK = 0.307075;      // MeV cm^2 / mol
+constexpr double kCoulomb = 1.439964e-13;  // e^2 / (4 pi eps0), MeV cm
+constexpr double kFineStructure = 1.0 / 137.035999;
+constexpr double kAvogadro = 6.02214076e23;
+constexpr double kMeVPerAmu = 931.494;
+
+double excitation_mev(double z) {
+  if (z < 1.5) return 19.0e-6;
+  return (z <= 13.0 ? 11.2 + 11.7 * z : 52.8 + 8.71 * z) * 1e-6;
+}
+
+double stopping_bethe_water(const pbs_physics &ph, double e) {
+  const double gam = 1.0 + e / ph.mp, beta2 = 1.0 - 1.0 / (gam * gam);
+  double s = 0.0;
+  for (const Element &el : kWater)
+    s += el.w * kBetheK * el.z / el.a / beta2 *
+         (std::log(2.0 * kMeC2 * beta2 * gam * gam / excitation_mev(el.z)) - beta2);
+  return ph.s_scale * s;
+}
+
+// rho sigma_tr per unit density (cm^2/g): sum over the atoms of one gram.
+double scattering_rutherford_water(const pbs_physics &ph, double e) {
+  const double gam = 1.0 + e / ph.mp, beta2 = 1.0 - 1.0 / (gam * gam);
+  const double p = std::sqrt(e * (e + 2.0 * ph.mp));
+  double s = 0.0;
+  for (const Element &el : kWater) {
+    const double m_target = el.a * kMeVPerAmu;
+    const double m_red = ph.mp * m_target / (ph.mp + m_target);
+    const double r = el.z * kCoulomb / (m_red * beta2);
+    const double theta_min = std::cbrt(el.z) * kFineStructure * kMeC2 / p;
+    const double eta = theta_min * theta_min;
+    const double sigma = 2.0 * 3.14159265358979323846 * r * r * (std::log((eta + 1.0) / eta) - 1.0 / (eta + 1.0));
+    s += kAvogadro * el.w / el.a * sigma;
+  }
+  return s;
+}
+
 double gamma_density(double th, double al, double be) {
   if (!(th > 0.0)) return al == 1.0 ? be : 0.0;
   return std::exp(al * std::log(be) + (al - 1.0) * std::log(th) - be * th - std::lgamma(al));
@@ -249,11 +295,28 @@ void build_tables(pbs_ctx *c, const pbs_physics &ph) {
   c->ts.assign(G, 0.0);
   c->sig.assign(G, ph.sigma_ct);
   // a face at E <= 0 takes the stopping power at half the lowest group width
-  const double floor_e = 0.5 * c->de[0];
-  for (int f = 0; f <= G; f++) c->s_face[f] = stopping_bk(ph, std::max(c->e_faces[f], floor_e));
+  // (the Bethe-Bloch tables: at no less than 0.5 MeV)
+  const bool bethe = ph.model == 1;
+  const double floor_e = bethe ? std::max(0.5 * c->de[0], 0.5) : 0.5 * c->de[0];
+  for (int f = 0; f <= G; f++) {
+    const double e = std::max(c->e_faces[f], floor_e);
+    c->s_face[f] = bethe ? stopping_bethe_water(ph, e) : stopping_bk(ph, e);
+  }
+  // 8-point Gauss-Legendre nodes / weights on [-1, 1] (positive half)
+  static const double gl_x[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+  static const double gl_w[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
   for (int g = 0; g < G; g++) {
     const double lo = std::max(c->e_faces[g], floor_e), hi = c->e_faces[g + 1];
-    c->ts[g] = ph.ts_scale * (highland_primitive(ph, hi) - highland_primitive(ph, lo)) / (hi - lo);
+    if (bethe) {
+      const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+      double acc = 0.0;
+      for (int q = 0; q < 4; q++)
+        acc += gl_w[q] * (scattering_rutherford_water(ph, mid - half * gl_x[q]) +
+                          scattering_rutherford_water(ph, mid + half * gl_x[q]));
+      c->ts[g] = ph.ts_scale * 0.5 * acc;
+    } else {
+      c->ts[g] = ph.ts_scale * (highland_primitive(ph, hi) - highland_primitive(ph, lo)) / (hi - lo);
+    }
   }
   transfer_tables(c, ph.lambda_p1);
   // angular transfer: Gamma density of the angle between (1,u',v') and (1,u,v),
@@ -855,8 +918,9 @@ pbs_status pbs_bind_workspace(pbs_ctx *c, void *p, size_t bytes) {
 
 pbs_status pbs_set_physics(pbs_ctx *c, const pbs_physics *ph) {
   if (!c || !ph) return fail(c, PBS_ERR_ARG, "null physics");
-  if (!(ph->bk_alpha > 0) || !(ph->bk_p > 0) || !(ph->x0 > 0) || !(ph->mp > 0) || !(ph->lambda_p1 > 0) ||
-      !(ph->g_beta > 0) || !(ph->g_alpha > 0) || ph->sigma_ct < 0 || ph->s_scale < 0 || ph->ts_scale < 0)
+  if (!(ph->mp > 0) || !(ph->lambda_p1 > 0) || !(ph->g_beta > 0) || !(ph->g_alpha > 0) || ph->sigma_ct < 0 ||
+      ph->s_scale < 0 || ph->ts_scale < 0 || ph->model < 0 || ph->model > 1 ||
+      (ph->model == 0 && (!(ph->bk_alpha > 0) || !(ph->bk_p > 0) || !(ph->x0 > 0))))
     return fail(c, PBS_ERR_ARG, "physics parameters out of range");
   build_tables(c, *ph);
   c->have_tables = true;

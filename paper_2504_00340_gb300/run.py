@@ -113,7 +113,7 @@ def march(binding, w, steps, prec, autotune=False, profile=True):
     precision: device time by CUDA events around step + flush on the
     context's stream; per-kernel times when profiling."""
     import torch
-    s = binding.Solver(w.grid(), nx=steps, dx=w.dx, n_scatter=w.n_scatter, precision=prec)
+    s = binding.Solver(w.grid(), nx=steps, dx=w.dx, n_scatter=w.n_scatter, precision=prec, physics=w.physics)
     try:
         s.set_material(w.density(steps))
         s.launch_beam(**w.beam)

@@ -158,7 +158,11 @@ GRF230 = Workload(
     dx=0.05, n_steps=660, u_max=0.15, v_max=0.15, n_scatter=3, beam=_beam(230.0, 0.5),
     medium="random_field", seed=20250402, precision="mixed")
 
-WORKLOADS = {w.name: w for w in (WATER100, WATER150, SLAB180, GRF230)}
+# The 100 MeV water beam with the paper's own physics tables (Appendix A:
+# Bethe-Bloch with Bragg additivity, screened Rutherford).
+WATER100_APPENDIX = WATER100.with_(name="water100_appendix_32x32_g64_a8x8_k1", physics=dict(PHYSICS, model=1))
+
+WORKLOADS = {w.name: w for w in (WATER100, WATER150, SLAB180, GRF230, WATER100_APPENDIX)}
 
 
 def spot_batch(n_beams=256, seed=20250401, pitch=0.5, sigma_lat=0.3):

@@ -46,6 +46,29 @@ def test_tables_match_oracle(orc):
     s.close()
 
 
+def test_appendix_physics_tables_and_march_match_oracle(orc):
+    """The paper's own physics (model 1: Bethe-Bloch with Bragg additivity,
+    screened Rutherford) built by the library equals the oracle's tables, and
+    the K = 1 FP64 march on them equals the oracle's march."""
+    grid = _grid(10, 12, 8, 8, 30, e_max=60.0)
+    phys = dict(model=1)
+    o = orc.Oracle(grid, phys)
+    nx, dx = 6, 0.05
+    s = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision="fp64", physics=phys)
+    got, ref = s.tables(), o.tables()
+    for k in ("s_face", "ts", "sig", "p1", "p2"):
+        assert _relerr(got[k], ref[k]) < 1e-13, k
+    rho = np.random.default_rng(12).uniform(0.5, 1.5, size=(nx, 10, 12))
+    s.set_material(rho)
+    beam = dict(e0=50.0, sigma_e=1.0, sigma_y=0.3, sigma_z=0.3)
+    s.launch_beam(**beam)
+    s.step(nx)
+    m = o.march(rho, nx, dx, beam=beam, n_scatter=1)
+    assert _relerr(s.read_dose(), m["dose"]) < 1e-10
+    assert _relerr(s.read_fluence(), m["fluence"]) < 1e-10
+    s.close()
+
+
 def test_caller_tables_match_oracle(orc):
     """Tables handed in through pbs_set_tables (the oracle's, for other
     physics parameters than the context's) drive the march exactly like the
