@@ -246,7 +246,7 @@ pbs_status pbs_get_options(const pbs_ctx *ctx, pbs_options *options);
  *   source_form     BF16 source contraction on the tensor cores (mixed
  *                   precision, n_scatter > 0): 0 tile by tile, 1 pipelined
  *                   (TMA loads, MMAs and epilogue of consecutive tiles
- *                   overlapped) */
+ *                   overlapped), 2 pipelined with 128-byte swizzled R tiles */
 typedef struct {
   int energy_angles;
   int energy_form;

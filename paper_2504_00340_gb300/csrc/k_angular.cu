@@ -65,7 +65,6 @@ struct DstTab<double> {
 template <typename real>
 struct AngTables {
   real lam[kMaxAngle * kMaxAngle];  // eigenvalues [n][m]
-  int exact;                        // 0: Crank-Nicolson factor, 1: exact exponential
 };
 
 // y[m] = sum_i S[m][i] x[i] for an orthonormal DST-I of even length N.
@@ -92,10 +91,16 @@ __device__ __forceinline__ float mode_factor(float den) { return __fdividef(2.0f
 // Factor of one sine mode over the step, ql = (h kappa / 4) lam <= 0:
 // Crank-Nicolson (1 + ql) / (1 - ql) = -1 + 2 / (1 - ql), or the exact
 // solution exp(2 ql) of the mode's ODE.
-__device__ __forceinline__ double mode_scale(double ql, int exact) { return exact ? exp(2.0 * ql) : mode_factor(1.0 - ql); }
-__device__ __forceinline__ float mode_scale(float ql, int exact) { return exact ? expf(2.0f * ql) : mode_factor(1.0f - ql); }
+template <bool EXACT>
+__device__ __forceinline__ double mode_scale(double ql) {
+  return EXACT ? exp(2.0 * ql) : mode_factor(1.0 - ql);
+}
+template <bool EXACT>
+__device__ __forceinline__ float mode_scale(float ql) {
+  return EXACT ? expf(2.0f * ql) : mode_factor(1.0f - ql);
+}
 
-template <typename real, int NU, int NV>
+template <typename real, int NU, int NV, bool EXACT>
 __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
     k_angular(real *__restrict__ psi, const real *__restrict__ rho_yz, const real *__restrict__ ts, int nyz,
               int ng, real hq, long long kgc0, const __grid_constant__ AngTables<real> tb) {
@@ -131,7 +136,7 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
     for (int j = 0; j < NV; j++) c[j] = tile[j * NU + t][x];
     dst_apply<real, NV>(c, y);
 #pragma unroll
-    for (int n = 0; n < NV; n++) y[n] *= mode_scale(q * tb.lam[n * NU + t], tb.exact);  // lam <= 0
+    for (int n = 0; n < NV; n++) y[n] *= mode_scale<EXACT>(q * tb.lam[n * NU + t]);  // lam <= 0
     dst_apply<real, NV>(y, c);
 #pragma unroll
     for (int j = 0; j < NV; j++) tile[j * NU + t][x] = c[j];
@@ -180,7 +185,7 @@ __device__ __forceinline__ void dst_apply2(const float2 (&x)[N], float2 (&y)[N])
 // and several CTAs fit an SM (one CTA's loads overlap another's transforms).
 // nyz must be even.
 constexpr int kF2X = 16;
-template <int NU, int NV>
+template <int NU, int NV, bool EXACT>
 __global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV))
     k_angular_f2(float *__restrict__ psi, const float *__restrict__ rho_yz, const float *__restrict__ ts, int nyz,
                  int ng, float hq, long long kgc0, const __grid_constant__ AngTables<float> tb) {
@@ -218,8 +223,8 @@ __global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV))
 #pragma unroll
     for (int n = 0; n < NV; n++) {
       const float l = tb.lam[n * NU + t];
-      y[n].x *= mode_scale(q.x * l, tb.exact);
-      y[n].y *= mode_scale(q.y * l, tb.exact);
+      y[n].x *= mode_scale<EXACT>(q.x * l);
+      y[n].y *= mode_scale<EXACT>(q.y * l);
     }
     dst_apply2<NV>(y, c);
 #pragma unroll
@@ -238,20 +243,21 @@ __global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV))
   }
 }
 
-template <int NU, int NV>
+template <int NU, int NV, bool EXACT>
 cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
                   const AngTables<float> &tb) {
   constexpr int NT = NU > NV ? NU : NV;
   const size_t smem = sizeof(float2) * NU * NV * kF2X;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_angular_f2<NU, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_angular_f2<NU, NV, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const long long total = (long long)d.ncomp * d.ng * 2;
   for (long long k0 = 0; k0 < total; k0 += 65535) {
     const long long cnt = total - k0 < 65535 ? total - k0 : 65535;
     dim3 grid((d.nyz / 2 + kF2X - 1) / kF2X, (unsigned)cnt);
-    k_angular_f2<NU, NV><<<grid, dim3(kF2X, NT), smem, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng,
+    k_angular_f2<NU, NV, EXACT><<<grid, dim3(kF2X, NT), smem, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng,
                                                                     (float)(0.25 * h), k0, tb);
     ++*lc.launches;
     cudaError_t e = cudaGetLastError();
@@ -284,7 +290,7 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 
 // Tile t covers rows [stack * NA, stack * NA + NA) and lateral points
 // [tx * TW, tx * TW + TW) with stack = t / ntx (= (k * ng + g) * 2 + c).
-template <typename real, int NU, int NV>
+template <typename real, int NU, int NV, bool EXACT>
 __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
     k_angular_tma(const __grid_constant__ CUtensorMap map, const real *__restrict__ rho_yz,
                   const real *__restrict__ ts, int nyz, int ng, int ntx, long long ntiles, real hq,
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
       for (int j = 0; j < NV; j++) c[j] = tl[j * NU + t][x];
       dst_apply<real, NV>(c, y);
 #pragma unroll
-      for (int n = 0; n < NV; n++) y[n] *= mode_scale(q * tb.lam[n * NU + t], tb.exact);
+      for (int n = 0; n < NV; n++) y[n] *= mode_scale<EXACT>(q * tb.lam[n * NU + t]);
       dst_apply<real, NV>(y, c);
 #pragma unroll
       for (int j = 0; j < NV; j++) tl[j * NU + t][x] = c[j];
@@ -397,7 +403,7 @@ bool angular_tma_ok(const Dims &d, const real *psi) {
          (reinterpret_cast<uintptr_t>(psi) % 16 == 0) && tensor_map_encoder() != nullptr;
 }
 
-template <typename real, int NU, int NV>
+template <typename real, int NU, int NV, bool EXACT>
 cudaError_t go_tma(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts, double h,
                    const AngTables<real> &tb) {
   constexpr int NA = NU * NV;
@@ -416,7 +422,7 @@ cudaError_t go_tma(const LaunchCtx &lc, const Dims &d, real *psi, const real *rh
   const int ntx = (d.nyz + kTW - 1) / kTW;
   const long long ntiles = rows / NA * ntx;
   const size_t smem = (size_t)kAngBufs * NA * kTW * sizeof(real);
-  auto kern = k_angular_tma<real, NU, NV>;
+  auto kern = k_angular_tma<real, NU, NV, EXACT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -432,8 +438,7 @@ cudaError_t go_tma(const LaunchCtx &lc, const Dims &d, real *psi, const real *rh
 }
 
 template <typename real>
-void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv, int exact) {
-  tb.exact = exact;
+void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv) {
   const double pi = 3.14159265358979323846;
   for (int n = 0; n < nv; n++)
     for (int m = 0; m < nu; m++)
@@ -441,16 +446,14 @@ void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv, int 
                                   (2.0 * std::cos(pi * (n + 1) / (nv + 1)) - 2.0) / (dv * dv));
 }
 
-template <typename real, int NU, int NV>
-cudaError_t go(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts, double h, double du,
-               double dv) {
-  AngTables<real> tb;
-  fill_tables(tb, NU, NV, du, dv, lc.angular_exact);
+template <typename real, int NU, int NV, bool EXACT>
+cudaError_t go_exact(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts, double h,
+                     const AngTables<real> &tb) {
   if constexpr (sizeof(real) == 4) {
-    if (lc.angular_form == 2 && (d.nyz % 2) == 0) return go_f2<NU, NV>(lc, d, psi, rho_yz, ts, h, tb);
+    if (lc.angular_form == 2 && (d.nyz % 2) == 0) return go_f2<NU, NV, EXACT>(lc, d, psi, rho_yz, ts, h, tb);
   }
   if (lc.angular_form == 1 && lc.err && angular_tma_ok<real>(d, psi))
-    return go_tma<real, NU, NV>(lc, d, psi, rho_yz, ts, h, tb);
+    return go_tma<real, NU, NV, EXACT>(lc, d, psi, rho_yz, ts, h, tb);
   constexpr int NT = NU > NV ? NU : NV;
   constexpr int kTW = tile_w<real>();
   dim3 block(kTW, NT);
@@ -459,12 +462,22 @@ cudaError_t go(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz
   for (long long k0 = 0; k0 < total; k0 += 65535) {
     const long long cnt = total - k0 < 65535 ? total - k0 : 65535;
     dim3 grid((d.nyz + kTW - 1) / kTW, (unsigned)cnt);
-    k_angular<real, NU, NV><<<grid, block, 0, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng, (real)(0.25 * h), k0, tb);
+    k_angular<real, NU, NV, EXACT><<<grid, block, 0, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng, (real)(0.25 * h), k0,
+                                                                   tb);
     ++*lc.launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+template <typename real, int NU, int NV>
+cudaError_t go(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts, double h, double du,
+               double dv) {
+  AngTables<real> tb;
+  fill_tables(tb, NU, NV, du, dv);
+  if (lc.angular_exact) return go_exact<real, NU, NV, true>(lc, d, psi, rho_yz, ts, h, tb);
+  return go_exact<real, NU, NV, false>(lc, d, psi, rho_yz, ts, h, tb);
 }
 
 }  // namespace

@@ -13,14 +13,15 @@ namespace {
 template <typename real>
 __global__ void k_init(real *__restrict__ psi0, const double *__restrict__ fe, const double *__restrict__ fa,
                        const double *__restrict__ fy, const double *__restrict__ fz, Dims d) {
-  // blockIdx.z = row (g, c), blockIdx.y = angle, x = lateral point
-  const int row = blockIdx.z, a = blockIdx.y;
-  const int yz = blockIdx.x * blockDim.x + threadIdx.x;
-  if (yz >= d.nyz) return;
-  const int p = yz / d.nz;
-  const int q = yz - p * d.nz;
+  // blockIdx.y = row (g, c), blockIdx.x = angle; the block walks the lateral points
+  const int row = blockIdx.y, a = blockIdx.x;
   const real f = (real)(fe[row] * fa[a]);
-  psi0[(long long)row * d.lanes + (long long)a * d.nyz + yz] = f * (real)fy[p] * (real)fz[q];
+  real *out = psi0 + (long long)row * d.lanes + (long long)a * d.nyz;
+  for (int yz = threadIdx.x; yz < d.nyz; yz += blockDim.x) {
+    const int p = yz / d.nz;
+    const int q = yz - p * d.nz;
+    out[yz] = f * (real)fy[p] * (real)fz[q];
+  }
 }
 
 // Planar fluence of the current state: flu[yz] += scale * sum_{k,g,a} dE_g psi^1
@@ -138,7 +139,7 @@ cudaError_t launch_source_input(const LaunchCtx &lc, const Dims &d, const void *
 template <typename real>
 cudaError_t launch_init(const LaunchCtx &lc, const Dims &d, real *psi0, const double *fe, const double *fa,
                         const double *fy, const double *fz) {
-  dim3 grid((unsigned)((d.nyz + 255) / 256), (unsigned)d.na, (unsigned)(2 * d.ng));
+  dim3 grid((unsigned)d.na, (unsigned)(2 * d.ng));
   k_init<real><<<grid, 256, 0, lc.stream>>>(psi0, fe, fa, fy, fz, d);
   ++*lc.launches;
   return cudaGetLastError();

@@ -51,6 +51,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;
 }
 
+// The same with the 128-byte swizzle (layout type 2, bits 61..63): rows of
+// 128 bytes, XOR-swizzled in 1024-byte atoms of 8 rows; start addresses on
+// atom boundaries (base offset 0).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return smem_desc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9 = 1, 10-12 = 1), A K-major (bit 15 = 0), B MN-major (bit 16 = 1),
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -253,6 +260,13 @@ constexpr int kPipeThreads = 288;                // warp 0: producer + MMA issue
 constexpr int kEpiThreads = kPipeThreads - 32;
 constexpr long long kPipeWait = 2000000000LL;    // ~1 s at 2 GHz
 
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint64_t *bar) {
   asm volatile(
@@ -273,6 +287,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// SWB: the R tile arrives as [k][64 lateral points] rows of 128 bytes with the
+// 128-byte swizzle (one TMA row per k, instead of 8 segments of 16 bytes),
+// described as MN-major with 8-row groups 1024 bytes apart along K.
+template <bool SWB>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     k_source_tc_pipe(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      __nv_bfloat16 *__restrict__ src, int na, int nyz, int ng, int ngb, int nstages, float dudv,
@@ -339,7 +357,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
           const long long t = t_beg + issued;
           const int gb = (int)(t / ntn), nt = (int)(t % ntn);
           mbar_arrive_expect_tx(&full_b[s], b_bytes);
-          tma_load_3d(sB + (size_t)s * b_bytes, &mapB, 0, gb * na, nt * (kTN / 8), &full_b[s]);
+          if (SWB)
+            tma_load_2d(sB + (size_t)s * b_bytes, &mapB, nt * kTN, gb * na, &full_b[s]);
+          else
+            tma_load_3d(sB + (size_t)s * b_bytes, &mapB, 0, gb * na, nt * (kTN / 8), &full_b[s]);
           issued++;
         }
         if (!ok) break;
@@ -370,9 +391,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         for (int h = 0; h < mh; h++) {
           const uint32_t a0 = smem_u32(sA) + (uint32_t)h * (kTM / 8) * kcm * 128u;
           const uint32_t d = tmem + (uint32_t)(acc * acc_cols + h * kTN);
-          for (int j = 0; j < na / 16; j++)
-            mma_bf16(d, smem_desc(a0 + (uint32_t)j * 256u, lbo, sbo), smem_desc(b0 + (uint32_t)j * 256u, lbo, sbo),
-                     idesc, j > 0);
+          for (int j = 0; j < na / 16; j++) {
+            // K = 16 per MMA: two 8-row groups of the B tile (2 x 1024 B swizzled, or 2 core matrices of 128 B)
+            const uint64_t bd = SWB ? smem_desc_sw128(b0 + (uint32_t)j * 2048u, 0u, 1024u)
+                                    : smem_desc(b0 + (uint32_t)j * 256u, lbo, sbo);
+            mma_bf16(d, smem_desc(a0 + (uint32_t)j * 256u, lbo, sbo), bd, idesc, j > 0);
+          }
         }
         mma_commit(&empty_b[s]);
         mma_commit(&acc_full[acc]);
@@ -444,9 +468,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 }
 
 // Tensor maps of the pipelined form: P^2 as [g][m8][kc][m7][k8] (5-D box = one
-// group) and R as [chunk][row][n8] (3-D box = whole K x 64 lateral points).
-bool source_pipe_maps(const Dims &d, const __nv_bfloat16 *p2, const __nv_bfloat16 *r, int nbatch, CUtensorMap &ma,
-                      CUtensorMap &mb) {
+// group) and R as [chunk][row][n8] (3-D box = whole K x 64 lateral points) or,
+// swizzled, as [row][64 n] (2-D box, 128-byte swizzle).
+bool source_pipe_maps(const Dims &d, const __nv_bfloat16 *p2, const __nv_bfloat16 *r, int nbatch, bool swb,
+                      CUtensorMap &ma, CUtensorMap &mb) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t na = (cuuint64_t)d.na, nyz = (cuuint64_t)d.nyz;
@@ -460,7 +485,16 @@ bool source_pipe_maps(const Dims &d, const __nv_bfloat16 *p2, const __nv_bfloat1
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return false;
   }
-  {
+  if (swb) {
+    cuuint64_t dims[2] = {nyz, (cuuint64_t)d.ng * nbatch * na};
+    cuuint64_t strides[1] = {nyz * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTN, (cuuint32_t)na};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(r), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  } else {
     cuuint64_t dims[3] = {8, (cuuint64_t)d.ng * nbatch * na, nyz / 8};
     cuuint64_t strides[2] = {nyz * 2, 16};
     cuuint32_t box[3] = {8, (cuuint32_t)na, kTN / 8};
@@ -481,16 +515,18 @@ cudaError_t launch_source_tc(const LaunchCtx &lc, const Dims &d, const __nv_bflo
                              __nv_bfloat16 *src, double dudv, int nbatch) {
   if (!source_tc_supported(d.na, d.nyz)) return launch_source_bf16_cc(lc, d, p2, r, src, dudv, nbatch);
   CUtensorMap ma, mb;
-  if (lc.source_form == 1 && source_pipe_maps(d, p2, r, nbatch, ma, mb)) {
+  const bool swb = lc.source_form == 2;
+  if (lc.source_form >= 1 && source_pipe_maps(d, p2, r, nbatch, swb, ma, mb)) {
     const int nstages = d.na == 256 ? 3 : kPipeMax;
     const size_t smem = (size_t)d.na * d.na * 2 + (size_t)nstages * d.na * kTN * 2;
-    cudaError_t e = cudaFuncSetAttribute(k_source_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = swb ? k_source_tc_pipe<true> : k_source_tc_pipe<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long ntot = (long long)d.ng * nbatch * ((d.nyz + kTN - 1) / kTN);
     long long blocks = lc.num_sms;  // one CTA per SM (shared memory; TMEM 256 columns)
     if (blocks > ntot) blocks = ntot;
-    k_source_tc_pipe<<<(unsigned)blocks, kPipeThreads, smem, lc.stream>>>(ma, mb, src, d.na, d.nyz, d.ng,
-                                                                          d.ng * nbatch, nstages, (float)dudv, lc.err);
+    kern<<<(unsigned)blocks, kPipeThreads, smem, lc.stream>>>(ma, mb, src, d.na, d.nyz, d.ng, d.ng * nbatch, nstages,
+                                                              (float)dudv, lc.err);
     ++*lc.launches;
     return cudaGetLastError();
   }

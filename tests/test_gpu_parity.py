@@ -242,11 +242,11 @@ def test_source_contraction(orc, precision, tol, ny, nz, nu, nv):
     s.close()
 
 
-@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("form", [0, 1, 2])
 @pytest.mark.parametrize("ny,nz,nu,nv,ng", [(24, 24, 16, 16, 40), (16, 20, 8, 16, 60), (12, 12, 16, 16, 7)])
 def test_source_contraction_tensor_core_forms(orc, form, ny, nz, nu, nv, ng):
-    """The tile-by-tile and the pipelined tcgen05 contraction (source_form 0 /
-    1) on many groups per CTA (P^2 reloads at group boundaries, every R stage
+    """The tile-by-tile, the pipelined and the pipelined-swizzled tcgen05
+    contraction (source_form 0 / 1 / 2) on many groups per CTA (P^2 reloads at group boundaries, every R stage
     and both TMEM accumulators reused) and a ragged last N tile, against the
     oracle in BF16 tolerance."""
     grid = _grid(ny, nz, nu, nv, ng)
