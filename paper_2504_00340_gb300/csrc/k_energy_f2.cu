@@ -111,7 +111,7 @@ __device__ __forceinline__ void two_sum(float2 &s, float2 &c, float2 x) {
 }
 
 template <typename st, bool HAS_SRC, bool HAS_R, bool TWO, int kY>
-__global__ void __launch_bounds__(kX *kY)
+__global__ void __launch_bounds__(kX *kY, (HAS_SRC && HAS_R && TWO) ? 1 : 512 / (kX * kY))
     k_energy_f2(Dims d, float *__restrict__ psi, const st *__restrict__ src_a, const st *__restrict__ src_b,
                 st *__restrict__ r_a, st *__restrict__ r_b, const float *__restrict__ rho_a,
                 const float *__restrict__ rho_b, const GroupCoef<float> *__restrict__ coef,
