@@ -150,3 +150,35 @@ def test_checkpoint_resume(orc, precision):
         other.restore(ck)  # another scattering order
     for s in (a, b, other):
         s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+def test_maximum_group_count(orc, precision, tol):
+    """ng = 2048, the largest group count the library accepts: the group table
+    no longer fits the packed energy kernel's shared memory, so the one-lane
+    form runs; one E substep with dose against the oracle."""
+    ng = 2048
+    grid = _grid(4, 6, 2, 2, ng, e_max=300.0)
+    s = binding.Solver(grid, nx=2, dx=0.05, precision=precision)
+    rho = np.full((2, 4, 6), 1.1)
+    s.set_material(rho)
+    psi = random_state((ng, 2, 2, 2, 4, 6), seed=3)
+    s.write_psi(0, psi)
+    s.substep_energy(0.025, 1)
+    ref, e, _ = orc.Oracle(grid).energy_substep(0.025, rho[1], psi, None)
+    assert _relerr(s.read_psi(0), ref) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("cols", [4, 8])
+def test_widest_rows(orc, cols):
+    """nz = 1024, the widest row the library accepts: nine segments with halo
+    lanes per row, against the oracle's transport."""
+    grid = _grid(3, 1024, 2, 4, 1)
+    s = binding.Solver(grid, nx=1, dx=0.05, precision="fp64")
+    s.set_tuning(transport_cols=cols)
+    psi = random_state((1, 2, 4, 2, 3, 1024), seed=8)
+    s.write_psi(0, psi)
+    s.substep_transport(0.3)
+    assert _relerr(s.read_psi(0), orc.Oracle(grid).transport_substep(0.3, psi)) < 1e-12
+    s.close()
