@@ -40,7 +40,8 @@ class _Grid(ctypes.Structure):
 class _Phys(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in
                 ("bk_alpha", "bk_p", "x0", "mp", "es", "sigma_ct", "lambda_p1",
-                 "g_alpha", "g_beta", "s_scale", "ts_scale")] + [("model", ctypes.c_int)]
+                 "g_alpha", "g_beta", "s_scale", "ts_scale")] + [("model", ctypes.c_int),
+                                                                  ("t_scale", ctypes.c_double)]
 
 
 class _Beam(ctypes.Structure):
@@ -79,7 +80,7 @@ def _load():
             lib.orc_get_tables.argtypes = [ctypes.c_void_p] + [_D] * 7
             lib.orc_highland.restype = ctypes.c_double
             lib.orc_highland.argtypes = [ctypes.POINTER(_Phys), ctypes.c_double]
-            for fn in ("orc_bethe_water", "orc_scat_power_water"):
+            for fn in ("orc_bethe_water", "orc_scat_power_water", "orc_williams_water"):
                 getattr(lib, fn).restype = ctypes.c_double
                 getattr(lib, fn).argtypes = [ctypes.POINTER(_Phys), ctypes.c_double]
             for fn in ("orc_bethe_element", "orc_sigma_tr_element"):
@@ -87,6 +88,11 @@ def _load():
                 getattr(lib, fn).argtypes = [ctypes.POINTER(_Phys), ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double]
             lib.orc_energy_blocks.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D, _D]
+            lib.orc_straggle_blocks.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D, _D, _D]
+            lib.orc_straggle_apply.argtypes = [ctypes.c_void_p, ctypes.c_double, _D, _D]
+            lib.orc_set_straggling_table.argtypes = [ctypes.c_void_p, _D]
+            lib.orc_set_straggling_cn.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            lib.orc_get_straggling.argtypes = [ctypes.c_void_p, _D, _D]
             lib.orc_energy_apply.argtypes = [ctypes.c_void_p, ctypes.c_double, _D, _D]
             lib.orc_energy_cn_lane.restype = ctypes.c_double
             lib.orc_energy_cn_lane.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D, _D]
@@ -118,7 +124,8 @@ def _f64(a):
 
 
 DEFAULT_PHYS = dict(bk_alpha=0.0022, bk_p=1.77, x0=36.08, mp=938.272, es=13.6, sigma_ct=0.012,
-                    lambda_p1=0.05, g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0, model=0)
+                    lambda_p1=0.05, g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0, model=0,
+                    t_scale=0.0)
 
 
 def num_threads() -> int:
@@ -157,6 +164,11 @@ def sigma_tr_element(z: float, a: float, e: float, **phys) -> float:
 
 def scat_power_water(e: float, **phys) -> float:
     return _load().orc_scat_power_water(_phys(phys), float(e))
+
+
+def williams_water(e: float, **phys) -> float:
+    """Straggling coefficient of water (MeV^2 cm^2/g), Appendix A.2."""
+    return _load().orc_williams_water(_phys(phys), float(e))
 
 
 class Oracle:
@@ -212,6 +224,34 @@ class Oracle:
         agg, aup = np.zeros((2, 2)), np.zeros((2, 2))
         self.lib.orc_energy_blocks(self.ctx, int(g), float(rho), _ptr(agg), _ptr(aup))
         return agg, aup
+
+    def straggle_blocks(self, g: int, rho: float):
+        """(alo, agg, aup) of the interior-penalty straggling operator."""
+        alo, agg, aup = np.zeros((2, 2)), np.zeros((2, 2)), np.zeros((2, 2))
+        self.lib.orc_straggle_blocks(self.ctx, int(g), float(rho), _ptr(alo), _ptr(agg), _ptr(aup))
+        return alo, agg, aup
+
+    def straggle_apply(self, rho: float, x):
+        x = _f64(x).reshape(-1)
+        out = np.zeros_like(x)
+        self.lib.orc_straggle_apply(self.ctx, float(rho), _ptr(x), _ptr(out))
+        return out
+
+    def set_straggling_table(self, t_face=None):
+        """Straggling coefficient at the faces (ng+1, MeV^2 cm^2/g); None: off.
+        Re-folds the drift T'/2 into the stopping power."""
+        t = None if t_face is None else _f64(t_face).reshape(self.ng + 1)
+        self.lib.orc_set_straggling_table(self.ctx, _ptr(t))
+
+    def set_straggling_cn(self, full: bool):
+        """False (default): straggling explicit inside the CN energy step;
+        True: straggling inside the CN step as well (block-tridiagonal)."""
+        self.lib.orc_set_straggling_cn(self.ctx, int(bool(full)))
+
+    def straggling(self) -> dict:
+        out = dict(t_face=np.zeros(self.ng + 1), s_base=np.zeros(self.ng + 1))
+        self.lib.orc_get_straggling(self.ctx, _ptr(out["t_face"]), _ptr(out["s_base"]))
+        return out
 
     def energy_apply(self, rho: float, x):
         x = _f64(x).reshape(-1)

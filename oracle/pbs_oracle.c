@@ -47,7 +47,11 @@ struct orc_ctx {
   double *e_faces;  /* ng+1 */
   double *e_c;      /* group centre E_g */
   double *de;       /* group width Delta E_g */
-  double *s_face;   /* mass stopping power at the faces, ng+1 */
+  double *s_face;   /* mass stopping power at the faces, ng+1, with the straggling drift folded in */
+  double *s_base;   /* mass stopping power at the faces, ng+1, as tabulated */
+  double *t_face;   /* mass straggling coefficient at the faces, ng+1 (0: no straggling) */
+  int strag_on;     /* any t_face != 0 */
+  int strag_cn;     /* straggling time integrator: 0 explicit inside CN, 1 Crank-Nicolson */
   double *ts;       /* group-averaged scattering power, ng */
   double *sig;      /* catastrophic removal (mass), ng */
   double *p1;       /* [gp][g] probability of gp -> g */
@@ -140,6 +144,61 @@ double orc_scat_power_water(const orc_phys *ph, double e) {
   return s;
 }
 
+/* Energy-straggling coefficient of Appendix A.2 (Williams' form of Bohr's
+ * formula with the binding correction), per gram of water: the per-electron
+ *   4 pi e^4 (1 + 4 I / (3 m_e v^2) ln(2 m_e v^2 / I))
+ * times the electrons per gram N_A Z / A of each element, with that
+ * element's I-value (the piecewise rule of Appendix A.1), summed over the
+ * mass fractions.  m_e v^2 = m_e c^2 beta^2.  MeV^2 cm^2 / g. */
+double orc_williams_water(const orc_phys *ph, double e) {
+  double gam = 1.0 + e / ph->mp, b2 = 1.0 - 1.0 / (gam * gam);
+  double mv2 = ORC_ME * b2, s = 0.0;
+  for (int k = 0; k < 2; k++) {
+    double z = orc_water[k][0], a = orc_water[k][1], w = orc_water[k][2], i = i_value_mev(z);
+    s += w * z / a * (1.0 + 4.0 * i / (3.0 * mv2) * log(2.0 * mv2 / i));
+  }
+  return 4.0 * 3.14159265358979323846 * ORC_E2 * ORC_E2 * ORC_NA * s;
+}
+
+/* Section 3.2 splits the straggling term (1/2) d^2(T psi)/dE^2 into
+ * (1/2) d/dE(T dpsi/dE), taken by the interior-penalty form below, and
+ * (1/2) d/dE(T' psi), which the paper treats like the stopping-power term.
+ * Reading: it IS the stopping-power operator with S replaced by T'/2, so
+ * the two drifts add at every face: S_eff = S + T'/2.  T is linear in each
+ * group through its face values (as S, Eq. appSE), so T' is the group's
+ * slope; at an inner face it is the mean of the two neighbouring slopes
+ * (on a uniform grid the paper's (T_{g+1} - T_g) / dE of centre values),
+ * at the two outer faces the one adjacent slope. */
+static void fold_straggling(orc_ctx *c) {
+  int G = c->ng;
+  c->strag_on = 0;
+  for (int f = 0; f <= G; f++) {
+    double tp;
+    if (G == 1) tp = (c->t_face[1] - c->t_face[0]) / c->de[0];
+    else if (f == 0) tp = (c->t_face[1] - c->t_face[0]) / c->de[0];
+    else if (f == G) tp = (c->t_face[G] - c->t_face[G - 1]) / c->de[G - 1];
+    else tp = 0.5 * ((c->t_face[f] - c->t_face[f - 1]) / c->de[f - 1] + (c->t_face[f + 1] - c->t_face[f]) / c->de[f]);
+    c->s_face[f] = c->s_base[f] + 0.5 * tp;
+    if (c->t_face[f] != 0.0) c->strag_on = 1;
+  }
+}
+
+/* Caller-given straggling coefficients at the faces (NULL: none). */
+void orc_set_straggling_table(orc_ctx *c, const double *t_face) {
+  for (int f = 0; f <= c->ng; f++) c->t_face[f] = t_face ? t_face[f] : 0.0;
+  fold_straggling(c);
+}
+
+/* Straggling time integrator inside the energy substep: 0 treats the
+ * interior-penalty part explicitly (old state only) inside the CN step of
+ * the rest of the energy operator, 1 takes it into the CN step as well. */
+void orc_set_straggling_cn(orc_ctx *c, int full) { c->strag_cn = full != 0; }
+
+void orc_get_straggling(const orc_ctx *c, double *t_face, double *s_base) {
+  if (t_face) memcpy(t_face, c->t_face, sizeof(double) * (c->ng + 1));
+  if (s_base) memcpy(s_base, c->s_base, sizeof(double) * (c->ng + 1));
+}
+
 /* Gamma density of the catastrophic deflection angle (Appendix A.4). */
 static double gamma_pdf(double th, double al, double be) {
   if (th <= 0.0) return (al == 1.0) ? be : 0.0;
@@ -163,6 +222,8 @@ orc_ctx *orc_create(const orc_grid *gr, const orc_phys *ph) {
   c->e_c = (double *)malloc(sizeof(double) * G);
   c->de = (double *)malloc(sizeof(double) * G);
   c->s_face = (double *)malloc(sizeof(double) * (G + 1));
+  c->s_base = (double *)malloc(sizeof(double) * (G + 1));
+  c->t_face = (double *)calloc((size_t)G + 1, sizeof(double));
   c->ts = (double *)malloc(sizeof(double) * G);
   c->sig = (double *)malloc(sizeof(double) * G);
   c->p1 = (double *)calloc((size_t)G * G, sizeof(double));
@@ -185,8 +246,10 @@ orc_ctx *orc_create(const orc_grid *gr, const orc_phys *ph) {
   if (ph->model == 1 && e_floor < 0.5) e_floor = 0.5;
   for (int f = 0; f <= G; f++) {
     double e = c->e_faces[f] > e_floor ? c->e_faces[f] : e_floor;
-    c->s_face[f] = ph->model == 1 ? ph->s_scale * orc_bethe_water(ph, e) : bk_stopping(ph, e);
+    c->s_base[f] = ph->model == 1 ? ph->s_scale * orc_bethe_water(ph, e) : bk_stopping(ph, e);
+    c->t_face[f] = ph->t_scale * orc_williams_water(ph, e);
   }
+  fold_straggling(c);
   /* sigma_tr,g is the group average of the scattering coefficient
    * (after Eq. (0041-d)); here rho*sigma_tr is the Highland scattering power,
    * averaged exactly over [max(E_lo, floor), E_hi]. */
@@ -244,7 +307,7 @@ orc_ctx *orc_create(const orc_grid *gr, const orc_phys *ph) {
 
 void orc_destroy(orc_ctx *c) {
   if (!c) return;
-  free(c->e_faces); free(c->e_c); free(c->de); free(c->s_face); free(c->ts);
+  free(c->e_faces); free(c->e_c); free(c->de); free(c->s_face); free(c->s_base); free(c->t_face); free(c->ts);
   free(c->sig); free(c->p1); free(c->p2); free(c->u); free(c->v);
   free(c);
 }
@@ -293,7 +356,9 @@ void orc_energy_blocks(const orc_ctx *c, int g, double rho, double agg[2][2], do
 }
 
 /* Apply the semi-discrete energy operator to one lane: out = A x.
- * x and out are [g][c] (2G values). */
+ * x and out are [g][c] (2G values).  Stopping power (with the straggling
+ * drift folded in) and removal only; the interior-penalty straggling part
+ * is orc_straggle_apply. */
 void orc_energy_apply(const orc_ctx *c, double rho, const double *x, double *out) {
   int G = c->ng;
   for (int g = 0; g < G; g++) {
@@ -301,6 +366,77 @@ void orc_energy_apply(const orc_ctx *c, double rho, const double *x, double *out
     orc_energy_blocks(c, g, rho, agg, aup);
     for (int r = 0; r < 2; r++) {
       double acc = agg[r][0] * x[2 * g] + agg[r][1] * x[2 * g + 1];
+      if (g + 1 < G) acc += aup[r][0] * x[2 * g + 2] + aup[r][1] * x[2 * g + 3];
+      out[2 * g + r] = acc;
+    }
+  }
+}
+
+/* Interior-penalty (SIPG) form of (rho/2) d/dE(T dpsi/dE) (Section 3.2, the
+ * terms Q_1 and Q_2 of Eq. 0041-d), written out for the P1 basis
+ * phi^1 = 1, phi^2 = 2 (E - E_g) / dE_g.  On group g, psi' = 2 psi^2 / dE_g
+ * and, T being linear through its face values, int_g T = Tbar_g dE_g with
+ * Tbar_g the mean of the two face values.  At an inner face f between
+ * groups g (below) and g+1 (above):
+ *   values   psi^- = psi^1_g + psi^2_g,  psi^+ = psi^1_{g+1} - psi^2_{g+1},
+ *   jump     [psi] = psi^- - psi^+,
+ *   average  {T psi'} = T_f (psi^2_g / dE_g + psi^2_{g+1} / dE_{g+1}),
+ *   penalty  sigma_f = alpha T_f / h_f, alpha = (1 + 1)^2 / 2 = 2,
+ *            h_f = (dE_g + dE_{g+1}) / 2.
+ * The bilinear form is
+ *   a(psi, v) = - sum_g int T psi' v' + sum_f ({T psi'}[v] + {T v'}[psi])
+ *               - sum_f sigma_f [psi][v],
+ * tested with v = phi^1_g / dE_g (row 1) and 3 phi^2_g / dE_g (row 2).
+ * Reading (penalty): the printed penalty alpha [psi][phi] / dE carries
+ * neither T nor a length; it is read as the standard sigma_f above.
+ * Reading (outer faces): no diffusive flux through E_{1/2} and E_{G+1/2};
+ * only inner faces carry the face terms, so straggling alone conserves the
+ * particle count.  Rows of group g:
+ *   row 1 = k/dE_g [ ({T psi'} - sigma [psi])_{g+1/2} - ({T psi'} - sigma [psi])_{g-1/2} ]
+ *   row 2 = 3k/dE_g [ -4 Tbar_g psi^2_g / dE_g
+ *                     + ({T psi'} + (T/dE_g - sigma)[psi])_{g+1/2}
+ *                     + ({T psi'} + (T/dE_g - sigma)[psi])_{g-1/2} ],
+ * k = rho / 2, a face term present only for inner faces.  The blocks:
+ *   d psi_g / dx += alo psi_{g-1} + agg psi_g + aup psi_{g+1}. */
+void orc_straggle_blocks(const orc_ctx *c, int g, double rho, double alo[2][2], double agg[2][2],
+                         double aup[2][2]) {
+  int G = c->ng;
+  double k = 0.5 * rho, d = 1.0 / c->de[g];
+  double tbar = 0.5 * (c->t_face[g] + c->t_face[g + 1]);
+  for (int r = 0; r < 2; r++)
+    for (int q = 0; q < 2; q++) alo[r][q] = agg[r][q] = aup[r][q] = 0.0;
+  agg[1][1] = 3.0 * k * d * (-4.0 * tbar * d);
+  if (g + 1 < G) { /* upper face: g is the lower side */
+    double t = c->t_face[g + 1], du = 1.0 / c->de[g + 1];
+    double sg = 2.0 * t / (0.5 * (c->de[g] + c->de[g + 1]));
+    /* flux coefficients on (psi^2_g, psi^2_{g+1}); jump on (p1g, p2g, p1u, p2u) = (1, 1, -1, 1) */
+    double w1 = k * d, w2 = 3.0 * k * d, tj = t * d - sg;
+    agg[0][0] += w1 * (-sg);           agg[0][1] += w1 * (t * d - sg);
+    aup[0][0] += w1 * sg;              aup[0][1] += w1 * (t * du - sg);
+    agg[1][0] += w2 * tj;              agg[1][1] += w2 * (t * d + tj);
+    aup[1][0] += w2 * (-tj);           aup[1][1] += w2 * (t * du + tj);
+  }
+  if (g > 0) { /* lower face: g is the upper side */
+    double t = c->t_face[g], dl = 1.0 / c->de[g - 1];
+    double sg = 2.0 * t / (0.5 * (c->de[g] + c->de[g - 1]));
+    /* flux on (psi^2_{g-1}, psi^2_g); jump on (p1l, p2l, p1g, p2g) = (1, 1, -1, 1) */
+    double w1 = -k * d, w2 = 3.0 * k * d, tj = t * d - sg;
+    alo[0][0] += w1 * (-sg);           alo[0][1] += w1 * (t * dl - sg);
+    agg[0][0] += w1 * sg;              agg[0][1] += w1 * (t * d - sg);
+    alo[1][0] += w2 * tj;              alo[1][1] += w2 * (t * dl + tj);
+    agg[1][0] += w2 * (-tj);           agg[1][1] += w2 * (t * d + tj);
+  }
+}
+
+/* out = A_T x for one lane, A_T the interior-penalty straggling operator. */
+void orc_straggle_apply(const orc_ctx *c, double rho, const double *x, double *out) {
+  int G = c->ng;
+  for (int g = 0; g < G; g++) {
+    double alo[2][2], agg[2][2], aup[2][2];
+    orc_straggle_blocks(c, g, rho, alo, agg, aup);
+    for (int r = 0; r < 2; r++) {
+      double acc = agg[r][0] * x[2 * g] + agg[r][1] * x[2 * g + 1];
+      if (g > 0) acc += alo[r][0] * x[2 * g - 2] + alo[r][1] * x[2 * g - 1];
       if (g + 1 < G) acc += aup[r][0] * x[2 * g + 2] + aup[r][1] * x[2 * g + 3];
       out[2 * g + r] = acc;
     }
@@ -315,40 +451,114 @@ static double energy_content(const orc_ctx *c, const double *x) {
   return s;
 }
 
+static void inv2(const double m[2][2], double out[2][2]) {
+  double det = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+  out[0][0] = m[1][1] / det;  out[0][1] = -m[0][1] / det;
+  out[1][0] = -m[1][0] / det; out[1][1] = m[0][0] / det;
+}
+
 /* One Crank-Nicolson step of length h for one lane:
  *   (I - h/2 A) x_new = (I + h/2 A) x_old + h/2 (src_old + src_new),
  * where src_sum = src_old + src_new acts on psi^1 only (Remark 1).
- * A is block upper-bidiagonal, so the system is solved from the top group
- * down (x_{G+1} = 0): M_g x_g = rhs_g + h/2 Aup x_{g+1}.
+ * A = A_S (stopping, drift, removal; block upper-bidiagonal) + A_T
+ * (interior-penalty straggling; block tridiagonal).
+ *  * Without straggling, or with it explicit (orc_set_straggling_cn 0):
+ *      (I - h/2 A_S) x_new = (I + h/2 A_S) x_old + h A_T x_old + h/2 src,
+ *    solved from the top group down (x_{G+1} = 0):
+ *      M_g x_g = rhs_g + h/2 Aup x_{g+1}.
+ *    This follows the authors' remark (kept in the paper's source, after
+ *    the splitting section) that the small straggling term is taken
+ *    explicitly in the implicit half of CN.
+ *  * With full CN (orc_set_straggling_cn 1) the system is block
+ *    tridiagonal and is solved by block elimination from the top group down
+ *    and substitution upward.
  * Returns the deposited energy content of the lane (difference form) and,
  * through *edep_w, the same quantity from the operator form
- *   -(h/2) phi^T A (x_old + x_new) - (h/2) phi^T src_sum. */
+ *   -(h/2) phi^T A_S (x_old + x_new) - h phi^T A_T x_old - (h/2) phi^T src
+ * (full CN: -(h/2) phi^T A (x_old + x_new) - (h/2) phi^T src). */
 double orc_energy_cn_lane(const orc_ctx *c, double rho, double h, double *x, const double *src_sum,
                           double *edep_w) {
   int G = c->ng;
+  int strag = c->strag_on, full = strag && c->strag_cn;
   double *old = (double *)malloc(sizeof(double) * 2 * G);
   double *ax = (double *)malloc(sizeof(double) * 2 * G);
+  double *tx = (double *)malloc(sizeof(double) * 2 * G);
   double *rhs = (double *)malloc(sizeof(double) * 2 * G);
+  double *dp = full ? (double *)malloc(sizeof(double) * 4 * G) : NULL; /* eliminated diagonal blocks */
   double hh = 0.5 * h;
   memcpy(old, x, sizeof(double) * 2 * G);
   orc_energy_apply(c, rho, old, ax);
-  for (int k = 0; k < 2 * G; k++) rhs[k] = old[k] + hh * ax[k];
+  if (strag) orc_straggle_apply(c, rho, old, tx);
+  for (int k = 0; k < 2 * G; k++) rhs[k] = old[k] + hh * ax[k] + (strag ? (full ? hh : h) * tx[k] : 0.0);
   if (src_sum)
     for (int g = 0; g < G; g++) rhs[2 * g] += hh * src_sum[g];
-  for (int g = G - 1; g >= 0; g--) {
-    double agg[2][2], aup[2][2], m[2][2], b[2];
-    orc_energy_blocks(c, g, rho, agg, aup);
-    b[0] = rhs[2 * g];
-    b[1] = rhs[2 * g + 1];
-    if (g + 1 < G) {
-      b[0] += hh * (aup[0][0] * x[2 * g + 2] + aup[0][1] * x[2 * g + 3]);
-      b[1] += hh * (aup[1][0] * x[2 * g + 2] + aup[1][1] * x[2 * g + 3]);
+  if (!full) {
+    for (int g = G - 1; g >= 0; g--) {
+      double agg[2][2], aup[2][2], m[2][2], b[2];
+      orc_energy_blocks(c, g, rho, agg, aup);
+      b[0] = rhs[2 * g];
+      b[1] = rhs[2 * g + 1];
+      if (g + 1 < G) {
+        b[0] += hh * (aup[0][0] * x[2 * g + 2] + aup[0][1] * x[2 * g + 3]);
+        b[1] += hh * (aup[1][0] * x[2 * g + 2] + aup[1][1] * x[2 * g + 3]);
+      }
+      m[0][0] = 1.0 - hh * agg[0][0]; m[0][1] = -hh * agg[0][1];
+      m[1][0] = -hh * agg[1][0];      m[1][1] = 1.0 - hh * agg[1][1];
+      double det = m[0][0] * m[1][1] - m[0][1] * m[1][0];
+      x[2 * g] = (m[1][1] * b[0] - m[0][1] * b[1]) / det;
+      x[2 * g + 1] = (-m[1][0] * b[0] + m[0][0] * b[1]) / det;
     }
-    m[0][0] = 1.0 - hh * agg[0][0]; m[0][1] = -hh * agg[0][1];
-    m[1][0] = -hh * agg[1][0];      m[1][1] = 1.0 - hh * agg[1][1];
-    double det = m[0][0] * m[1][1] - m[0][1] * m[1][0];
-    x[2 * g] = (m[1][1] * b[0] - m[0][1] * b[1]) / det;
-    x[2 * g + 1] = (-m[1][0] * b[0] + m[0][0] * b[1]) / det;
+  } else {
+    /* rows: L_g x_{g-1} + D_g x_g + U_g x_{g+1} = rhs_g with
+     * D = I - hh (A_S,gg + A_T,gg), U = -hh (A_S,up + A_T,up), L = -hh A_T,lo.
+     * Eliminate from the top: D'_g = D_g - U_g D'^{-1}_{g+1} L_{g+1},
+     * b'_g = b_g - U_g D'^{-1}_{g+1} b'_{g+1}; then x_0 = D'^{-1}_0 b'_0 and
+     * x_g = D'^{-1}_g (b'_g - L_g x_{g-1}) upward. */
+    double lnext[2][2] = {{0, 0}, {0, 0}};
+    for (int g = G - 1; g >= 0; g--) {
+      double sgg[2][2], sup[2][2], tlo[2][2], tgg[2][2], tup[2][2], D[2][2], U[2][2], Di[2][2];
+      orc_energy_blocks(c, g, rho, sgg, sup);
+      orc_straggle_blocks(c, g, rho, tlo, tgg, tup);
+      for (int r = 0; r < 2; r++)
+        for (int q = 0; q < 2; q++) {
+          D[r][q] = (r == q ? 1.0 : 0.0) - hh * (sgg[r][q] + tgg[r][q]);
+          U[r][q] = (g + 1 < G) ? -hh * (sup[r][q] + tup[r][q]) : 0.0;
+        }
+      if (g + 1 < G) {
+        /* W = U_g D'^{-1}_{g+1} */
+        double Dn[2][2], W[2][2];
+        for (int r = 0; r < 2; r++)
+          for (int q = 0; q < 2; q++) Dn[r][q] = dp[4 * (g + 1) + 2 * r + q];
+        inv2(Dn, Di);
+        for (int r = 0; r < 2; r++)
+          for (int q = 0; q < 2; q++) W[r][q] = U[r][0] * Di[0][q] + U[r][1] * Di[1][q];
+        for (int r = 0; r < 2; r++) {
+          for (int q = 0; q < 2; q++) D[r][q] -= W[r][0] * lnext[0][q] + W[r][1] * lnext[1][q];
+        }
+        double b0 = rhs[2 * g] - (W[0][0] * rhs[2 * g + 2] + W[0][1] * rhs[2 * g + 3]);
+        double b1 = rhs[2 * g + 1] - (W[1][0] * rhs[2 * g + 2] + W[1][1] * rhs[2 * g + 3]);
+        rhs[2 * g] = b0;
+        rhs[2 * g + 1] = b1;
+      }
+      for (int r = 0; r < 2; r++)
+        for (int q = 0; q < 2; q++) {
+          dp[4 * g + 2 * r + q] = D[r][q];
+          lnext[r][q] = (g > 0) ? -hh * tlo[r][q] : 0.0;
+        }
+    }
+    for (int g = 0; g < G; g++) {
+      double tlo[2][2], tgg[2][2], tup[2][2], Dg[2][2], Di[2][2], b0 = rhs[2 * g], b1 = rhs[2 * g + 1];
+      if (g > 0) {
+        orc_straggle_blocks(c, g, rho, tlo, tgg, tup);
+        b0 -= -hh * (tlo[0][0] * x[2 * g - 2] + tlo[0][1] * x[2 * g - 1]);
+        b1 -= -hh * (tlo[1][0] * x[2 * g - 2] + tlo[1][1] * x[2 * g - 1]);
+      }
+      for (int r = 0; r < 2; r++)
+        for (int q = 0; q < 2; q++) Dg[r][q] = dp[4 * g + 2 * r + q];
+      inv2(Dg, Di);
+      x[2 * g] = Di[0][0] * b0 + Di[0][1] * b1;
+      x[2 * g + 1] = Di[1][0] * b0 + Di[1][1] * b1;
+    }
   }
   double dep = energy_content(c, old) - energy_content(c, x);
   if (edep_w) {
@@ -356,6 +566,10 @@ double orc_energy_cn_lane(const orc_ctx *c, double rho, double h, double *x, con
     for (int k = 0; k < 2 * G; k++) sum[k] = old[k] + x[k];
     orc_energy_apply(c, rho, sum, ax);
     double w = -hh * energy_content(c, ax);
+    if (strag) {
+      orc_straggle_apply(c, rho, full ? sum : old, tx);
+      w -= (full ? hh : h) * energy_content(c, tx);
+    }
     if (src_sum) {
       double s = 0.0;
       for (int g = 0; g < G; g++) s += c->de[g] * c->e_c[g] * src_sum[g];
@@ -363,7 +577,7 @@ double orc_energy_cn_lane(const orc_ctx *c, double rho, double h, double *x, con
     }
     *edep_w = w;
   }
-  free(old); free(ax); free(rhs);
+  free(old); free(ax); free(tx); free(rhs); free(dp);
   return dep;
 }
 

@@ -28,6 +28,7 @@ typedef struct {
   double ts_scale;         /* multiplies the scattering power */
   int model;               /* 0: Bragg-Kleeman + Highland; 1: the paper's Appendix A
                               (Bethe-Bloch with Bragg additivity, screened Rutherford) */
+  double t_scale;          /* multiplies the straggling coefficient of Appendix A.2 (0: none) */
 } orc_phys;
 
 typedef struct {
@@ -51,6 +52,13 @@ double orc_bethe_water(const orc_phys *ph, double e);
 double orc_bethe_element(const orc_phys *ph, double z, double a, double e);
 double orc_sigma_tr_element(const orc_phys *ph, double z, double a, double e);
 double orc_scat_power_water(const orc_phys *ph, double e);
+double orc_williams_water(const orc_phys *ph, double e);
+void orc_set_straggling_table(orc_ctx *c, const double *t_face);
+void orc_set_straggling_cn(orc_ctx *c, int full);
+void orc_get_straggling(const orc_ctx *c, double *t_face, double *s_base);
+void orc_straggle_blocks(const orc_ctx *c, int g, double rho, double alo[2][2], double agg[2][2],
+                         double aup[2][2]);
+void orc_straggle_apply(const orc_ctx *c, double rho, const double *x, double *out);
 void orc_energy_blocks(const orc_ctx *c, int g, double rho, double agg[2][2], double aup[2][2]);
 void orc_energy_apply(const orc_ctx *c, double rho, const double *x, double *out);
 double orc_energy_cn_lane(const orc_ctx *c, double rho, double h, double *x, const double *src_sum,
