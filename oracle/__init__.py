@@ -99,6 +99,9 @@ def _load():
             lib.orc_energy_substep.argtypes = [ctypes.c_void_p, ctypes.c_double, _D, _D, _D, _D, _D]
             lib.orc_source.argtypes = [ctypes.c_void_p, _D, _D, _D]
             lib.orc_transport_substep.argtypes = [ctypes.c_void_p, ctypes.c_double, _D]
+            lib.orc_transport_apply.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _D, _D,
+                                                ctypes.c_int]
+            lib.orc_set_transport_cn.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_angular_substep.argtypes = [ctypes.c_void_p, ctypes.c_double, _D, _D]
             lib.orc_set_angular_exact.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_init_beam.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Beam), _D]
@@ -290,6 +293,19 @@ class Oracle:
         assert psi.shape == self.comp_shape
         self.lib.orc_transport_substep(self.ctx, float(h), _ptr(psi))
         return psi
+
+    def transport_apply(self, uu: float, vv: float, plane, first_order: bool = False):
+        """L(plane) of the limited transport operator (or its first-order
+        upwind part) for one [ny][nz] plane moving with angle (uu, vv)."""
+        f = _f64(plane).reshape(self.ny, self.nz)
+        out = np.zeros_like(f)
+        self.lib.orc_transport_apply(self.ctx, float(uu), float(vv), _ptr(f), _ptr(out), int(bool(first_order)))
+        return out
+
+    def set_transport_cn(self, cn: bool):
+        """Transport time integrator: False = explicit trapezoid (default),
+        True = Crank-Nicolson with the slope lagged, solved by an upwind sweep."""
+        self.lib.orc_set_transport_cn(self.ctx, int(bool(cn)))
 
     def set_angular_exact(self, exact: bool):
         """Angular time integrator: False = Crank-Nicolson (default), True =

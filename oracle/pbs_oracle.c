@@ -58,6 +58,7 @@ struct orc_ctx {
   double *p2;       /* [g][a][ap] density in (u,v) of ap -> a */
   double *u, *v;    /* angle nodes */
   int angular_exact; /* angular time integrator: 0 Crank-Nicolson, 1 exact exponential */
+  int transport_cn;  /* transport time integrator: 0 explicit trapezoid, 1 CN with lagged slope */
 };
 
 /* Angular time integrator (Section 3.4: the paper integrates each sine mode
@@ -247,7 +248,9 @@ orc_ctx *orc_create(const orc_grid *gr, const orc_phys *ph) {
   for (int f = 0; f <= G; f++) {
     double e = c->e_faces[f] > e_floor ? c->e_faces[f] : e_floor;
     c->s_base[f] = ph->model == 1 ? ph->s_scale * orc_bethe_water(ph, e) : bk_stopping(ph, e);
-    c->t_face[f] = ph->t_scale * orc_williams_water(ph, e);
+    /* Reading: the straggling formula is held below 0.5 MeV in both models
+     * (at a few tens of keV its logarithm turns negative). */
+    c->t_face[f] = ph->t_scale * orc_williams_water(ph, e > 0.5 ? e : 0.5);
   }
   fold_straggling(c);
   /* sigma_tr,g is the group average of the scattering coefficient
@@ -702,12 +705,50 @@ static void transport_rhs(const orc_ctx *c, double uu, double vv, const double *
     }
 }
 
+/* The first-order upwind part of the same operator: the fluxes without
+ * their slope terms, s+ psi_m - s- psi_{m+1}. */
+static void transport_rhs_upwind(const orc_ctx *c, double uu, double vv, const double *f, double *out) {
+  int ny = c->ny, nz = c->nz;
+#define V(p, q) (((p) >= 0 && (p) < ny && (q) >= 0 && (q) < nz) ? f[(long)(p) * nz + (q)] : 0.0)
+  double up = uu > 0.0 ? uu : 0.0, um = uu < 0.0 ? -uu : 0.0;
+  double vp = vv > 0.0 ? vv : 0.0, vm = vv < 0.0 ? -vv : 0.0;
+  for (int p = 0; p < ny; p++)
+    for (int q = 0; q < nz; q++) {
+      double fy = (up * V(p, q) - um * V(p + 1, q)) - (up * V(p - 1, q) - um * V(p, q));
+      double fz = (vp * V(p, q) - vm * V(p, q + 1)) - (vp * V(p, q - 1) - vm * V(p, q));
+      out[(long)p * nz + q] = -fy / c->dy - fz / c->dz;
+    }
+#undef V
+}
+
+/* L(psi) (first_order = 0) or its first-order upwind part L1 (1) for one
+ * plane [p][q] moving with angle (uu, vv). */
+void orc_transport_apply(const orc_ctx *c, double uu, double vv, const double *f, double *out, int first_order) {
+  if (first_order) transport_rhs_upwind(c, uu, vv, f, out);
+  else transport_rhs(c, uu, vv, f, out);
+}
+
+/* Transport time integrator (Remark 3).  0 (default): the slope is treated
+ * explicitly, which makes the Crank-Nicolson average an explicit trapezoid
+ * (Heun).  1: Crank-Nicolson in which only the slope part of the implicit
+ * half is taken from the old state (the remark's "slope explicitly in the
+ * implicit part"); the first-order upwind part stays implicit and is solved
+ * by one sweep in the upwind direction. */
+void orc_set_transport_cn(orc_ctx *c, int cn) { c->transport_cn = cn != 0; }
+
 /* Transport substep T(h) for every (g, c, u, v) plane (Remark 2).
- * Reading (Remark 3, depth integration): the slope is treated explicitly,
- * which makes the Crank-Nicolson average an explicit trapezoid (Heun):
- *   psi* = psi + h L(psi),  psi_new = psi + h/2 (L(psi) + L(psi*)). */
+ *  * Heun: psi* = psi + h L(psi),  psi_new = psi + h/2 (L(psi) + L(psi*)).
+ *  * CN with lagged slope: with L = L1 + Ld (upwind part, slope part),
+ *      psi_new - psi = h/2 (L(psi) + L1(psi_new) + Ld(psi)),
+ *    i.e. (I - h/2 L1) psi_new = psi + h/2 L(psi) + h/2 Ld(psi).
+ *    I - h/2 L1 couples a cell only to its upstream neighbours in y and z
+ *    (zero inflow outside the plane), so visiting the cells in the upwind
+ *    order solves it exactly:
+ *      psi_new(p,q) = (r(p,q) + cy psi_new(p-sy,q) + cz psi_new(p,q-sz)) / (1 + cy + cz),
+ *    cy = h |u| / (2 dy), cz = h |v| / (2 dz), sy, sz the signs of u, v. */
 void orc_transport_substep(const orc_ctx *c, double h, double *psi) {
-  int G = c->ng, na = c->na, n = c->ny * c->nz;
+  int G = c->ng, na = c->na, n = c->ny * c->nz, ny = c->ny, nz = c->nz;
+  int cn = c->transport_cn;
 #pragma omp parallel for schedule(static)
   for (int plane = 0; plane < G * 2 * na; plane++) {
     int a = plane % na;
@@ -717,9 +758,27 @@ void orc_transport_substep(const orc_ctx *c, double h, double *psi) {
     double *st = (double *)malloc(sizeof(double) * n);
     double *l1 = (double *)malloc(sizeof(double) * n);
     transport_rhs(c, uu, vv, f, l0);
-    for (int k = 0; k < n; k++) st[k] = f[k] + h * l0[k];
-    transport_rhs(c, uu, vv, st, l1);
-    for (int k = 0; k < n; k++) f[k] = f[k] + 0.5 * h * (l0[k] + l1[k]);
+    if (!cn) {
+      for (int k = 0; k < n; k++) st[k] = f[k] + h * l0[k];
+      transport_rhs(c, uu, vv, st, l1);
+      for (int k = 0; k < n; k++) f[k] = f[k] + 0.5 * h * (l0[k] + l1[k]);
+    } else {
+      transport_rhs_upwind(c, uu, vv, f, l1);
+      /* r = psi + h/2 L + h/2 (L - L1) */
+      for (int k = 0; k < n; k++) st[k] = f[k] + 0.5 * h * l0[k] + 0.5 * h * (l0[k] - l1[k]);
+      double cy = 0.5 * h * fabs(uu) / c->dy, cz = 0.5 * h * fabs(vv) / c->dz;
+      int sy = uu < 0.0 ? -1 : 1, sz = vv < 0.0 ? -1 : 1;
+      for (int i = 0; i < ny; i++) {
+        int p = sy > 0 ? i : ny - 1 - i;
+        for (int j = 0; j < nz; j++) {
+          int q = sz > 0 ? j : nz - 1 - j;
+          int pu = p - sy, qu = q - sz;
+          double xy = (pu >= 0 && pu < ny) ? f[(long)pu * nz + q] : 0.0; /* already new */
+          double xz = (qu >= 0 && qu < nz) ? f[(long)p * nz + qu] : 0.0;
+          f[(long)p * nz + q] = (st[(long)p * nz + q] + cy * xy + cz * xz) / (1.0 + cy + cz);
+        }
+      }
+    }
     free(l0); free(st); free(l1);
   }
 }

@@ -67,6 +67,8 @@ void orc_energy_substep(const orc_ctx *c, double h, const double *rho_yz, double
                         double *edep_yz, double *edep_w_yz);
 void orc_source(const orc_ctx *c, const double *rho_yz, const double *prev, double *out);
 void orc_transport_substep(const orc_ctx *c, double h, double *psi);
+void orc_transport_apply(const orc_ctx *c, double uu, double vv, const double *f, double *out, int first_order);
+void orc_set_transport_cn(orc_ctx *c, int cn);
 void orc_angular_substep(const orc_ctx *c, double h, const double *rho_yz, double *psi);
 void orc_set_angular_exact(orc_ctx *c, int exact);
 void orc_init_beam(const orc_ctx *c, const orc_beam *b, double *psi);
