@@ -103,7 +103,11 @@ typedef struct {
  * lambda_p1 (1/MeV) and Gamma(g_alpha, g_beta) angular deflection P^2
  * (Section 4 and Appendix A.4); s_scale and ts_scale multiply S and the
  * scattering power (0 switches a process off); mp is the proton rest
- * energy (MeV). */
+ * energy (MeV).  t_scale multiplies the energy-straggling coefficient of
+ * Appendix A.2 (Williams' binding-corrected Bohr coefficient of water, per
+ * element with the I-values above, held below 0.5 MeV; either model); 0
+ * (the default) leaves straggling out (see pbs_set_straggling for how the
+ * energy substep takes it). */
 typedef struct {
   double bk_alpha, bk_p;
   double x0;
@@ -114,6 +118,7 @@ typedef struct {
   double g_alpha, g_beta;
   double s_scale, ts_scale;
   int model;
+  double t_scale;
 } pbs_physics;
 
 /* Pencil beam of Eq. (bdy): Gaussian in y, z (cm), u, v and E (MeV). */
@@ -159,6 +164,30 @@ pbs_status pbs_set_physics(pbs_ctx *ctx, const pbs_physics *phys);
  * and no previous P^2. */
 pbs_status pbs_set_tables(pbs_ctx *ctx, const double *s_face, const double *ts, const double *sig_ct,
                           double lambda_p1, const double *p2);
+
+/* Energy straggling (Section 3.2, the Q_1 / Q_2 terms of Eq. 0041-d;
+ * Appendix A.2) with a caller-given coefficient: t_face[ng+1] the mass
+ * straggling coefficient at the group faces (MeV^2 cm^2/g, finite, >= 0;
+ * linear within each group), or NULL to switch straggling off.  Replaces the
+ * coefficient pbs_set_physics built (its t_scale) and keeps every other
+ * table; pbs_set_tables switches straggling off again.  The term splits into
+ * (rho/2) d/dE(T dpsi/dE), discretised by the symmetric interior-penalty
+ * method (penalty 2 T_f over the mean width of the two groups at face f, no
+ * flux through the two outer faces) and applied explicitly to the old state
+ * inside each Crank-Nicolson energy substep, and the drift
+ * (rho/2) d/dE(T' psi), added to the face stopping powers as T'/2 (T' at an
+ * inner face: the mean of its two groups' slopes).  The explicit part is
+ * stable while h rho_max lambda_max / 2 <= 2 (lambda_max bounded by the row
+ * sums of the straggling blocks, h = dx/2); pbs_step, pbs_run, pbs_autotune
+ * and pbs_substep_energy return PBS_ERR_ARG beyond it.  Host array, copied
+ * during the call.  PBS_ERR_STATE before pbs_set_physics / pbs_set_tables. */
+pbs_status pbs_set_straggling(pbs_ctx *ctx, const double *t_face);
+
+/* Copy out the straggling coefficient at the faces t_face[ng+1] (zeros when
+ * off) and the face stopping power before the drift is added, s_base[ng+1]
+ * (pbs_get_tables returns the stopping power with the drift).  Either
+ * pointer may be NULL. */
+pbs_status pbs_get_straggling(const pbs_ctx *ctx, double *t_face, double *s_base);
 
 /* Copy the FP64 host tables out (any pointer may be NULL):
  * s_face[ng+1] (MeV cm^2/g), ts[ng] (rad^2 cm^2/g), sig[ng] (cm^2/g),
@@ -214,15 +243,27 @@ pbs_status pbs_set_beam_steps(pbs_ctx *ctx, const int *steps, int n);
 pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
 
 /* Method options (each changes the computed result, unlike pbs_tuning):
- *   angular_integrator  time integration of each sine mode of the angular
- *                       diffusion (Section 3.4): 0 Crank-Nicolson (Section
- *                       3.3, the default), 1 the mode's exact exponential
- *                       exp(h kappa lam / 2) (the "ODE solver" reading). */
+ *   angular_integrator    time integration of each sine mode of the angular
+ *                         diffusion (Section 3.4): 0 Crank-Nicolson (Section
+ *                         3.3, the default), 1 the mode's exact exponential
+ *                         exp(h kappa lam / 2) (the "ODE solver" reading).
+ *   transport_integrator  depth integration of the lateral transport
+ *                         (Remark 3): 0 the explicit trapezoid (Heun) of the
+ *                         limited upwind operator L (the default); 1
+ *                         Crank-Nicolson whose implicit half keeps the
+ *                         first-order upwind part L1 implicit and takes the
+ *                         limited slope from the old state:
+ *                         (I - h/2 L1) psi_new = psi + h L(psi) - h/2 L1(psi),
+ *                         solved exactly by one sweep in the upwind
+ *                         direction (stable beyond the explicit Courant
+ *                         limit).  Needs nz <= 256. */
 typedef struct {
   int angular_integrator;
+  int transport_integrator;
 } pbs_options;
 
-/* Set / read the method options; PBS_ERR_ARG for an unknown value.  The
+/* Set / read the method options; PBS_ERR_ARG for an unknown value,
+ * PBS_ERR_UNSUPPORTED for transport_integrator 1 with nz > 256.  The
  * deferred closing E(h/2) of the march, if any, is applied first. */
 pbs_status pbs_set_options(pbs_ctx *ctx, const pbs_options *options);
 pbs_status pbs_get_options(const pbs_ctx *ctx, pbs_options *options);

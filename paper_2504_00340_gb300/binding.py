@@ -37,7 +37,8 @@ class PbsGrid(ctypes.Structure):
 
 class PbsPhysics(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("bk_alpha", "bk_p", "x0", "mp", "es", "sigma_ct", "lambda_p1",
-                                               "g_alpha", "g_beta", "s_scale", "ts_scale")] + [("model", ctypes.c_int)]
+                                               "g_alpha", "g_beta", "s_scale", "ts_scale")] + [
+        ("model", ctypes.c_int), ("t_scale", ctypes.c_double)]
 
 
 class PbsBeam(ctypes.Structure):
@@ -54,7 +55,7 @@ class PbsTuning(ctypes.Structure):
 
 
 class PbsOptions(ctypes.Structure):
-    _fields_ = [("angular_integrator", ctypes.c_int)]
+    _fields_ = [("angular_integrator", ctypes.c_int), ("transport_integrator", ctypes.c_int)]
 
 
 class PbsError(RuntimeError):
@@ -71,6 +72,8 @@ SIGNATURES = [
     ("pbs_set_physics", ctypes.c_int, [_VP, ctypes.POINTER(PbsPhysics)]),
     ("pbs_set_tables", ctypes.c_int, [_VP, _D, _D, _D, ctypes.c_double, _D]),
     ("pbs_get_tables", ctypes.c_int, [_VP, _D, _D, _D, _D, _D, _D, _D]),
+    ("pbs_set_straggling", ctypes.c_int, [_VP, _D]),
+    ("pbs_get_straggling", ctypes.c_int, [_VP, _D, _D]),
     ("pbs_set_material", ctypes.c_int, [_VP, _D, ctypes.c_int]),
     ("pbs_launch_beam", ctypes.c_int, [_VP, ctypes.POINTER(PbsBeam)]),
     ("pbs_launch_beams", ctypes.c_int, [_VP, ctypes.POINTER(PbsBeam), ctypes.c_int]),
@@ -177,6 +180,14 @@ def pbs_set_tables(ctx, s_face, ts, sig_ct, lambda_p1: float, p2=None) -> None:
 
 def pbs_get_tables(ctx, s_face, ts, sig, p1, p2, u, v) -> None:
     _check(ctx, load_library().pbs_get_tables(_VP(ctx), *(_ptr(x) for x in (s_face, ts, sig, p1, p2, u, v))))
+
+
+def pbs_set_straggling(ctx, t_face) -> None:
+    _check(ctx, load_library().pbs_set_straggling(_VP(ctx), _ptr(t_face)))
+
+
+def pbs_get_straggling(ctx, t_face, s_base) -> None:
+    _check(ctx, load_library().pbs_get_straggling(_VP(ctx), _ptr(t_face), _ptr(s_base)))
 
 
 def pbs_set_material(ctx, rho: np.ndarray, n_slabs: int) -> None:
@@ -331,7 +342,7 @@ def pbs_destroy(ctx) -> None:
 # ---------------------------------------------------------------- convenience
 
 DEFAULT_PHYSICS = dict(bk_alpha=0.0022, bk_p=1.77, x0=36.08, mp=938.272, es=13.6, sigma_ct=0.012, lambda_p1=0.05,
-                       g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0, model=0)
+                       g_alpha=2.0, g_beta=40.0, s_scale=1.0, ts_scale=1.0, model=0, t_scale=0.0)
 _BEAM_DEFAULTS = dict(e0=100.0, sigma_e=1.0, y0=0.0, z0=0.0, sigma_y=0.3, sigma_z=0.3, u0=0.0, v0=0.0,
                       sigma_u=1e-6, sigma_v=1e-6)
 
@@ -396,6 +407,19 @@ class Solver:
         f = lambda x: None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float64))  # noqa: E731
         pbs_set_tables(self.ctx, f(s_face), f(ts), f(sig_ct), lambda_p1, f(p2))
 
+    def set_straggling(self, t_face=None):
+        """Straggling coefficient at the group faces (ng+1, MeV^2 cm^2/g), or
+        None to switch straggling off (see pbs_set_straggling)."""
+        t = None if t_face is None else np.ascontiguousarray(np.asarray(t_face, dtype=np.float64))
+        if t is not None and t.shape != (self.ng + 1,):
+            raise ValueError("t_face must have ng + 1 entries")
+        pbs_set_straggling(self.ctx, t)
+
+    def straggling(self) -> dict:
+        out = dict(t_face=np.zeros(self.ng + 1), s_base=np.zeros(self.ng + 1))
+        pbs_get_straggling(self.ctx, out["t_face"], out["s_base"])
+        return out
+
     def tables(self) -> dict:
         G, na = self.ng, self.na
         out = dict(s_face=np.zeros(G + 1), ts=np.zeros(G), sig=np.zeros(G), p1=np.zeros((G, G)),
@@ -437,10 +461,13 @@ class Solver:
         transport_ctas, transport_cols, angular_form, source_form."""
         return pbs_get_tuning(self.ctx).as_dict()
 
-    def set_options(self, angular_integrator: str = "cn"):
+    def set_options(self, angular_integrator: str = "cn", transport_integrator: str = "heun"):
         """Method options: angular_integrator 'cn' (Crank-Nicolson, default)
-        or 'exact' (exact exponential of each sine mode)."""
-        pbs_set_options(self.ctx, PbsOptions({"cn": 0, "exact": 1}[angular_integrator]))
+        or 'exact' (exact exponential of each sine mode); transport_integrator
+        'heun' (explicit trapezoid, default) or 'cn' (Crank-Nicolson with the
+        slope lagged, upwind sweep)."""
+        pbs_set_options(self.ctx, PbsOptions({"cn": 0, "exact": 1}[angular_integrator],
+                                             {"heun": 0, "cn": 1}[transport_integrator]))
 
     def set_tuning(self, **kw):
         t = pbs_get_tuning(self.ctx)

@@ -25,7 +25,7 @@
 // opening E(h/2) of step s+1, which Strang splitting puts back to back) are
 // fused: both scans descend in g, so the second consumes the first's output
 // group by group and psi makes one trip through HBM instead of two.
-#include "pbs_internal.cuh"
+#include "energy_scan.cuh"
 
 #include <type_traits>
 
@@ -33,74 +33,12 @@ namespace pbs {
 
 namespace {
 
-template <typename real, typename st>
-__device__ __forceinline__ real load_src(const st *p) { return static_cast<real>(*p); }
-template <>
-__device__ __forceinline__ float load_src<float, __nv_bfloat16>(const __nv_bfloat16 *p) {
-  return __bfloat162float(*p);
-}
-
-template <typename st, typename real>
-__device__ __forceinline__ void store_st(st *p, real v) { *p = static_cast<st>(v); }
-template <>
-__device__ __forceinline__ void store_st<__nv_bfloat16, float>(__nv_bfloat16 *p, float v) {
-  *p = __float2bfloat16_rn(v);
-}
-
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }  // ~1 ulp, ample for FP32 psi
-
-// Neumaier compensated accumulation.
-template <typename real>
-__device__ __forceinline__ void comp_add(real &s, real &c, real x) {
-  real t = s + x;
-  c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
-  s = t;
-}
+using namespace escan;
 
 constexpr int kLanesX = 32;   // lateral points per block (coalesced)
 constexpr int kUnroll = 4;    // groups per prefetch block
 // Angles per block (reduced in shared memory for the dose): a tile-shape
 // knob of the autotuner, 4, 8 (default) or 16.
-
-// Per-lane state of one CN scan.
-template <typename real>
-struct Scan {
-  real rho, rc, c;
-  real carry;        // (psi^1 - psi^2)_{g+1} of old + new
-  real dep, dep_c;   // deposited energy content (compensated)
-  real tsum;         // source recursion T_g
-
-  __device__ __forceinline__ void init(real rho_, real c_) {
-    rho = rho_;
-    c = c_;
-    rc = rho_ * c_;
-    carry = dep = dep_c = tsum = real(0);
-  }
-  // One group: old (o1, o2) -> new (x1, x2); s = src_old + src_new (or 0).
-  // Returns y1 = o1 + x1 for the source recursion of the next component.
-  template <bool HAS_SRC>
-  __device__ __forceinline__ real group(const GroupCoef<real> &k, real o1, real o2, real s, real &x1, real &x2) {
-    const real am = rc * k.sm, ap = rc * k.sp, sg = rc * k.sig;
-    real r0 = (real(1) - am - sg) * o1 + am * o2 + ap * carry;
-    const real r1 = real(-3) * ap * o1 + (real(1) - ap - real(2) * am - sg) * o2 + real(3) * ap * carry;
-    if (HAS_SRC) r0 += c * s;
-    // M = I - c A_gg = [[1+am+sg, -am], [3ap, 1+ap+2am+sg]]
-    const real m00 = real(1) + am + sg;
-    const real m11 = real(1) + ap + real(2) * am + sg;
-    const real inv = recip(m00 * m11 + real(3) * am * ap);
-    x1 = (m11 * r0 + am * r1) * inv;
-    x2 = (m00 * r1 - real(3) * ap * r0) * inv;
-    // deposited energy content: -(phi_g^T c A_gg y_g + phi_g^T c A_up y_{g+1}) - c phi^T src
-    const real y1 = o1 + x1, y2 = o2 + x2;
-    real t = k.ehat * ((-am - sg) * y1 + am * y2) + k.dq * (real(-3) * ap * y1 + (-ap - real(2) * am - sg) * y2) +
-             (k.ehat + real(3) * k.dq) * ap * carry;
-    if (HAS_SRC) t += c * k.ehat * s;
-    comp_add(dep, dep_c, -t);
-    carry = y1 - y2;
-    return y1;
-  }
-};
 
 template <typename real, typename st, bool HAS_SRC, bool HAS_R, bool TWO, int kAnglesY>
 __global__ void __launch_bounds__(kLanesX *kAnglesY)
@@ -239,11 +177,12 @@ __global__ void __launch_bounds__(kLanesX *kAnglesY)
 template <typename real, typename st>
 cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
                           const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
-                          double dose_scale, double flu_scale, const BeamStrides &bs) {
+                          double dose_scale, double flu_scale, const BeamStrides &bs, const StragCoef<real> *strag) {
   if constexpr (sizeof(real) == 4) {
     if (lc.energy_form == 1 && energy_f2_supported(d))
-      return launch_energy_f2<st>(lc, d, psi_k, ha, hb, coef, flu_yz, dose_scale, flu_scale, bs);
+      return launch_energy_f2<st>(lc, d, psi_k, ha, hb, coef, flu_yz, dose_scale, flu_scale, bs, strag);
   }
+  if (strag) return launch_energy_strag<real, st>(lc, d, psi_k, ha, hb, coef, strag, flu_yz, dose_scale, flu_scale, bs);
   const int ay = lc.energy_angles;
   dim3 block(kLanesX, ay);
   dim3 grid((d.nyz + kLanesX - 1) / kLanesX, (d.na + ay - 1) / ay, d.nbeam);
@@ -278,14 +217,16 @@ cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const
 template cudaError_t launch_energy<double, double>(const LaunchCtx &, const Dims &, double *,
                                                    const EnergyHalf<double, double> &,
                                                    const EnergyHalf<double, double> *, const GroupCoef<double> *,
-                                                   double *, double, double, const BeamStrides &);
+                                                   double *, double, double, const BeamStrides &,
+                                                   const StragCoef<double> *);
 template cudaError_t launch_energy<float, float>(const LaunchCtx &, const Dims &, float *,
                                                  const EnergyHalf<float, float> &, const EnergyHalf<float, float> *,
-                                                 const GroupCoef<float> *, double *, double, double, const BeamStrides &);
+                                                 const GroupCoef<float> *, double *, double, double, const BeamStrides &,
+                                                 const StragCoef<float> *);
 template cudaError_t launch_energy<float, __nv_bfloat16>(const LaunchCtx &, const Dims &, float *,
                                                          const EnergyHalf<float, __nv_bfloat16> &,
                                                          const EnergyHalf<float, __nv_bfloat16> *,
                                                          const GroupCoef<float> *, double *, double, double,
-                                                         const BeamStrides &);
+                                                         const BeamStrides &, const StragCoef<float> *);
 
 }  // namespace pbs

@@ -267,7 +267,7 @@ struct PlaneMarch {
   using IO = RowIO<real, VEC, FZ, KV>;
   real *ring;  // this lane's ring base (slot stride 32*KV)
   real *pbase;
-  int ny, nz, col0, gw;  // col0: the lane's first column in the march frame
+  int ny, nz, col0, gw, li;  // col0: the lane's first column in the march frame; li: lane in its group
   bool fwd, on, own;     // on: the lane's columns are loaded; own: they are stored
   real sy, gz, zl, zr;
   int rd, wr;
@@ -422,6 +422,134 @@ struct PlaneMarch {
 };
 
 template <typename real, bool VEC, bool FZ, int KV>
+struct PlaneMarchCN : PlaneMarch<real, VEC, FZ, KV> {
+  using B = PlaneMarch<real, VEC, FZ, KV>;
+  using IO = typename B::IO;
+  Vk<real, KV> xp;   // psi_new of the previous march row (zero before the first: inflow)
+  real a, dinv, cy;  // sweep coefficients: a = cz / D, 1 / D, cy = h |u| / (2 dy)
+  real apow[KV];     // a^(j+1)
+  real aK;           // a^KV
+
+  __device__ __forceinline__ void setup_cn() {
+    cy = real(0.5) * this->sy;
+    const real cz = real(0.5) * this->gz;
+    dinv = real(1) / (real(1) + cy + cz);
+    a = cz * dinv;
+    real t = real(1);
+#pragma unroll
+    for (int j = 0; j < KV; j++) {
+      t *= a;
+      apow[j] = t;
+    }
+    aK = t;
+#pragma unroll
+    for (int j = 0; j < KV; j++) xp.v[j] = real(0);
+  }
+
+  // One iteration: LOAD row i; COMP: solve row m = i-1 (needs psi rows
+  // m-2..m+1 = w[0..3]); FIRST: the first solved row (initialise the carried
+  // y flux).
+  template <bool LOAD, bool COMP, bool FIRST>
+  __device__ __forceinline__ void iter_cn(int i) {
+    Vk<real, KV> *w = this->w;
+    cp_async_wait<kP - 1>();
+    Vk<real, KV> x;
+    if (LOAD) {
+      IO::read(this->ring + this->rd * 32 * KV, x);
+    } else {
+#pragma unroll
+      for (int j = 0; j < KV; j++) x.v[j] = real(0);
+    }
+    this->rd = (this->rd + 1) & (kR - 1);
+    if (i + kP < this->ny) this->issue_row(this->ring + this->wr * 32 * KV, i + kP);
+    cp_async_commit();
+    this->wr = (this->wr + 1) & (kR - 1);
+#pragma unroll
+    for (int k = 0; k < 3; k++) w[k] = w[k + 1];
+    w[3] = x;
+    if (!COMP) return;
+    const real sy = this->sy, gz = this->gz;
+    if (FIRST) {
+      const Vk<real, KV> d = sub4(w[2], w[1]);
+      this->f1 = face4(sy, w[1], slope4(sub4(w[1], w[0]), d));
+      this->e1 = d;
+    }
+    // psi + h L(psi): the limited operator on the old rows
+    Vk<real, KV> dz;
+    z_delta(w[2], gz, this->zl, this->zr, this->gw, dz);
+    const Vk<real, KV> d = sub4(w[3], w[2]);
+    const Vk<real, KV> fh = face4(sy, w[2], slope4(this->e1, d));
+    this->e1 = d;
+    const Vk<real, KV> s = upd4(w[2], this->f1, fh, dz);
+    this->f1 = fh;
+    // minus h/2 L1(psi), h L1 = sy (psi_{m-1} - psi_m) + gz (psi_{q-1} - psi_q)
+    // (march frame: both speeds >= 0, zero ghosts upstream), then the
+    // implicit upwind sweep  x_q = b_q + a x_{q-1},  b_q = (r_q + cy x_{m-1,q}) / D
+    const real lft = this->zl * __shfl_up_sync(0xffffffffu, w[2].v[KV - 1], 1, this->gw);
+    Vk<real, KV> y;
+    real run = real(0);
+#pragma unroll
+    for (int j = 0; j < KV; j++) {
+      const real zprev = j == 0 ? lft : w[2].v[j - 1];
+      real r = s.v[j] - real(0.5) * (sy * (w[1].v[j] - w[2].v[j]) + gz * (zprev - w[2].v[j]));
+      if (!VEC && this->col0 + j >= this->nz) r = real(0);
+      const real b = (r + cy * xp.v[j]) * dinv;
+      run = fma(a, run, b);
+      y.v[j] = run;
+    }
+    // carry into the lane: x(first column - 1), a scan of the lanes' spans
+    // x -> a^KV x + y_last over the lanes to the left (zero inflow at lane 0)
+    real bsum = y.v[KV - 1], ad = aK;
+    for (int dd = 1; dd < this->gw; dd <<= 1) {
+      const real t = __shfl_up_sync(0xffffffffu, bsum, dd, this->gw);
+      if (this->li >= dd) bsum = fma(ad, t, bsum);
+      ad *= ad;
+    }
+    real xin = __shfl_up_sync(0xffffffffu, bsum, 1, this->gw);
+    if (this->li == 0) xin = real(0);
+#pragma unroll
+    for (int j = 0; j < KV; j++) xp.v[j] = fma(apow[j], xin, y.v[j]);
+    this->store_row(i - 1, xp);
+  }
+
+  __device__ __forceinline__ void run_cn() {
+    this->prologue();
+    setup_cn();
+    const int ny = this->ny;
+    iter_cn<true, false, false>(0);
+    if (ny == 1) {
+      iter_cn<false, true, true>(1);
+      return;
+    }
+    iter_cn<true, true, true>(1);
+#pragma unroll 4
+    for (int i = 2; i < ny; i++) iter_cn<true, true, false>(i);
+    iter_cn<false, true, false>(ny);
+  }
+};
+
+template <typename real, bool VEC, bool FZ, int KV>
+__device__ __forceinline__ void march_plane_cn(real *ring, real *pbase, int ny, int nz, int col0, int gw, int li,
+                                               bool fwd, bool on, real sy, real gz, real zl, real zr) {
+  PlaneMarchCN<real, VEC, FZ, KV> pm;
+  pm.ring = ring;
+  pm.pbase = pbase;
+  pm.ny = ny;
+  pm.nz = nz;
+  pm.col0 = col0;
+  pm.gw = gw;
+  pm.li = li;
+  pm.fwd = fwd;
+  pm.on = on;
+  pm.own = on;
+  pm.sy = sy;
+  pm.gz = gz;
+  pm.zl = zl;
+  pm.zr = zr;
+  pm.run_cn();
+}
+
+template <typename real, bool VEC, bool FZ, int KV>
 __device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int nz, int col0, int gw, bool fwd,
                                             bool on, bool own, real sy, real gz, real zl, real zr) {
   PlaneMarch<real, VEC, FZ, KV> pm;
@@ -451,7 +579,10 @@ __device__ __forceinline__ void march_plane(real *ring, real *pbase, int ny, int
 // upstream and 2 downstream, so the owned columns come out exact while the halo
 // lanes' own results (their outer neighbours are missing) are discarded.  A
 // task is one (plane, segment).
-template <typename real, bool VEC, bool FZ, int KV>
+//
+// CN: Crank-Nicolson with the slope lagged (Remark 3; see launch_transport_rows)
+// instead of the explicit trapezoid; one segment per row.
+template <typename real, bool VEC, bool FZ, int KV, bool CN>
 __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict__ psi, long long nplanes, int ny, int nz,
                                                                 int na, int a0, int na_half, int nu, int nv, real du,
                                                                 real dv, real ky, real kz, int nseg, int seg_w, int gw) {
@@ -488,8 +619,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict
     const real uu = (real)((a % nu) - 0.5 * (nu - 1)) * du;
     const real vv = (real)((a / nu) - 0.5 * (nv - 1)) * dv;
     real *pbase = psi + plane * (long long)ny * nz;
-    march_plane<real, VEC, FZ, KV>(ring, pbase, ny, nz, col0, gw, uu >= real(0), on, own, fabs(uu) * ky,
-                               fabs(vv) * kz, zl, zr);
+    if (CN)
+      march_plane_cn<real, VEC, FZ, KV>(ring, pbase, ny, nz, col0, gw, li, uu >= real(0), on, fabs(uu) * ky,
+                                        fabs(vv) * kz, zl, zr);
+    else
+      march_plane<real, VEC, FZ, KV>(ring, pbase, ny, nz, col0, gw, uu >= real(0), on, own, fabs(uu) * ky,
+                                     fabs(vv) * kz, zl, zr);
   }
   cp_async_wait<0>();
 }
@@ -525,7 +660,7 @@ int pick_kv(int nz) {
   return 4;
 }
 
-template <typename real, int KV>
+template <typename real, int KV, bool CN>
 cudaError_t launch_kv(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv, double dy,
                       double dz) {
   const long long nstacks = (long long)d.ncomp * d.ng * 2;
@@ -535,6 +670,7 @@ cudaError_t launch_kv(const LaunchCtx &lc, const Dims &d, real *psi, double tau,
   row_segments(d.nz, KV, nseg, seg_w, lp);
   int gw = 1;
   while (gw < lp) gw <<= 1;
+  if (CN && nseg != 1) return cudaErrorNotSupported;  // the sweep runs along whole rows
   const bool vec = (d.nz % KV) == 0;
   const size_t smem = (size_t)kWarps * kR * 32 * KV * sizeof(real);
   for (int half = 0; half < 2; half++) {
@@ -543,8 +679,8 @@ cudaError_t launch_kv(const LaunchCtx &lc, const Dims &d, real *psi, double tau,
     const int na_half = fz ? d.na - a_split : a_split;
     if (na_half == 0) continue;
     const long long nplanes = nstacks * na_half;
-    auto kern = vec ? (fz ? k_transport_rows<real, true, true, KV> : k_transport_rows<real, true, false, KV>)
-                    : (fz ? k_transport_rows<real, false, true, KV> : k_transport_rows<real, false, false, KV>);
+    auto kern = vec ? (fz ? k_transport_rows<real, true, true, KV, CN> : k_transport_rows<real, true, false, KV, CN>)
+                    : (fz ? k_transport_rows<real, false, true, KV, CN> : k_transport_rows<real, false, false, KV, CN>);
     cudaError_t e;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -569,13 +705,33 @@ cudaError_t launch_kv(const LaunchCtx &lc, const Dims &d, real *psi, double tau,
 
 }  // namespace
 
+// Transport time integrator (Remark 3), lc.transport_cn:
+//  0  explicit trapezoid (Heun) of the limited operator L;
+//  1  Crank-Nicolson whose implicit half keeps the first-order upwind part
+//     L1 implicit and takes the slope part from the old state:
+//       (I - h/2 L1) psi_new = psi + h L(psi) - h/2 L1(psi),
+//     one row at a time in the march frame: the right-hand side of row m
+//     from the old rows m-2..m+1 (as stage 1 of Heun), then the implicit
+//     part couples each cell to the new value upstream in y (the previous
+//     row, in registers) and in z (its left neighbour): a first-order linear
+//     recurrence along the row with the constant factor a = cz / D, run in
+//     each lane over its columns and across lanes by a shuffle scan of the
+//     lanes' affine maps (x -> a^KV x + y_last).  Rows of at most 32 KV
+//     columns (one warp; 256 with KV = 8).
 template <typename real>
 cudaError_t launch_transport_rows(const LaunchCtx &lc, const Dims &d, real *psi, double tau, double du, double dv,
                                   double dy, double dz) {
-  const int kv = lc.transport_cols ? lc.transport_cols : pick_kv(d.nz);
-  if (kv == 6) return launch_kv<real, 6>(lc, d, psi, tau, du, dv, dy, dz);
-  if (kv == 8) return launch_kv<real, 8>(lc, d, psi, tau, du, dv, dy, dz);
-  return launch_kv<real, 4>(lc, d, psi, tau, du, dv, dy, dz);
+  int kv = lc.transport_cols ? lc.transport_cols : pick_kv(d.nz);
+  if (lc.transport_cn) {
+    while (kv < 8 && d.nz > 32 * kv) kv = kv == 4 ? 6 : 8;  // the whole row in one warp
+    if (d.nz > 32 * kv) return cudaErrorNotSupported;
+    if (kv == 6) return launch_kv<real, 6, true>(lc, d, psi, tau, du, dv, dy, dz);
+    if (kv == 8) return launch_kv<real, 8, true>(lc, d, psi, tau, du, dv, dy, dz);
+    return launch_kv<real, 4, true>(lc, d, psi, tau, du, dv, dy, dz);
+  }
+  if (kv == 6) return launch_kv<real, 6, false>(lc, d, psi, tau, du, dv, dy, dz);
+  if (kv == 8) return launch_kv<real, 8, false>(lc, d, psi, tau, du, dv, dy, dz);
+  return launch_kv<real, 4, false>(lc, d, psi, tau, du, dv, dy, dz);
 }
 
 template cudaError_t launch_transport_rows<double>(const LaunchCtx &, const Dims &, double *, double, double, double,

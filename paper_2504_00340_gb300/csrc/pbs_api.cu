@@ -42,6 +42,12 @@ struct pbs_ctx {
   Dims d;
   // FP64 host tables
   std::vector<double> s_face, ts, sig, p1, p2, q1, decay, u, v;
+  // energy straggling: coefficient at the faces, and the stopping power
+  // before the drift T'/2 is folded into s_face
+  std::vector<double> t_face, s_base;
+  bool strag = false;
+  double rho_max = 0.0;      // densest voxel of the material (explicit straggling bound)
+  double strag_bound = 0.0;  // Gershgorin row bound of the straggling blocks
   bool have_tables = false, have_material = false, have_beam = false;
   int n_slabs = 0;
   int steps_done = 0;
@@ -49,12 +55,13 @@ struct pbs_ctx {
   // workspace
   unsigned char *ws = nullptr;
   size_t ws_bytes = 0;
-  size_t off_psi, off_r, off_s, off_rho, off_dose, off_flu, off_coef, off_ts, off_p2, off_init, off_err, total;
+  size_t off_psi, off_r, off_s, off_rho, off_dose, off_flu, off_coef, off_strag, off_ts, off_p2, off_init, off_err,
+      total;
   size_t rsize, ssize;  // element sizes of real and of the source storage
   long long launches = 0;
   // launch shapes (pbs_autotune / pbs_set_tuning)
   pbs_tuning tune{8, 1, 0, 0, 2, 1};
-  pbs_options opts{0};
+  pbs_options opts{0, 0};
   // whole-march CUDA graph (pbs_run with use_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -111,6 +118,7 @@ void layout(pbs_ctx *c) {
   c->off_dose = o; o = align256(o + B * c->nx * nyz * 8);       // [beam][slab][yz]
   c->off_flu = o; o = align256(o + B * (c->nx + 1) * nyz * 8);  // [beam][plane][yz]
   c->off_coef = o; o = align256(o + (size_t)c->ng * 10 * S);
+  c->off_strag = o; o = align256(o + (size_t)c->ng * 12 * S);
   c->off_ts = o; o = align256(o + (size_t)c->ng * S);
   c->off_p2 = o; o = align256(o + ((c->K > 0) ? (size_t)c->ng * c->na * c->na * SS : 0));
   c->off_init = o; o = align256(o + B * init_stride(c) * 8);  // beam projection factors per beam
@@ -130,6 +138,7 @@ LaunchCtx lctx(pbs_ctx *c) {
   lc.angular_form = c->tune.angular_form;
   lc.source_form = c->tune.source_form;
   lc.angular_exact = c->opts.angular_integrator;
+  lc.transport_cn = c->opts.transport_integrator;
   return lc;
 }
 
@@ -271,6 +280,98 @@ double gamma_density(double th, double al, double be) {
   return std::exp(al * std::log(be) + (al - 1.0) * std::log(th) - be * th - std::lgamma(al));
 }
 
+// Straggling coefficient of water per gram (Appendix A.2): Bohr's
+// 4 pi e^4 per electron with Williams' binding factor
+// 1 + 4 I / (3 m_e v^2) ln(2 m_e v^2 / I), m_e v^2 = m_e c^2 beta^2, for the
+// electrons of each element (N_A Z / A per gram, its own I-value).
+double straggling_williams_water(const pbs_physics &ph, double e) {
+  const double gam = 1.0 + e / ph.mp, mv2 = kMeC2 * (1.0 - 1.0 / (gam * gam));
+  const double bohr = 4.0 * 3.14159265358979323846 * kCoulomb * kCoulomb * kAvogadro;  // MeV^2 cm^2 / mol
+  double s = 0.0;
+  for (const Element &el : kWater) {
+    const double i = excitation_mev(el.z);
+    s += el.w * el.z / el.a * (1.0 + 4.0 * i / (3.0 * mv2) * std::log(2.0 * mv2 / i));
+  }
+  return bohr * s;
+}
+
+// The drift half of the straggling term, (rho/2) d/dE(T' psi), is the
+// stopping-power operator with S replaced by T'/2: fold it into the face
+// stopping powers.  T is linear in each group; T' at an inner face is the
+// mean of the slopes of its two groups, at an outer face its one group's.
+void fold_straggling(pbs_ctx *c) {
+  const int G = c->ng;
+  c->s_face.assign(G + 1, 0.0);
+  c->strag = false;
+  for (int f = 0; f <= G; f++) {
+    const double lo = f > 0 ? (c->t_face[f] - c->t_face[f - 1]) / c->de[f - 1] : 0.0;
+    const double hi = f < G ? (c->t_face[f + 1] - c->t_face[f]) / c->de[f] : 0.0;
+    const double slope = (f == 0) ? hi : (f == G ? lo : 0.5 * (lo + hi));
+    c->s_face[f] = c->s_base[f] + 0.5 * slope;
+    c->strag = c->strag || c->t_face[f] != 0.0;
+  }
+}
+
+// Blocks of the interior-penalty part (rho/2) d/dE(T dpsi/dE) for group g,
+// per unit density and times 2 (StragCoef).  Face f between groups a (below)
+// and b = a + 1 (above) adds, with the traces psi^-_f = p1_a + p2_a,
+// psi^+_f = p1_b - p2_b, the jump J = psi^- - psi^+, the flux average
+// F = T_f (p2_a / dE_a + p2_b / dE_b) and the penalty s = 2 T_f / h_f
+// (alpha = (1+1)^2/2, h_f the mean width of a and b):
+//   to row 1 of a:  (F - s J) / dE_a          to row 1 of b:  -(F - s J) / dE_b
+//   to row 2 of a:  3 (F + (T_f / dE_a - s) J) / dE_a
+//   to row 2 of b:  3 (F + (T_f / dE_b - s) J) / dE_b
+// and each group adds -12 Tbar_g p2_g / dE_g^2 to its row 2 (the volume
+// term, Tbar_g the mean of its face values).  Outer faces carry nothing.
+void strag_blocks(const pbs_ctx *c, int g, double out[12]) {
+  const int G = c->ng;
+  double *lo = out, *dd = out + 4, *up = out + 8;
+  for (int i = 0; i < 12; i++) out[i] = 0.0;
+  const double de = c->de[g];
+  dd[3] -= 12.0 * 0.5 * (c->t_face[g] + c->t_face[g + 1]) / (de * de);
+  // side 0: the face above g (g is side a, the neighbour b = g + 1 fills up);
+  // side 1: the face below g (g is side b, the neighbour a = g - 1 fills lo)
+  for (int side = 0; side < 2; side++) {
+    const int f = side == 0 ? g + 1 : g;
+    if (f <= 0 || f >= G) continue;
+    const int ga = f - 1, gb = f;
+    const double t = c->t_face[f], da = c->de[ga], db = c->de[gb];
+    const double pen = 2.0 * t / (0.5 * (da + db));
+    // F and J as linear forms on (p1_a, p2_a, p1_b, p2_b)
+    const double F[4] = {0.0, t / da, 0.0, t / db};
+    const double J[4] = {1.0, 1.0, -1.0, 1.0};
+    const double own_de = side == 0 ? da : db;
+    const double sign1 = side == 0 ? 1.0 : -1.0;
+    double *other = side == 0 ? up : lo;
+    for (int q = 0; q < 4; q++) {
+      const double r1 = sign1 * (F[q] - pen * J[q]) / own_de;
+      const double r2 = 3.0 * (F[q] + (t / own_de - pen) * J[q]) / own_de;
+      // q = 0, 1 act on group a, q = 2, 3 on group b
+      const bool on_self = (side == 0) == (q < 2);
+      double *blk = on_self ? dd : other;
+      blk[0 * 2 + (q & 1)] += r1;
+      blk[1 * 2 + (q & 1)] += r2;
+    }
+  }
+}
+
+// Gershgorin bound of the explicit straggling update: a substep of length
+// h applies rho h (St / 2) psi explicitly; forward Euler on this operator
+// (real, non-positive spectrum) is stable for h rho lambda_max / 2 <= 2.
+double strag_row_bound(const pbs_ctx *c) {
+  double m = 0.0;
+  for (int g = 0; g < c->ng; g++) {
+    double b[12];
+    strag_blocks(c, g, b);
+    for (int r = 0; r < 2; r++) {
+      double s = 0.0;
+      for (int blk = 0; blk < 3; blk++) s += std::fabs(b[4 * blk + 2 * r]) + std::fabs(b[4 * blk + 2 * r + 1]);
+      m = std::max(m, s);
+    }
+  }
+  return m;
+}
+
 // Exponential energy transfer P^1(g' -> g) = lambda e^{-lambda (E_g' - E_g)},
 // normalised per emitting group g', and the source weights of the fused
 // recursion (q1 = lambda sigma_g' dE_g' / Z_g', decay = e^{-lambda (E_g+1 - E_g)}),
@@ -291,17 +392,22 @@ void transfer_tables(pbs_ctx *c, double lambda) {
 
 void build_tables(pbs_ctx *c, const pbs_physics &ph) {
   const int G = c->ng, na = c->na;
-  c->s_face.assign(G + 1, 0.0);
   c->ts.assign(G, 0.0);
   c->sig.assign(G, ph.sigma_ct);
   // a face at E <= 0 takes the stopping power at half the lowest group width
   // (the Bethe-Bloch tables: at no less than 0.5 MeV)
   const bool bethe = ph.model == 1;
   const double floor_e = bethe ? std::max(0.5 * c->de[0], 0.5) : 0.5 * c->de[0];
+  c->s_base.assign(G + 1, 0.0);
+  c->t_face.assign(G + 1, 0.0);
   for (int f = 0; f <= G; f++) {
     const double e = std::max(c->e_faces[f], floor_e);
-    c->s_face[f] = bethe ? stopping_bethe_water(ph, e) : stopping_bk(ph, e);
+    c->s_base[f] = bethe ? stopping_bethe_water(ph, e) : stopping_bk(ph, e);
+    // the straggling formula is held below 0.5 MeV (its logarithm turns
+    // negative at a few tens of keV)
+    if (ph.t_scale > 0.0) c->t_face[f] = ph.t_scale * straggling_williams_water(ph, std::max(e, 0.5));
   }
+  fold_straggling(c);
   // 8-point Gauss-Legendre nodes / weights on [-1, 1] (positive half)
   static const double gl_x[4] = {0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
   static const double gl_w[4] = {0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
@@ -366,6 +472,16 @@ pbs_status upload_tables(pbs_ctx *c) {
     k.decay = (real)c->decay[g];
     k.pad = 0;
   }
+  std::vector<StragCoef<real>> sc(c->strag ? G : 0);
+  for (int g = 0; g < (int)sc.size(); g++) {
+    double b[12];
+    strag_blocks(c, g, b);
+    real *o = reinterpret_cast<real *>(&sc[g]);
+    for (int i = 0; i < 12; i++) o[i] = (real)b[i];
+  }
+  if (!sc.empty())
+    PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_strag), sc.data(), sizeof(StragCoef<real>) * G,
+                                cudaMemcpyHostToDevice, c->stream));
   std::vector<real> ts(G);
   for (int g = 0; g < G; g++) ts[g] = (real)c->ts[g];
   PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_coef), coef.data(), sizeof(GroupCoef<real>) * G,
@@ -462,7 +578,8 @@ pbs_status energy_run(pbs_ctx *c, double h, int slab_a, int slab_b, int flu_plan
     {
       ProfScope ps(c, PBS_KERNEL_ENERGY);
       e = launch_energy<real, st>(lc, d, psi + (size_t)k * c->d.comp_elems, ha, two ? &hb : nullptr, coef, flu,
-                                  c->du * c->dv / c->dx, c->du * c->dv, bs);
+                                  c->du * c->dv / c->dx, c->du * c->dv, bs,
+                                  c->strag ? at<StragCoef<real>>(c, c->off_strag) : nullptr);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "energy kernel");
     if (k < c->K) {
@@ -710,6 +827,16 @@ pbs_status eval_source_impl(pbs_ctx *c, int k_from, int slab, double *out) {
 
 bool ready_to_march(pbs_ctx *c) { return c->ws && c->have_tables && c->have_material && c->have_beam; }
 
+// Explicit straggling is stable while a substep h keeps
+// h rho_max lambda_max(St) / 2 <= 2 (Gershgorin bound of lambda_max).
+pbs_status strag_guard(pbs_ctx *c, double h) {
+  if (!c->strag) return PBS_OK;
+  if (h * c->rho_max * c->strag_bound > 4.0)
+    return fail(c, PBS_ERR_ARG,
+                "explicit straggling unstable for this step: h rho T / dE^2 too large (refine dx or coarsen the groups)");
+  return PBS_OK;
+}
+
 // Launch-shape autotuner.  Times each candidate shape of the energy pass
 // (angles per block) and of the streaming transport (resident CTAs per SM)
 // on the launched beams with CUDA events, best of `reps`, keeps the fastest,
@@ -919,11 +1046,15 @@ pbs_status pbs_bind_workspace(pbs_ctx *c, void *p, size_t bytes) {
 pbs_status pbs_set_physics(pbs_ctx *c, const pbs_physics *ph) {
   if (!c || !ph) return fail(c, PBS_ERR_ARG, "null physics");
   if (!(ph->mp > 0) || !(ph->lambda_p1 > 0) || !(ph->g_beta > 0) || !(ph->g_alpha > 0) || ph->sigma_ct < 0 ||
-      ph->s_scale < 0 || ph->ts_scale < 0 || ph->model < 0 || ph->model > 1 ||
+      ph->s_scale < 0 || ph->ts_scale < 0 || ph->model < 0 || ph->model > 1 || !(ph->t_scale >= 0) ||
+      !std::isfinite(ph->t_scale) ||
       (ph->model == 0 && (!(ph->bk_alpha > 0) || !(ph->bk_p > 0) || !(ph->x0 > 0))))
     return fail(c, PBS_ERR_ARG, "physics parameters out of range");
+  { pbs_status fr = c->ws ? PBS_DISPATCH(c, flush_impl, c) : PBS_OK; if (fr != PBS_OK) return fr; }
   build_tables(c, *ph);
+  c->strag_bound = strag_row_bound(c);
   c->have_tables = true;
+  drop_graph(c);
   if (!c->ws) return PBS_OK;  // uploaded at bind time
   return PBS_DISPATCH(c, upload_tables, c);
 }
@@ -946,7 +1077,10 @@ pbs_status pbs_set_tables(pbs_ctx *c, const double *s_face, const double *ts, co
     return fail(c, PBS_ERR_STATE, "no previous P^2: pass p2");
   }
   { pbs_status fr = c->ws ? PBS_DISPATCH(c, flush_impl, c) : PBS_OK; if (fr != PBS_OK) return fr; }
-  c->s_face.assign(s_face, s_face + G + 1);
+  c->s_base.assign(s_face, s_face + G + 1);
+  c->t_face.assign(G + 1, 0.0);  // caller tables replace the built-in straggling too
+  fold_straggling(c);
+  c->strag_bound = 0.0;
   c->ts.assign(ts, ts + G);
   c->sig.assign(sig_ct, sig_ct + G);
   if (p2) c->p2.assign(p2, p2 + np2);
@@ -971,6 +1105,31 @@ pbs_status pbs_get_tables(const pbs_ctx *c, double *s_face, double *ts, double *
   return PBS_OK;
 }
 
+pbs_status pbs_set_straggling(pbs_ctx *c, const double *t_face) {
+  if (!c) return PBS_ERR_ARG;
+  if (!c->have_tables) return fail(c, PBS_ERR_STATE, "set the physics or the tables first");
+  const int G = c->ng;
+  if (t_face)
+    for (int f = 0; f <= G; f++)
+      if (!(t_face[f] >= 0) || !std::isfinite(t_face[f])) return fail(c, PBS_ERR_ARG, "t_face must be finite and >= 0");
+  { pbs_status fr = c->ws ? PBS_DISPATCH(c, flush_impl, c) : PBS_OK; if (fr != PBS_OK) return fr; }
+  if (t_face) c->t_face.assign(t_face, t_face + G + 1);
+  else c->t_face.assign(G + 1, 0.0);
+  fold_straggling(c);
+  c->strag_bound = strag_row_bound(c);
+  drop_graph(c);
+  if (!c->ws) return PBS_OK;
+  return PBS_DISPATCH(c, upload_tables, c);
+}
+
+pbs_status pbs_get_straggling(const pbs_ctx *c, double *t_face, double *s_base) {
+  if (!c) return PBS_ERR_ARG;
+  if (!c->have_tables) return PBS_ERR_STATE;
+  if (t_face) std::memcpy(t_face, c->t_face.data(), 8 * c->t_face.size());
+  if (s_base) std::memcpy(s_base, c->s_base.data(), 8 * c->s_base.size());
+  return PBS_OK;
+}
+
 pbs_status pbs_set_material(pbs_ctx *c, const double *rho, int n) {
   if (!c || !rho || n < 1 || n > c->nx) return fail(c, PBS_ERR_ARG, "bad material");
   if (!c->ws) return fail(c, PBS_ERR_STATE, "bind a workspace first");
@@ -979,6 +1138,8 @@ pbs_status pbs_set_material(pbs_ctx *c, const double *rho, int n) {
     if (!(rho[e] >= 0.0) || !std::isfinite(rho[e])) return fail(c, PBS_ERR_ARG, "density must be finite and >= 0");
   pbs_status r = PBS_DISPATCH_R(c, set_material_impl, c, rho, n);
   if (r != PBS_OK) return r;
+  c->rho_max = 0.0;
+  for (size_t e = 0; e < (size_t)n * c->ny * c->nz; e++) c->rho_max = std::max(c->rho_max, rho[e]);
   c->n_slabs = n;
   c->have_material = true;
   return PBS_OK;
@@ -1022,6 +1183,7 @@ pbs_status pbs_set_beam_steps(pbs_ctx *c, const int *steps, int n) {
 pbs_status pbs_run(pbs_ctx *c, int use_graph) {
   if (!c) return PBS_ERR_ARG;
   if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
+  { pbs_status gr = strag_guard(c, 0.5 * c->dx); if (gr != PBS_OK) return gr; }
   if (use_graph) return PBS_DISPATCH(c, run_graph_impl, c);
   return PBS_DISPATCH(c, run_impl, c);
 }
@@ -1029,6 +1191,7 @@ pbs_status pbs_run(pbs_ctx *c, int use_graph) {
 pbs_status pbs_autotune(pbs_ctx *c, int reps) {
   if (!c || reps < 1) return fail(c, PBS_ERR_ARG, "reps must be >= 1");
   if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
+  { pbs_status gr = strag_guard(c, 0.5 * c->dx); if (gr != PBS_OK) return gr; }
   return PBS_DISPATCH(c, autotune_impl, c, reps);
 }
 
@@ -1048,6 +1211,10 @@ pbs_status pbs_set_tuning(pbs_ctx *c, const pbs_tuning *t) {
 pbs_status pbs_set_options(pbs_ctx *c, const pbs_options *o) {
   if (!c || !o) return fail(c, PBS_ERR_ARG, "null options");
   if (o->angular_integrator < 0 || o->angular_integrator > 1) return fail(c, PBS_ERR_ARG, "unknown angular integrator");
+  if (o->transport_integrator < 0 || o->transport_integrator > 1)
+    return fail(c, PBS_ERR_ARG, "unknown transport integrator");
+  if (o->transport_integrator == 1 && c->nz > 256)
+    return fail(c, PBS_ERR_UNSUPPORTED, "the Crank-Nicolson transport sweep takes rows of at most 256 columns");
   { pbs_status fr = c->ws ? PBS_DISPATCH(c, flush_impl, c) : PBS_OK; if (fr != PBS_OK) return fr; }
   c->opts = *o;
   drop_graph(c);
@@ -1070,6 +1237,7 @@ pbs_status pbs_step(pbs_ctx *c, int n) {
   if (!c || n < 0) return fail(c, PBS_ERR_ARG, "bad step count");
   if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
   if (c->steps_done + n > c->n_slabs) return fail(c, PBS_ERR_ARG, "march would pass the last material slab");
+  { pbs_status gr = strag_guard(c, 0.5 * c->dx); if (gr != PBS_OK) return gr; }
   return PBS_DISPATCH(c, step_impl, c, n);
 }
 
@@ -1206,6 +1374,7 @@ pbs_status pbs_substep_energy(pbs_ctx *c, double h, int slab, int flu_plane) {
   if (!c || !(h >= 0) || slab < 0 || slab >= c->n_slabs || flu_plane > c->nx)
     return fail(c, PBS_ERR_ARG, "bad substep arguments");
   if (!c->ws || !c->have_tables || !c->have_material) return fail(c, PBS_ERR_STATE, "not set up");
+  { pbs_status gr = strag_guard(c, h); if (gr != PBS_OK) return gr; }
   { pbs_status fr = PBS_DISPATCH(c, flush_impl, c); if (fr != PBS_OK) return fr; }
   return PBS_DISPATCH(c, energy_all, c, h, slab, flu_plane);
 }

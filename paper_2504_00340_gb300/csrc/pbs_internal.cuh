@@ -39,6 +39,16 @@ struct GroupCoef {
   real pad;
 };
 
+// Energy straggling (interior-penalty DG, Section 3.2): the 2x2 blocks of
+// group g on psi_{g-1}, psi_g, psi_{g+1}, per unit density and times 2, so
+// that rho c (lo psi_{g-1} + d psi_g + up psi_{g+1}) is the explicit
+// straggling contribution of a substep with CN factor c = h/2.  Row-major
+// [r][q]: entry [2 r + q] couples DG coefficient q to row r.
+template <typename real>
+struct StragCoef {
+  real lo[4], d[4], up[4];
+};
+
 struct Dims {
   int ny, nz, ng, nu, nv, na, nyz, ncomp;  // ncomp = n_beams * (K + 1): all components
   int nbeam;                                // independent beams
@@ -156,6 +166,7 @@ struct LaunchCtx {
                            // (form 1 where the grid allows, else 0)
   int source_form = 1;     // BF16 source contraction: 0 tile by tile, 1 TMA/MMA/epilogue pipeline
   int angular_exact = 0;   // angular time integrator: 0 Crank-Nicolson, 1 exact exponential per mode
+  int transport_cn = 0;    // transport time integrator: 0 explicit trapezoid, 1 CN with lagged slope
 };
 
 // One E substep's per-lane inputs and outputs: density of its slab, c = h/2,
@@ -181,7 +192,8 @@ bool energy_f2_supported(const Dims &d);
 template <typename st>
 cudaError_t launch_energy_f2(const LaunchCtx &lc, const Dims &d, float *psi_k, const EnergyHalf<float, st> &ha,
                              const EnergyHalf<float, st> *hb, const GroupCoef<float> *coef, double *flu_yz,
-                             double dose_scale, double flu_scale, const BeamStrides &bs);
+                             double dose_scale, double flu_scale, const BeamStrides &bs,
+                             const StragCoef<float> *strag = nullptr);
 
 // E substep on one component of every beam; with hb != NULL, two consecutive
 // E substeps (ha then hb) fused in one pass.  flu_yz receives the fluence
@@ -189,7 +201,15 @@ cudaError_t launch_energy_f2(const LaunchCtx &lc, const Dims &d, float *psi_k, c
 template <typename real, typename st>
 cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
                           const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef, double *flu_yz,
-                          double dose_scale, double flu_scale, const BeamStrides &bs);
+                          double dose_scale, double flu_scale, const BeamStrides &bs,
+                          const StragCoef<real> *strag = nullptr);
+
+// The same with the explicit straggling term (strag != NULL), one lane per thread.
+template <typename real, typename st>
+cudaError_t launch_energy_strag(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,
+                                const EnergyHalf<real, st> *hb, const GroupCoef<real> *coef,
+                                const StragCoef<real> *strag, double *flu_yz, double dose_scale, double flu_scale,
+                                const BeamStrides &bs);
 
 // The driver's tensor-map encoder (cuTensorMapEncodeTiled), looked up once
 // through the runtime; NULL when the driver does not provide it.

@@ -72,6 +72,13 @@ def main(argv=None):
     p.add_argument("--ng", type=int)
     p.add_argument("--steps", type=int)
     p.add_argument("--precision", choices=["fp64", "fp32", "mixed"])
+    p.add_argument("--straggling", type=float, default=0.0,
+                   help="energy straggling: multiple of the Appendix A.2 coefficient (0: off)")
+    p.add_argument("--physics-model", type=int, choices=[0, 1],
+                   help="0: Bragg-Kleeman + Highland, 1: the paper's Appendix A tables")
+    p.add_argument("--energy-form", type=int, choices=[0, 1], help="FP32 energy kernel form (default: tuned)")
+    p.add_argument("--transport", choices=["heun", "cn"], default="heun",
+                   help="transport integrator: explicit trapezoid (default) or CN with the slope lagged")
     p.add_argument("--spots", type=int, default=0, help="run the first N spots of the 256-spot batch")
     p.add_argument("--max-gb", type=float, default=48.0, help="device workspace per spot bucket (GiB)")
     p.add_argument("--no-graph", action="store_true")
@@ -91,16 +98,23 @@ def main(argv=None):
     if a.ng:
         # keep the group width: the energy range scales with the group count
         kw["e_max"] = w.e_min + (w.e_max - w.e_min) * a.ng / w.ng
+    if a.straggling or a.physics_model is not None:
+        phys = dict(w.physics, t_scale=a.straggling)
+        if a.physics_model is not None:
+            phys["model"] = a.physics_model
+        kw["physics"] = phys
     w = w.with_(**kw)
     steps = a.steps or w.n_steps
     prec = a.precision or w.precision
     import torch
     torch.cuda.set_device(0)
-    out, dose, flu = march(binding, w, steps, prec, autotune=a.autotune, profile=not a.no_profile)
+    out, dose, flu = march(binding, w, steps, prec, autotune=a.autotune, profile=not a.no_profile,
+                           energy_form=a.energy_form, transport=a.transport)
     out.update({"workload": w.name, "ny": w.ny, "nz": w.nz, "ng": w.ng, "n_scatter": w.n_scatter,
-                "medium": w.medium})
+                "medium": w.medium, "physics_model": w.physics.get("model", 0),
+                "straggling": w.physics.get("t_scale", 0.0), "transport": a.transport})
     if a.vs_fp64 and prec != "fp64":
-        ref, dose64, flu64 = march(binding, w, steps, "fp64", autotune=False, profile=False)
+        ref, dose64, flu64 = march(binding, w, steps, "fp64", autotune=False, profile=False, transport=a.transport)
         out["fp64"] = {"cell_updates_per_s": ref["cell_updates_per_s"],
                        "speedup": out["cell_updates_per_s"] / ref["cell_updates_per_s"],
                        "dose_err_vs_fp64": float(np.abs(dose - dose64).max() / np.abs(dose64).max()),
@@ -108,17 +122,21 @@ def main(argv=None):
     print(json.dumps(out))
 
 
-def march(binding, w, steps, prec, autotune=False, profile=True):
+def march(binding, w, steps, prec, autotune=False, profile=True, energy_form=None, transport="heun"):
     """The whole march of workload w (steps depth steps) in the given
     precision: device time by CUDA events around step + flush on the
     context's stream; per-kernel times when profiling."""
     import torch
     s = binding.Solver(w.grid(), nx=steps, dx=w.dx, n_scatter=w.n_scatter, precision=prec, physics=w.physics)
     try:
+        if transport != "heun":
+            s.set_options(transport_integrator=transport)
         s.set_material(w.density(steps))
         s.launch_beam(**w.beam)
         if autotune:
             s.autotune(2)
+        if energy_form is not None:
+            s.set_tuning(energy_form=energy_form)
         s.set_profiling(profile)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()

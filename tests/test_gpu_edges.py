@@ -174,10 +174,10 @@ def test_maximum_group_count(orc, precision, tol):
 def test_widest_rows(orc, cols):
     """nz = 1024, the widest row the library accepts: nine segments with halo
     lanes per row, against the oracle's transport."""
-    grid = _grid(3, 1024, 2, 4, 1)
+    grid = _grid(3, 1024, 4, 4, 1)
     s = binding.Solver(grid, nx=1, dx=0.05, precision="fp64")
     s.set_tuning(transport_cols=cols)
-    psi = random_state((1, 2, 4, 2, 3, 1024), seed=8)
+    psi = random_state((1, 2, 4, 4, 3, 1024), seed=8)
     s.write_psi(0, psi)
     s.substep_transport(0.3)
     assert _relerr(s.read_psi(0), orc.Oracle(grid).transport_substep(0.3, psi)) < 1e-12
