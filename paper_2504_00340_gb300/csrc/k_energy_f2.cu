@@ -350,7 +350,7 @@ __device__ __forceinline__ void step_angle_x(const Coef2 &q, float2 cs, float2 r
 // from psi_{g-1}, psi_g, psi_{g+1}, the deposited energy its phi-weighted
 // angle sum; the fused pair's second scan runs one group behind the first.
 template <typename st, bool HAS_SRC, bool HAS_R, bool TWO, int kY>
-__global__ void __launch_bounds__(kX *kY, TWO ? 1 : 512 / (kX * kY))
+__global__ void __launch_bounds__(kX *kY, (TWO && (HAS_SRC || HAS_R)) ? 1 : 512 / (kX * kY))
     k_energy_f2_strag(Dims d, float *__restrict__ psi, const st *__restrict__ src_a, const st *__restrict__ src_b,
                 st *__restrict__ r_a, st *__restrict__ r_b, const float *__restrict__ rho_a,
                 const float *__restrict__ rho_b, const GroupCoef<float> *__restrict__ coef,
