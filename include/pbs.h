@@ -256,10 +256,20 @@ pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
  *                         (I - h/2 L1) psi_new = psi + h L(psi) - h/2 L1(psi),
  *                         solved exactly by one sweep in the upwind
  *                         direction (stable beyond the explicit Courant
- *                         limit).  Needs nz <= 256. */
+ *                         limit).  Needs nz <= 256.
+ *   straggling_integrator with energy straggling on (pbs_set_straggling):
+ *                         0 the interior-penalty part explicit inside the
+ *                         Crank-Nicolson energy step (the default; one scan
+ *                         per fused pair of substeps); 1 inside the
+ *                         Crank-Nicolson step as well, as the printed scheme
+ *                         reads: the block-tridiagonal system is solved by
+ *                         block elimination from the top group down and
+ *                         substitution upward (two passes over psi per
+ *                         substep, no fused pair, no stability bound). */
 typedef struct {
   int angular_integrator;
   int transport_integrator;
+  int straggling_integrator;
 } pbs_options;
 
 /* Set / read the method options; PBS_ERR_ARG for an unknown value,

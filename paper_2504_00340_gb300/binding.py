@@ -55,7 +55,8 @@ class PbsTuning(ctypes.Structure):
 
 
 class PbsOptions(ctypes.Structure):
-    _fields_ = [("angular_integrator", ctypes.c_int), ("transport_integrator", ctypes.c_int)]
+    _fields_ = [("angular_integrator", ctypes.c_int), ("transport_integrator", ctypes.c_int),
+                ("straggling_integrator", ctypes.c_int)]
 
 
 class PbsError(RuntimeError):
@@ -461,13 +462,17 @@ class Solver:
         transport_ctas, transport_cols, angular_form, source_form."""
         return pbs_get_tuning(self.ctx).as_dict()
 
-    def set_options(self, angular_integrator: str = "cn", transport_integrator: str = "heun"):
+    def set_options(self, angular_integrator: str = "cn", transport_integrator: str = "heun",
+                    straggling_integrator: str = "explicit"):
         """Method options: angular_integrator 'cn' (Crank-Nicolson, default)
         or 'exact' (exact exponential of each sine mode); transport_integrator
         'heun' (explicit trapezoid, default) or 'cn' (Crank-Nicolson with the
-        slope lagged, upwind sweep)."""
+        slope lagged, upwind sweep); straggling_integrator 'explicit' (inside
+        the CN energy step, default) or 'cn' (in the CN step, block
+        elimination)."""
         pbs_set_options(self.ctx, PbsOptions({"cn": 0, "exact": 1}[angular_integrator],
-                                             {"heun": 0, "cn": 1}[transport_integrator]))
+                                             {"heun": 0, "cn": 1}[transport_integrator],
+                                             {"explicit": 0, "cn": 1}[straggling_integrator]))
 
     def set_tuning(self, **kw):
         t = pbs_get_tuning(self.ctx)

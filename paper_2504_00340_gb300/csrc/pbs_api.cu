@@ -55,13 +55,13 @@ struct pbs_ctx {
   // workspace
   unsigned char *ws = nullptr;
   size_t ws_bytes = 0;
-  size_t off_psi, off_r, off_s, off_rho, off_dose, off_flu, off_coef, off_strag, off_ts, off_p2, off_init, off_err,
-      total;
+  size_t off_psi, off_r, off_s, off_rho, off_dose, off_flu, off_coef, off_strag, off_omega, off_dinv, off_ts, off_p2,
+      off_init, off_err, total;
   size_t rsize, ssize;  // element sizes of real and of the source storage
   long long launches = 0;
   // launch shapes (pbs_autotune / pbs_set_tuning)
   pbs_tuning tune{8, 1, 0, 0, 2, 1};
-  pbs_options opts{0, 0};
+  pbs_options opts{0, 0, 0};
   // whole-march CUDA graph (pbs_run with use_graph)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
@@ -119,6 +119,8 @@ void layout(pbs_ctx *c) {
   c->off_flu = o; o = align256(o + B * (c->nx + 1) * nyz * 8);  // [beam][plane][yz]
   c->off_coef = o; o = align256(o + (size_t)c->ng * 10 * S);
   c->off_strag = o; o = align256(o + (size_t)c->ng * 12 * S);
+  c->off_omega = o; o = align256(o + (size_t)c->ng * 2 * S);          // column weights of the CN straggling dose
+  c->off_dinv = o; o = align256(o + (size_t)c->ng * 4 * nyz * S);     // eliminated blocks, [g][4][yz]
   c->off_ts = o; o = align256(o + (size_t)c->ng * S);
   c->off_p2 = o; o = align256(o + ((c->K > 0) ? (size_t)c->ng * c->na * c->na * SS : 0));
   c->off_init = o; o = align256(o + B * init_stride(c) * 8);  // beam projection factors per beam
@@ -372,6 +374,48 @@ double strag_row_bound(const pbs_ctx *c) {
   return m;
 }
 
+// Column weights of the deposited energy for the CN straggling step: with
+// A the energy operator per unit rho c and phi_g = (E_g dE_g, dE_g^2 / 6),
+// Om_g = A_gg^T phi_g + A_{g-1,up}^T phi_{g-1} + A_{g+1,lo}^T phi_{g+1}, so that
+// phi^T c A y = rho c sum_g Om_g . y_g.
+void omega_table(const pbs_ctx *c, std::vector<double> &om) {
+  const int G = c->ng;
+  om.assign(2 * (size_t)G, 0.0);
+  auto phi = [&](int g, int r) { return r == 0 ? c->e_c[g] * c->de[g] : c->de[g] * c->de[g] / 6.0; };
+  for (int g = 0; g < G; g++) {
+    double b[12], gg[4], up[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    strag_blocks(c, g, b);
+    const double sm = c->s_face[g] / c->de[g], sp = c->s_face[g + 1] / c->de[g], sig = c->sig[g];
+    gg[0] = -sm - sig + 0.5 * b[4];
+    gg[1] = sm + 0.5 * b[5];
+    gg[2] = -3.0 * sp + 0.5 * b[6];
+    gg[3] = -sp - 2.0 * sm - sig + 0.5 * b[7];
+    if (g > 0) {  // row g-1's block on psi_g
+      double bm[12];
+      strag_blocks(c, g - 1, bm);
+      const double spm = c->s_face[g] / c->de[g - 1];
+      up[0] = spm + 0.5 * bm[8];
+      up[1] = -spm + 0.5 * bm[9];
+      up[2] = 3.0 * spm + 0.5 * bm[10];
+      up[3] = -3.0 * spm + 0.5 * bm[11];
+    }
+    if (g + 1 < G) {  // row g+1's block on psi_g
+      double bp[12];
+      strag_blocks(c, g + 1, bp);
+      for (int i = 0; i < 4; i++) lo[i] = 0.5 * bp[i];
+    }
+    for (int q = 0; q < 2; q++) {
+      double w = 0.0;
+      for (int r = 0; r < 2; r++) {
+        w += gg[2 * r + q] * phi(g, r);
+        if (g > 0) w += up[2 * r + q] * phi(g - 1, r);
+        if (g + 1 < G) w += lo[2 * r + q] * phi(g + 1, r);
+      }
+      om[2 * g + q] = w;
+    }
+  }
+}
+
 // Exponential energy transfer P^1(g' -> g) = lambda e^{-lambda (E_g' - E_g)},
 // normalised per emitting group g', and the source weights of the fused
 // recursion (q1 = lambda sigma_g' dE_g' / Z_g', decay = e^{-lambda (E_g+1 - E_g)}),
@@ -479,9 +523,16 @@ pbs_status upload_tables(pbs_ctx *c) {
     real *o = reinterpret_cast<real *>(&sc[g]);
     for (int i = 0; i < 12; i++) o[i] = (real)b[i];
   }
-  if (!sc.empty())
+  std::vector<real> om_r;
+  if (!sc.empty()) {
     PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_strag), sc.data(), sizeof(StragCoef<real>) * G,
                                 cudaMemcpyHostToDevice, c->stream));
+    std::vector<double> om;
+    omega_table(c, om);
+    om_r.assign(om.begin(), om.end());
+    PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_omega), om_r.data(), sizeof(real) * om_r.size(),
+                                cudaMemcpyHostToDevice, c->stream));
+  }
   std::vector<real> ts(G);
   for (int g = 0; g < G; g++) ts[g] = (real)c->ts[g];
   PBS_CUDA(c, cudaMemcpyAsync(at<void>(c, c->off_coef), coef.data(), sizeof(GroupCoef<real>) * G,
@@ -552,8 +603,16 @@ void beam_factors(const pbs_ctx *c, const pbs_beam &b, std::vector<double> &out)
 // (slab_a, then slab_b) fused in one pass per component.  Fluence after the
 // first substep goes to plane flu_plane (if >= 0).
 template <typename real, typename st>
+pbs_status energy_cn_run(pbs_ctx *c, double h, int slab, int flu_plane, int b0, int b1);
+
+template <typename real, typename st>
 pbs_status energy_run(pbs_ctx *c, double h, int slab_a, int slab_b, int flu_plane, int b0, int b1) {
   if (b1 <= b0) return PBS_OK;
+  if (c->strag && c->opts.straggling_integrator == 1) {  // no fused pair: two substeps in turn
+    pbs_status r = energy_cn_run<real, st>(c, h, slab_a, flu_plane, b0, b1);
+    if (r == PBS_OK && slab_b >= 0) r = energy_cn_run<real, st>(c, h, slab_b, -1, b0, b1);
+    return r;
+  }
   LaunchCtx lc = lctx(c);
   const Dims d = dims_for(c, b1 - b0);
   const size_t nyz = (size_t)c->ny * c->nz;
@@ -589,6 +648,49 @@ pbs_status energy_run(pbs_ctx *c, double h, int slab_a, int slab_b, int flu_plan
                                     sbuf + half * half_stride, c->du * c->dv, b1 - b0);
         if (e != cudaSuccess) return cuda_fail(c, e, "source kernel");
       }
+    }
+  }
+  return PBS_OK;
+}
+
+// One E substep with straggling inside the Crank-Nicolson step (block
+// elimination, k_energy_cn.cu): the eliminated blocks of the slab, then per
+// component the two passes (and the R recursion), then the source of the
+// next component as in energy_run.
+template <typename real, typename st>
+pbs_status energy_cn_run(pbs_ctx *c, double h, int slab, int flu_plane, int b0, int b1) {
+  LaunchCtx lc = lctx(c);
+  const Dims d = dims_for(c, b1 - b0);
+  const size_t nyz = (size_t)c->ny * c->nz;
+  const size_t nsrc = (size_t)c->ng * c->na * nyz;
+  const BeamStrides bs{(long long)(c->K + 1) * c->d.comp_elems, (long long)nsrc, (long long)c->nx * (long long)nyz,
+                       (long long)(c->nx + 1) * (long long)nyz};
+  real *psi = at<real>(c, c->off_psi) + (size_t)b0 * bs.psi;
+  const real *rho = at<real>(c, c->off_rho) + (size_t)slab * nyz;
+  double *dose = at<double>(c, c->off_dose) + (size_t)b0 * bs.dose + (size_t)slab * nyz;
+  double *flu = flu_plane >= 0 ? at<double>(c, c->off_flu) + (size_t)b0 * bs.flu + (size_t)flu_plane * nyz : nullptr;
+  st *rbuf = at<st>(c, c->off_r) + (size_t)b0 * nsrc, *sbuf = at<st>(c, c->off_s) + (size_t)b0 * nsrc;
+  const auto *coef = at<GroupCoef<real>>(c, c->off_coef);
+  const auto *strag = at<StragCoef<real>>(c, c->off_strag);
+  real *dinv = at<real>(c, c->off_dinv);
+  cudaError_t e;
+  {
+    ProfScope ps(c, PBS_KERNEL_ENERGY);
+    e = launch_cn_factor<real>(lc, d, rho, coef, strag, (real)(0.5 * h), dinv);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy factor kernel");
+  for (int k = 0; k <= c->K; k++) {
+    EnergyHalf<real, st> hs{rho, (real)(0.5 * h), k >= 1 ? sbuf : nullptr, k < c->K ? rbuf : nullptr, dose};
+    {
+      ProfScope ps(c, PBS_KERNEL_ENERGY);
+      e = launch_energy_cn<real, st>(lc, d, psi + (size_t)k * c->d.comp_elems, hs, coef, strag,
+                                     at<real>(c, c->off_omega), dinv, flu, c->du * c->dv / c->dx, c->du * c->dv, bs);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "energy kernel");
+    if (k < c->K) {
+      ProfScope ps(c, PBS_KERNEL_SOURCE);
+      e = launch_source<real, st>(lc, d, at<st>(c, c->off_p2), rbuf, sbuf, c->du * c->dv, b1 - b0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "source kernel");
     }
   }
   return PBS_OK;
@@ -830,7 +932,7 @@ bool ready_to_march(pbs_ctx *c) { return c->ws && c->have_tables && c->have_mate
 // Explicit straggling is stable while a substep h keeps
 // h rho_max lambda_max(St) / 2 <= 2 (Gershgorin bound of lambda_max).
 pbs_status strag_guard(pbs_ctx *c, double h) {
-  if (!c->strag) return PBS_OK;
+  if (!c->strag || c->opts.straggling_integrator == 1) return PBS_OK;  // CN: no bound
   if (h * c->rho_max * c->strag_bound > 4.0)
     return fail(c, PBS_ERR_ARG,
                 "explicit straggling unstable for this step: h rho T / dE^2 too large (refine dx or coarsen the groups)");
@@ -1213,6 +1315,8 @@ pbs_status pbs_set_options(pbs_ctx *c, const pbs_options *o) {
   if (o->angular_integrator < 0 || o->angular_integrator > 1) return fail(c, PBS_ERR_ARG, "unknown angular integrator");
   if (o->transport_integrator < 0 || o->transport_integrator > 1)
     return fail(c, PBS_ERR_ARG, "unknown transport integrator");
+  if (o->straggling_integrator < 0 || o->straggling_integrator > 1)
+    return fail(c, PBS_ERR_ARG, "unknown straggling integrator");
   if (o->transport_integrator == 1 && c->nz > 256)
     return fail(c, PBS_ERR_UNSUPPORTED, "the Crank-Nicolson transport sweep takes rows of at most 256 columns");
   { pbs_status fr = c->ws ? PBS_DISPATCH(c, flush_impl, c) : PBS_OK; if (fr != PBS_OK) return fr; }

@@ -204,6 +204,18 @@ cudaError_t launch_energy(const LaunchCtx &lc, const Dims &d, real *psi_k, const
                           double dose_scale, double flu_scale, const BeamStrides &bs,
                           const StragCoef<real> *strag = nullptr);
 
+// E substep with straggling inside the CN step (k_energy_cn.cu): the
+// eliminated diagonal blocks D'^{-1} of a slab ([g][4][yz]), then the two
+// passes over one component (and the R recursion when h.r_out is set).
+template <typename real>
+cudaError_t launch_cn_factor(const LaunchCtx &lc, const Dims &d, const real *rho, const GroupCoef<real> *coef,
+                             const StragCoef<real> *strag, real c, real *dinv);
+template <typename real, typename st>
+cudaError_t launch_energy_cn(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &h,
+                             const GroupCoef<real> *coef, const StragCoef<real> *strag, const real *omega,
+                             const real *dinv, double *flu_yz, double dose_scale, double flu_scale,
+                             const BeamStrides &bs);
+
 // The same with the explicit straggling term (strag != NULL), one lane per thread.
 template <typename real, typename st>
 cudaError_t launch_energy_strag(const LaunchCtx &lc, const Dims &d, real *psi_k, const EnergyHalf<real, st> &ha,

@@ -79,6 +79,8 @@ def main(argv=None):
     p.add_argument("--energy-form", type=int, choices=[0, 1], help="FP32 energy kernel form (default: tuned)")
     p.add_argument("--transport", choices=["heun", "cn"], default="heun",
                    help="transport integrator: explicit trapezoid (default) or CN with the slope lagged")
+    p.add_argument("--straggling-integrator", choices=["explicit", "cn"], default="explicit",
+                   help="straggling inside the CN energy step explicitly (default) or in the CN step")
     p.add_argument("--spots", type=int, default=0, help="run the first N spots of the 256-spot batch")
     p.add_argument("--max-gb", type=float, default=48.0, help="device workspace per spot bucket (GiB)")
     p.add_argument("--no-graph", action="store_true")
@@ -109,12 +111,14 @@ def main(argv=None):
     import torch
     torch.cuda.set_device(0)
     out, dose, flu = march(binding, w, steps, prec, autotune=a.autotune, profile=not a.no_profile,
-                           energy_form=a.energy_form, transport=a.transport)
+                           energy_form=a.energy_form, transport=a.transport, strag_int=a.straggling_integrator)
     out.update({"workload": w.name, "ny": w.ny, "nz": w.nz, "ng": w.ng, "n_scatter": w.n_scatter,
                 "medium": w.medium, "physics_model": w.physics.get("model", 0),
-                "straggling": w.physics.get("t_scale", 0.0), "transport": a.transport})
+                "straggling": w.physics.get("t_scale", 0.0), "transport": a.transport,
+                "straggling_integrator": a.straggling_integrator})
     if a.vs_fp64 and prec != "fp64":
-        ref, dose64, flu64 = march(binding, w, steps, "fp64", autotune=False, profile=False, transport=a.transport)
+        ref, dose64, flu64 = march(binding, w, steps, "fp64", autotune=False, profile=False, transport=a.transport,
+                                   strag_int=a.straggling_integrator)
         out["fp64"] = {"cell_updates_per_s": ref["cell_updates_per_s"],
                        "speedup": out["cell_updates_per_s"] / ref["cell_updates_per_s"],
                        "dose_err_vs_fp64": float(np.abs(dose - dose64).max() / np.abs(dose64).max()),
@@ -122,15 +126,16 @@ def main(argv=None):
     print(json.dumps(out))
 
 
-def march(binding, w, steps, prec, autotune=False, profile=True, energy_form=None, transport="heun"):
+def march(binding, w, steps, prec, autotune=False, profile=True, energy_form=None, transport="heun",
+          strag_int="explicit"):
     """The whole march of workload w (steps depth steps) in the given
     precision: device time by CUDA events around step + flush on the
     context's stream; per-kernel times when profiling."""
     import torch
     s = binding.Solver(w.grid(), nx=steps, dx=w.dx, n_scatter=w.n_scatter, precision=prec, physics=w.physics)
     try:
-        if transport != "heun":
-            s.set_options(transport_integrator=transport)
+        if transport != "heun" or strag_int != "explicit":
+            s.set_options(transport_integrator=transport, straggling_integrator=strag_int)
         s.set_material(w.density(steps))
         s.launch_beam(**w.beam)
         if autotune:

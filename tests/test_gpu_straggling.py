@@ -173,3 +173,79 @@ def test_unstable_explicit_straggling_is_refused():
         s.substep_energy(1.0, 0)
     s.substep_energy(0.002, 0)
     s.close()
+
+
+# ---- straggling inside the Crank-Nicolson step (block elimination), pbs_options.straggling_integrator = 1
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 3e-6)])
+@pytest.mark.parametrize("ng,ny,nz", [(37, 6, 10), (64, 3, 33)])
+def test_energy_substep_full_cn(orc, precision, tol, ng, ny, nz):
+    phys = dict(t_scale=20.0)
+    grid = _grid(ny, nz, 4, 4, ng)
+    rho = np.random.default_rng(ng + 7).uniform(0.4, 1.9, size=(1, ny, nz))
+    s = binding.Solver(grid, nx=1, dx=0.05, precision=precision, physics=phys)
+    s.set_options(straggling_integrator="cn")
+    s.set_material(rho)
+    psi = np.abs(random_state((ng, 2, 4, 4, ny, nz), seed=ng + 3))
+    s.write_psi(0, psi)
+    s.substep_energy(0.025, 0, 0)
+    o = orc.Oracle(grid, phys)
+    o.set_straggling_cn(True)
+    ref, edep, _ = o.energy_substep(0.025, rho[0], psi)
+    assert _relerr(s.read_psi(0), ref) < tol
+    assert _relerr(s.read_dose(1)[0], edep / (rho[0] * 0.05 * 0.1 * 0.1)) < (1e-11 if precision == "fp64" else 2e-5)
+    # fluence after the substep: du dv sum_g dE psi^1 summed over the angles
+    de = np.diff(grid["e_faces"])
+    du = 2 * grid["u_max"] / 5
+    flu_ref = du * du * np.einsum("g,gjipq->pq", de, ref[:, 0])
+    assert _relerr(s.read_fluence(1)[0], flu_ref) < (1e-12 if precision == "fp64" else 3e-6)
+    # and it differs from the explicit form
+    expl = orc.Oracle(grid, phys).energy_substep(0.025, rho[0], psi)[0]
+    assert _relerr(expl, ref) > 1e3 * tol
+    s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5), ("mixed", 1e-3)])
+def test_march_full_cn(orc, precision, tol):
+    """Two beams with their own depths, K = 1, Appendix-A physics: each beam
+    against the oracle's full-CN march of that beam alone."""
+    phys = dict(model=1, t_scale=1.0)
+    grid = _grid(12, 10, 8, 8, 48, e_max=60.0) if precision != "mixed" else _grid(12, 10, 16, 16, 48, e_max=60.0)
+    nx, dx = 7, 0.05
+    rho = np.random.default_rng(23).uniform(0.5, 1.6, size=(nx, 12, 10))
+    beams = [dict(e0=42.0, sigma_e=1.0, sigma_y=0.25, sigma_z=0.2, y0=0.05), dict(e0=36.0, sigma_e=0.8, sigma_y=0.3)]
+    steps = [7, 5]
+    s = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision=precision, physics=phys, n_beams=2)
+    s.set_options(straggling_integrator="cn")
+    s.set_material(rho)
+    s.set_beam_steps(steps)
+    s.launch_beams(beams)
+    s.step(3)
+    s.step(nx - 3)
+    dose, flu = s.read_dose(), s.read_fluence()
+    o = orc.Oracle(grid, phys)
+    o.set_straggling_cn(True)
+    for b, beam in enumerate(beams):
+        ref = o.march(rho[:steps[b]], steps[b], dx, beam=beam, n_scatter=1)
+        assert _relerr(dose[b, :steps[b]], ref["dose"]) < tol, b
+        assert _relerr(flu[b, :steps[b] + 1], ref["fluence"]) < tol, b
+        if precision == "fp64":
+            assert _relerr(s.read_psi(2 * b + 1), ref["psi"][1]) < 1e-10, b
+    s.close()
+
+
+def test_full_cn_has_no_stability_bound(orc):
+    """The configuration the explicit form refuses runs in CN and matches the
+    oracle's CN substep."""
+    grid = _grid(4, 4, 4, 4, 200, e_max=20.0)
+    phys = dict(t_scale=1.0)
+    s = binding.Solver(grid, nx=2, dx=2.0, precision="fp64", physics=phys)
+    s.set_material(np.full((2, 4, 4), 1.9))
+    s.set_options(straggling_integrator="cn")
+    psi = np.abs(random_state((200, 2, 4, 4, 4, 4), seed=4))
+    s.write_psi(0, psi)
+    s.substep_energy(1.0, 0)
+    o = orc.Oracle(grid, phys)
+    o.set_straggling_cn(True)
+    assert _relerr(s.read_psi(0), o.energy_substep(1.0, np.full((4, 4), 1.9), psi)[0]) < 1e-11
+    s.close()
