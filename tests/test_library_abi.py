@@ -57,3 +57,30 @@ def test_product_package_does_not_import_the_oracle():
                 with open(os.path.join(dirpath, f)) as fh:
                     src = fh.read()
                 assert "import oracle" not in src and "pbs_oracle" not in src, f
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Size and field offsets of every struct the binding marshals equal the
+    C compiler's for include/pbs.h (a field added on one side only would
+    shift everything after it)."""
+    import subprocess
+
+    from paper_2504_00340_gb300 import binding as B
+    structs = {"pbs_grid": B.PbsGrid, "pbs_physics": B.PbsPhysics, "pbs_beam": B.PbsBeam,
+               "pbs_options": B.PbsOptions, "pbs_tuning": B.PbsTuning}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pbs.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
