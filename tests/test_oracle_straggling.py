@@ -248,3 +248,29 @@ def test_straggling_reproduces_the_paper_distal_falloff(oracle_mod, e0):
     assert abs(w / w_ref - 1.0) < 0.06, (w, w_ref)
     none = _landmarks(oracle_mod, float(e0), 0.0)
     assert abs((none[3] - none[2]) / w_ref - 1.0) > abs(w / w_ref - 1.0)
+
+
+@pytest.mark.parametrize("full", [False, True])
+def test_march_energy_balance_with_straggling(oracle_mod, full):
+    """A K = 1 march with straggling (Appendix-A physics), transport on and
+    angular diffusion off so that nothing leaves through the walls: the
+    energy content lost by the state equals the tallied deposit (difference
+    form) and the operator-form tally, for both straggling integrators."""
+    G, n, dx = 60, 20, 0.05
+    grid = dict(ny=16, nz=16, nu=4, nv=4, dy=0.1, dz=0.1, u_max=0.1, v_max=0.1,
+                e_faces=np.linspace(0.0, 60.0, G + 1))
+    o = oracle_mod.Oracle(grid, dict(model=1, t_scale=5.0))
+    o.set_straggling_cn(full)
+    t = o.tables()
+    beam = dict(e0=45.0, sigma_e=1.5, sigma_y=0.15, sigma_z=0.15)
+    r = o.march(np.ones((n, 16, 16)), n, dx, beam=beam, n_scatter=1, do_angular=False)
+    psi0 = o.init_beam(beam)
+
+    def content(p):  # p: [..., g, c, j, i, y, z]
+        e = (t["de"] * t["e_c"])[:, None, None, None, None] * p[..., :, 0, :, :, :, :] + \
+            (t["de"] ** 2 / 6)[:, None, None, None, None] * p[..., :, 1, :, :, :, :]
+        return e.sum() * o.du * o.dv * o.dy * o.dz
+
+    dep = r["dose"].sum() * dx * o.dy * o.dz  # rho = 1
+    assert content(psi0) - content(r["psi"]) == pytest.approx(dep, rel=1e-10)
+    assert r["dose"] == pytest.approx(r["dose_w"], rel=1e-9, abs=1e-12 * np.abs(r["dose"]).max())
