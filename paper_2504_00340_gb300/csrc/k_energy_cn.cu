@@ -26,8 +26,6 @@
 // rho q1 psi^1, pass B adds rho q1 x^1, and k_cn_r runs the recursion.
 #include "energy_scan.cuh"
 
-#include <type_traits>
-
 namespace pbs {
 
 namespace {
