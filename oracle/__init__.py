@@ -90,6 +90,7 @@ def _load():
             lib.orc_energy_blocks.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D, _D]
             lib.orc_straggle_blocks.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, _D, _D, _D]
             lib.orc_straggle_apply.argtypes = [ctypes.c_void_p, ctypes.c_double, _D, _D]
+            lib.orc_set_sigma.argtypes = [ctypes.c_void_p, _D]
             lib.orc_set_straggling_table.argtypes = [ctypes.c_void_p, _D]
             lib.orc_set_straggling_cn.argtypes = [ctypes.c_void_p, ctypes.c_int]
             lib.orc_get_straggling.argtypes = [ctypes.c_void_p, _D, _D]
@@ -239,6 +240,14 @@ class Oracle:
         out = np.zeros_like(x)
         self.lib.orc_straggle_apply(self.ctx, float(rho), _ptr(x), _ptr(out))
         return out
+
+    def set_sigma(self, sig):
+        """Removal cross section of every group (ng values, cm^2/g) in place
+        of the constant sigma_ct: group g is removed at sig[g] and the source
+        it emits into the next component carries sig[g] (Section 4, the
+        emitting group's rate)."""
+        s = _f64(sig).reshape(self.ng)
+        self.lib.orc_set_sigma(self.ctx, _ptr(s))
 
     def set_straggling_table(self, t_face=None):
         """Straggling coefficient at the faces (ng+1, MeV^2 cm^2/g); None: off.

@@ -315,6 +315,18 @@ void orc_destroy(orc_ctx *c) {
   free(c);
 }
 
+/* Catastrophic removal cross section of every group, sig[g] (mass, cm^2/g),
+ * in place of the constant of the physics parameters.  Section 4 writes the
+ * removal term of group g with sigma_c,t,g, and sigma_c,s,g = sigma_c,t P^1 P^2
+ * with sigma_c,t printed on the destination group.  Reading: a proton leaves
+ * group g' at the rate of g' itself, so the removal term of group g uses
+ * sig[g] and the source that group g receives from g' >= g uses sig[g'] (the
+ * emitting group); only this form puts back into the next component exactly
+ * what the removal took out (orc_source, orc_energy_blocks). */
+void orc_set_sigma(orc_ctx *c, const double *sig) {
+  for (int g = 0; g < c->ng; g++) c->sig[g] = sig[g];
+}
+
 void orc_get_tables(const orc_ctx *c, double *s_face, double *ts, double *sig, double *p1, double *p2,
                     double *u, double *v) {
   int G = c->ng, na = c->na;

@@ -53,6 +53,7 @@ double orc_bethe_element(const orc_phys *ph, double z, double a, double e);
 double orc_sigma_tr_element(const orc_phys *ph, double z, double a, double e);
 double orc_scat_power_water(const orc_phys *ph, double e);
 double orc_williams_water(const orc_phys *ph, double e);
+void orc_set_sigma(orc_ctx *c, const double *sig);
 void orc_set_straggling_table(orc_ctx *c, const double *t_face);
 void orc_set_straggling_cn(orc_ctx *c, int full);
 void orc_get_straggling(const orc_ctx *c, double *t_face, double *s_base);
