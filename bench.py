@@ -107,13 +107,18 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline helpers
 
-def _kernel_hash(name: str) -> str:
-    with open(os.path.join(ROOT, "paper_2504_00340_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def _kernel_hash(names) -> str:
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(ROOT, "paper_2504_00340_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
-KERNEL_FILES = {"energy": "k_energy_f2.cu", "transport": "k_transport_rows.cu", "angular": "k_angular.cu",
-                "source": "k_source_tc.cu"}
+# the source files of each kernel (its .cu and the device code it includes)
+KERNEL_FILES = {"energy": ("k_energy_f2.cu", "energy_f2.cuh"),
+                "transport": ("k_transport_rows.cu", "transport_rows.cuh"),
+                "angular": ("k_angular.cu", "angular_f2.cuh"), "source": ("k_source_tc.cu",)}
 
 
 def _traffic_from_profiles(kind: str, workload: str):
@@ -286,33 +291,54 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def fp64_comparison(binding, w, stream, n=4):
+def _march_dose(binding, w, grid, nx, prec, stream, timed=False):
+    """March nx depth steps of workload w on grid in one precision; returns
+    (cell-updates/s or None, dose [s][y][z], fluence [s][y][z])."""
     import numpy as np
     import torch
-    rho = np.ones((n, w.ny, w.nz))
-    out = {}
-    doses = {}
-    for prec in ("fp64", "fp32"):
-        s = binding.Solver(w.grid(), nx=n, dx=w.dx, n_scatter=w.n_scatter, precision=prec, stream=stream)
-        s.set_material(rho)
-        s.launch_beam(**w.beam)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.step(n)
-        s.flush()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        out[prec] = w.cells_per_step * (w.n_scatter + 1) * n / (e0.elapsed_time(e1) / 1e3)
-        doses[prec] = s.read_dose(n)
-        s.close()
-        del s
-        torch.cuda.empty_cache()
-    d64, d32 = doses["fp64"], doses["fp32"]
-    return {"value": out["fp64"], "unit": UNIT, "steps": n,
-            "fp32_speedup": out["fp32"] / out["fp64"],
-            "dose_err_fp32_vs_fp64": float(np.abs(d32 - d64).max() / np.abs(d64).max()),
-            "note": "same workload, first steps from the entrance"}
+    s = binding.Solver(grid, nx=nx, dx=w.dx, n_scatter=w.n_scatter, precision=prec, stream=stream)
+    s.set_material(np.ones((nx, grid["ny"], grid["nz"])))
+    s.launch_beam(**w.beam)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(nx)
+    s.flush()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cells = grid["ny"] * grid["nz"] * (len(grid["e_faces"]) - 1) * grid["nu"] * grid["nv"] * (w.n_scatter + 1)
+    rate = cells * nx / (e0.elapsed_time(e1) / 1e3) if timed else None
+    dose, flu = s.read_dose(nx), s.read_fluence(nx + 1)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return rate, dose, flu
+
+
+def fp64_comparison(binding, w, stream, n=4, lateral=32):
+    """The FP64 GPU form of the workload: its speed on the full grid over the
+    first n steps, and the FP32 dose and fluence error against it over the
+    whole depth (all of the workload's steps, through the Bragg peak) on a
+    reduced lateral grid with the workload's own energy and angle grids."""
+    import numpy as np
+    grid = w.grid()
+    rate64, d64, _ = _march_dose(binding, w, grid, n, "fp64", stream, timed=True)
+    rate32, d32, _ = _march_dose(binding, w, grid, n, "fp32", stream, timed=True)
+    small = dict(grid, ny=lateral, nz=lateral)
+    _, fd64, ff64 = _march_dose(binding, w, small, w.n_steps, "fp64", stream)
+    _, fd32, ff32 = _march_dose(binding, w, small, w.n_steps, "fp32", stream)
+    idd = fd64.sum(axis=(1, 2))
+    return {"value": rate64, "unit": UNIT, "steps": n,
+            "fp32_speedup": rate32 / rate64,
+            "dose_err_fp32_vs_fp64_entrance": float(np.abs(d32 - d64).max() / np.abs(d64).max()),
+            "full_depth": {
+                "lateral": f"{lateral}x{lateral} @ {w.dy * 10:g} mm", "steps": w.n_steps,
+                "depth_cm": w.n_steps * w.dx,
+                "bragg_peak_cm": float((np.argmax(idd) + 0.5) * w.dx),
+                "dose_err_fp32_vs_fp64": float(np.abs(fd32 - fd64).max() / np.abs(fd64).max()),
+                "fluence_err_fp32_vs_fp64": float(np.abs(ff32 - ff64).max() / np.abs(ff64).max())},
+            "note": (f"speed: the full workload grid, first {n} steps; error: every step of the workload's depth on a "
+                     f"{lateral}x{lateral} lateral grid with its 256 groups and 16x16 angles (max-normalised)")}
 
 
 # ---------------------------------------------------------------- CPU oracle

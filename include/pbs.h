@@ -221,6 +221,63 @@ pbs_status pbs_step(pbs_ctx *ctx, int n_steps);
 /* Apply a deferred closing E(h/2), if any.  Asynchronous. */
 pbs_status pbs_flush(pbs_ctx *ctx);
 
+/* One depth step in four stages (Section 3.3's Strang sequence), for callers
+ * that act between the substeps, e.g. to exchange halo rows between lateral
+ * parts held by different processes:
+ *   stage 0  E(h/2) opening the step (fused with a deferred closing half)
+ *   stage 1  T(h/2)      stage 2  A(h)      stage 3  T(h/2)
+ * after which the step is counted and its closing E(h/2) deferred, exactly
+ * as pbs_step does.  Stages must come in the order 0, 1, 2, 3 (PBS_ERR_STATE
+ * otherwise); pbs_step, pbs_run and pbs_domain_step refuse to start while a
+ * staged step is incomplete.  Stage 0 returns PBS_ERR_ARG if the step would
+ * pass the material's last slab.  Asynchronous. */
+pbs_status pbs_step_stage(pbs_ctx *ctx, int stage);
+
+/* Lateral domain decomposition of one beam (Remark 2: the energy and
+ * angular subsystems are independent at every lateral point, only the
+ * transport couples neighbouring cells).  Declares this context's rows
+ * 0..ny-1 to be rows y_offset..y_offset+ny-1 of a grid of ny_global rows
+ * (the same z, energy and angle grids and cell sizes), of which the first
+ * halo_lo and the last halo_hi are halo rows: copies of the neighbouring
+ * parts' own rows, refreshed before every transport substep.  A part at the
+ * grid's lower edge (y_offset = 0) has halo_lo = 0, at the upper edge
+ * halo_hi = 0, and every interior side has a halo (PBS_ERR_ARG otherwise).
+ * The beam projection then evaluates the part's rows of the whole grid with
+ * the whole grid's normalisation, so that the parts hold exactly the values
+ * of the undivided grid.  Call it before pbs_launch_beam (PBS_ERR_STATE
+ * after); contexts with n_beams > 1 return PBS_ERR_UNSUPPORTED.  Each part's
+ * material is its own rows of the density field. */
+pbs_status pbs_set_lateral_part(pbs_ctx *ctx, int y_offset, int ny_global, int halo_lo, int halo_hi);
+
+/* March n_steps depth steps of one beam split into n_parts lateral parts
+ * (pbs_set_lateral_part), ordered by y, in lock-step: stages 0-3 of each step
+ * on every part, and before stages 1 and 3 the halo rows of every interior
+ * interface copied from the neighbour's own rows into each part's own
+ * workspace (cudaMemcpy2DAsync, every psi plane of every component; parts on
+ * different streams or devices are ordered by event waits).  Interior halos
+ * need at least 4 rows, the reach of the two stages of the explicit
+ * trapezoid; the Crank-Nicolson transport (pbs_options) couples whole rows
+ * and returns PBS_ERR_UNSUPPORTED.  The parts must share precision, z,
+ * energy and angle grids, cell sizes, options, tables and depth, and their
+ * own rows must tile the grid (PBS_ERR_ARG / PBS_ERR_STATE otherwise).  A
+ * part's own rows of psi then equal those of the undivided march bit for bit
+ * when both run the same kernel forms (pbs_tuning; FP64 has one form): the
+ * arithmetic of each cell is the same.  Its halo rows hold nothing
+ * meaningful between steps, and the dose and fluence of its own rows equal
+ * the undivided ones up to the order of the FP64 tally's atomic sums.  The closing E(h/2) of the last step is deferred on every part as
+ * in pbs_step.  Asynchronous on the parts' streams. */
+pbs_status pbs_domain_step(pbs_ctx *const *parts, int n_parts, int n_steps);
+
+/* Copy rows first_row..first_row+n_rows-1 of every psi plane of every
+ * component (the [k][g][c][j][i] planes of ny x nz cells) to (to_buffer = 1)
+ * or from (to_buffer = 0) a caller-owned device buffer laid out
+ * [plane][row][q], planes * n_rows * nz values of the working precision.
+ * With pbs_step_stage this is a halo exchange between lateral parts held by
+ * different processes: pack the rows a neighbour needs, send them with the
+ * caller's own transport, unpack the received rows into the halo.
+ * Asynchronous on the context's stream. */
+pbs_status pbs_copy_rows(pbs_ctx *ctx, int first_row, int n_rows, int to_buffer, void *dev_buf);
+
 /* Depth range of each beam of a batch: beam b marches steps[b] depth steps
  * (capped by the material's n_slabs) and then only receives its closing
  * E(h/2); later launches skip it.  steps must be non-increasing in b (order
@@ -241,6 +298,58 @@ pbs_status pbs_set_beam_steps(pbs_ctx *ctx, const int *steps, int n);
  * first graph call records; call it once before capturing the caller's own
  * work around it. */
 pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
+
+/* Persistent batch of pencil beams (spots): the whole march of n_beams
+ * independent beams in one persistent kernel launch, each beam a context of
+ * its own (its own lateral grid, energy groups, tables, density, depth range
+ * (pbs_set_beam_steps / material extent) and workspace).  A device work queue
+ * hands out the tiles of every beam's passes (per depth step E(h/2) fused
+ * across steps, T(h/2), A(h), T(h/2); Section 3.3), round-robin over the
+ * beams; per-beam completion counters order a beam's passes, so beams of
+ * different depth and size fill the GPU together with no bucketing and no
+ * empty energy groups.  Every tile is the same device code as the matching
+ * block of the per-substep kernels, so each beam's psi equals its own
+ * pbs_run with the tuning {energy_angles 8, energy_form 1, angular_form 2}
+ * bit for bit (the dose up to the order of its atomic FP64 sums).
+ *   use_graph      nonzero: record the batch (every beam's restart from its
+ *                  projection, the queue reset, the launch) into a CUDA graph
+ *                  on first use and replay it; the graph is kept by beams[0]
+ *                  until the batch (contexts, depths, workspace, options)
+ *                  changes.  Record it before capturing around it.
+ *   wait_limit_ms  bound of every device wait of a tile for the beam's
+ *                  earlier passes (<= 0: 2000 ms).  A wait that runs out sets
+ *                  every beam's device status word and the launch stops at
+ *                  the next tile boundary with no copy in flight; the next
+ *                  synchronising call on any beam (e.g. pbs_read_dose)
+ *                  returns PBS_ERR_TIMEOUT, and the next pbs_run_batch
+ *                  starts afresh.
+ *   hold_beam      failure-detection test hook (-1 in normal use): beam
+ *                  hold_beam's second pass waits for one tile more than its
+ *                  first pass has, so its waits can only run out. */
+typedef struct {
+  int use_graph;
+  double wait_limit_ms;
+  int hold_beam;
+} pbs_batch_options;
+
+/* Bytes of the device workspace pbs_run_batch needs for these beams with
+ * their current depth ranges (descriptors, task list, queue counters). */
+pbs_status pbs_batch_workspace_size(pbs_ctx *const *beams, int n_beams, size_t *bytes);
+
+/* Restart every beam from its projection (as pbs_run does) and march all of
+ * them to their own depths in one persistent launch (see pbs_batch_options),
+ * on the beams' common stream.  dev_ws: caller-owned device memory of at
+ * least pbs_batch_workspace_size bytes, 256-byte aligned, kept alive while
+ * the batch runs; opts may be NULL (no graph, 2000 ms waits).  The beams
+ * must be FP32 or mixed-precision contexts with n_scatter = 0 and n_beams =
+ * 1, the default integrators and no straggling, ny*nz even, nz a multiple
+ * of 4, one angle grid of at most 8 x 8 for all, one device and one stream
+ * (PBS_ERR_UNSUPPORTED / PBS_ERR_ARG otherwise), each with a workspace,
+ * tables, material and a launched beam (PBS_ERR_STATE otherwise).
+ * Asynchronous; afterwards every beam's dose and fluence are final (read
+ * them per context). */
+pbs_status pbs_run_batch(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_t bytes,
+                         const pbs_batch_options *opts);
 
 /* Method options (each changes the computed result, unlike pbs_tuning):
  *   angular_integrator    time integration of each sine mode of the angular
@@ -319,15 +428,22 @@ pbs_status pbs_autotune(pbs_ctx *ctx, int reps);
 pbs_status pbs_set_tuning(pbs_ctx *ctx, const pbs_tuning *tuning);
 pbs_status pbs_get_tuning(const pbs_ctx *ctx, pbs_tuning *tuning);
 
-/* Checkpoint / resume of the march state: psi of every component of every
+/* Checkpoint / resume of the march state (the library's own addition; the
+ * paper marches once from the entrance): psi of every component of every
  * beam (working precision), dose, fluence, the beam projection factors, the
  * per-beam depth ranges, the depth counter and a deferred closing E(h/2)
- * (kept deferred, not applied).  The material and the tables are inputs,
- * not state: set them on the restoring context as before.  pbs_checkpoint_size
- * gives the bytes of the host buffer; save copies the state into it
- * (synchronises); load restores a checkpoint written by a context with the
- * same grid, precision, n_scatter and n_beams (PBS_ERR_ARG otherwise, or for
- * a buffer that is not a checkpoint).  Host buffers are the caller's. */
+ * (kept deferred, not applied).  The material, the tables and the method
+ * options are inputs, not state: set them on the restoring context before
+ * pbs_checkpoint_load, equal to those of the saving context (the checkpoint
+ * records the options and hashes of the FP64 tables and of the density
+ * field, and load compares them).  pbs_checkpoint_size gives the bytes of
+ * the host buffer; save copies the state into it (synchronises); load
+ * restores a checkpoint written by a context with the same grid, precision,
+ * n_scatter and n_beams.  load returns PBS_ERR_STATE before the tables and
+ * the material are set, and PBS_ERR_ARG for another grid, options, tables or
+ * density, or for a buffer that is not a consistent checkpoint (flags other
+ * than 0/1, a deferred half with no marched step, depths out of range); it
+ * rejects before touching the device.  Host buffers are the caller's. */
 pbs_status pbs_checkpoint_size(const pbs_ctx *ctx, size_t *bytes);
 pbs_status pbs_checkpoint_save(pbs_ctx *ctx, void *host, size_t bytes);
 pbs_status pbs_checkpoint_load(pbs_ctx *ctx, const void *host, size_t bytes);
@@ -368,10 +484,11 @@ pbs_status pbs_eval_source(pbs_ctx *ctx, int k_from, int slab, double *host_out,
 
 /* Allocation-free variant of pbs_eval_source, for callers that cannot
  * allocate device memory (no cudaMalloc and no caching allocator: e.g. code
- * embedded in a host framework that hands it pre-carved device buffers).  The
- * paper has no counterpart to this call; it evaluates the same catastrophic
- * source of Remark 1 as pbs_eval_source on an FP32 context, without a
- * context or workspace:
+ * embedded in a host framework that hands it pre-carved device buffers, or a
+ * process whose device memory belongs to another owner).  The paper has no
+ * counterpart to this call.  It evaluates the same catastrophic source as
+ * pbs_eval_source on an FP32 context (one removal cross section for every
+ * group), without a context or workspace:
  *   psi_k    device, FP32 component [g][c][j][i][p][q] (ng*2*nu*nv*ny*nz)
  *   rho_yz   device, FP32 density of the slab [p][q]
  *   p2       device, FP32 P^2 matrices [g][a][a'] (ng*na*na), e.g. the FP64
@@ -386,10 +503,11 @@ pbs_status pbs_eval_source(pbs_ctx *ctx, int k_from, int slab, double *host_out,
  * and ng must not exceed 2048: larger calls return PBS_ERR_UNSUPPORTED.  The
  * call allocates no device memory.  Its first call on a device looks up the
  * array's device address (once per device, with that device current): make
- * that first call before any stream capture.  All calls share the one
- * scratch array, whose contents are fully overwritten by each call; calls
- * that overlap on the GPU (different streams, or devices sharing nothing
- * else) race on it and must be serialised by the caller. */
+ * that first call before any stream capture.  Each device has its own copy
+ * of the array, so calls on different devices are independent; on one
+ * device every call shares the one array, whose contents each call fully
+ * overwrites, so calls that overlap on the same device (e.g. on different
+ * streams) race on it and must be serialised by the caller. */
 pbs_status pbs_eval_source_noalloc(const float *psi_k, const float *rho_yz, const float *p2, const double *e_faces,
                                    int ng, int nu, int nv, int ny, int nz, double u_max, double v_max,
                                    double sigma_ct, double lambda_p1, float *src_out, void *stream);

@@ -59,6 +59,10 @@ class PbsOptions(ctypes.Structure):
                 ("straggling_integrator", ctypes.c_int)]
 
 
+class PbsBatchOptions(ctypes.Structure):
+    _fields_ = [("use_graph", ctypes.c_int), ("wait_limit_ms", ctypes.c_double), ("hold_beam", ctypes.c_int)]
+
+
 class PbsError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -87,6 +91,13 @@ SIGNATURES = [
     ("pbs_get_tuning", ctypes.c_int, [_VP, ctypes.POINTER(PbsTuning)]),
     ("pbs_step", ctypes.c_int, [_VP, ctypes.c_int]),
     ("pbs_flush", ctypes.c_int, [_VP]),
+    ("pbs_step_stage", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("pbs_set_lateral_part", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("pbs_domain_step", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int]),
+    ("pbs_copy_rows", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP]),
+    ("pbs_batch_workspace_size", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    ("pbs_run_batch", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_size_t,
+                                     ctypes.POINTER(PbsBatchOptions)]),
     ("pbs_get_depth", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     ("pbs_checkpoint_size", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
     ("pbs_checkpoint_save", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
@@ -245,6 +256,39 @@ def pbs_flush(ctx) -> None:
     _check(ctx, load_library().pbs_flush(_VP(ctx)))
 
 
+def pbs_step_stage(ctx, stage: int) -> None:
+    _check(ctx, load_library().pbs_step_stage(_VP(ctx), int(stage)))
+
+
+def pbs_set_lateral_part(ctx, y_offset: int, ny_global: int, halo_lo: int, halo_hi: int) -> None:
+    _check(ctx, load_library().pbs_set_lateral_part(_VP(ctx), int(y_offset), int(ny_global), int(halo_lo),
+                                                    int(halo_hi)))
+
+
+def pbs_domain_step(ctxs, n_steps: int) -> None:
+    arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
+    _check(ctxs[0], load_library().pbs_domain_step(arr, len(ctxs), int(n_steps)))
+
+
+def pbs_copy_rows(ctx, first_row: int, n_rows: int, to_buffer: bool, dev_ptr: int) -> None:
+    _check(ctx, load_library().pbs_copy_rows(_VP(ctx), int(first_row), int(n_rows), int(bool(to_buffer)),
+                                             _VP(dev_ptr)))
+
+
+def pbs_batch_workspace_size(ctxs) -> int:
+    arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
+    n = ctypes.c_size_t()
+    _check(ctxs[0], load_library().pbs_batch_workspace_size(arr, len(ctxs), ctypes.byref(n)))
+    return n.value
+
+
+def pbs_run_batch(ctxs, dev_ptr: int, nbytes: int, use_graph: bool = False, wait_limit_ms: float = 0.0,
+                  hold_beam: int = -1) -> None:
+    arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
+    opts = PbsBatchOptions(int(bool(use_graph)), float(wait_limit_ms), int(hold_beam))
+    _check(ctxs[0], load_library().pbs_run_batch(arr, len(ctxs), _VP(dev_ptr), nbytes, ctypes.byref(opts)))
+
+
 def pbs_checkpoint_size(ctx) -> int:
     n = ctypes.c_size_t()
     _check(ctx, load_library().pbs_checkpoint_size(_VP(ctx), ctypes.byref(n)))
@@ -348,6 +392,20 @@ _BEAM_DEFAULTS = dict(e0=100.0, sigma_e=1.0, y0=0.0, z0=0.0, sigma_y=0.3, sigma_
                       sigma_u=1e-6, sigma_v=1e-6)
 
 
+def run_batch(solvers, use_graph: bool = False, wait_limit_ms: float = 0.0, hold_beam: int = -1, workspace=None):
+    """March every Solver of the list (one beam each, see pbs_run_batch) in
+    one persistent launch on their common stream.  The batch workspace is a
+    torch tensor allocated here unless given (keep it alive while the batch
+    runs: it is returned)."""
+    import torch
+    ctxs = [s.ctx for s in solvers]
+    nbytes = pbs_batch_workspace_size(ctxs)
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+    pbs_run_batch(ctxs, workspace.data_ptr(), workspace.numel(), use_graph, wait_limit_ms, hold_beam)
+    return workspace
+
+
 class Solver:
     """One context on the current CUDA device, holding n_beams beams on one grid.
 
@@ -444,6 +502,26 @@ class Solver:
     def launch_beams(self, beams):
         """One beam dict per beam of the context."""
         pbs_launch_beams(self.ctx, [self._beam(b) for b in beams])
+
+    def set_lateral_part(self, y_offset: int, ny_global: int, halo_lo: int, halo_hi: int):
+        """Declare this context a lateral part of a beam split along y (see
+        pbs_set_lateral_part); before launch_beam."""
+        pbs_set_lateral_part(self.ctx, y_offset, ny_global, halo_lo, halo_hi)
+
+    def step_stage(self, stage: int):
+        """Stage 0..3 of the next depth step (see pbs_step_stage)."""
+        pbs_step_stage(self.ctx, stage)
+
+    def copy_rows(self, first_row: int, n_rows: int, to_buffer: bool, buf):
+        """Rows of every psi plane to / from a device tensor buf laid out
+        [plane][row][z] (see pbs_copy_rows)."""
+        pbs_copy_rows(self.ctx, first_row, n_rows, to_buffer, buf.data_ptr())
+
+    @property
+    def n_planes(self) -> int:
+        """psi planes (ny x nz cells) of all components: the rows of
+        copy_rows' buffer per copied row."""
+        return self.n_beams * (self.K + 1) * self.ng * 2 * self.na
 
     def set_beam_steps(self, steps):
         pbs_set_beam_steps(self.ctx, steps)

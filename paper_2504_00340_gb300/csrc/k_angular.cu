@@ -25,6 +25,7 @@
 // two tiles load.  No per-element global address arithmetic remains; the
 // direct form (k_angular) serves grids whose row pitch breaks the TMA rules.
 #include "pbs_internal.cuh"
+#include "angular_f2.cuh"
 
 #include <cmath>
 #include <mutex>
@@ -32,6 +33,8 @@
 namespace pbs {
 
 namespace {
+
+using namespace ang;
 
 // lateral points per CTA: one 128-byte row of the tile per angle
 template <typename real>
@@ -41,13 +44,10 @@ __host__ __device__ constexpr int tile_w() { return sizeof(real) == 8 ? 16 : 32;
 // even size N <= 16, row-major [m][i], packed one after another (size N at
 // offset dst_off(N)) in the constant bank (they depend on N only).  Indexed
 // with compile-time offsets, so the multiply-adds read them as constant
-// operands.  c_dst_f2 holds each FP32 entry twice, as the pair operand of the
-// packed FP32x2 multiply-adds.
-__host__ __device__ constexpr int dst_off(int n) { return n <= 2 ? 0 : dst_off(n - 2) + (n - 2) * (n - 2); }
-constexpr int kDstEntries = dst_off(kMaxAngle + 2);
+// operands.  The pair table of the packed FP32x2 form, c_dst_f2, is in
+// angular_f2.cuh.
 __constant__ float c_dst_f[kDstEntries];
 __constant__ double c_dst_d[kDstEntries];
-__constant__ float2 c_dst_f2[kDstEntries];
 
 template <typename real>
 struct DstTab;
@@ -62,10 +62,6 @@ struct DstTab<double> {
   static __device__ __forceinline__ double at(int idx) { return c_dst_d[dst_off(N) + idx]; }
 };
 
-template <typename real>
-struct AngTables {
-  real lam[kMaxAngle * kMaxAngle];  // eigenvalues [n][m]
-};
 
 // y[m] = sum_i S[m][i] x[i] for an orthonormal DST-I of even length N.
 template <typename real, int N>
@@ -83,21 +79,6 @@ __device__ __forceinline__ void dst_apply(const real (&x)[N], real (&y)[N]) {
   for (int i = 0; i < H; i++)
 #pragma unroll
     for (int m = 0; m < N; m++) y[m] = fma(DstTab<real>::template at<N>(m * N + i), (m & 1) ? o[i] : e[i], y[m]);
-}
-
-__device__ __forceinline__ double mode_factor(double den) { return 2.0 / den - 1.0; }
-__device__ __forceinline__ float mode_factor(float den) { return __fdividef(2.0f, den) - 1.0f; }
-
-// Factor of one sine mode over the step, ql = (h kappa / 4) lam <= 0:
-// Crank-Nicolson (1 + ql) / (1 - ql) = -1 + 2 / (1 - ql), or the exact
-// solution exp(2 ql) of the mode's ODE.
-template <bool EXACT>
-__device__ __forceinline__ double mode_scale(double ql) {
-  return EXACT ? exp(2.0 * ql) : mode_factor(1.0 - ql);
-}
-template <bool EXACT>
-__device__ __forceinline__ float mode_scale(float ql) {
-  return EXACT ? expf(2.0f * ql) : mode_factor(1.0f - ql);
 }
 
 template <typename real, int NU, int NV, bool EXACT>
@@ -158,89 +139,13 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
 
 // ---------------------------------------------------------------- packed FP32 form
 
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-
-// dst_apply on pairs (two lateral points per register pair).
-template <int N>
-__device__ __forceinline__ void dst_apply2(const float2 (&x)[N], float2 (&y)[N]) {
-  constexpr int H = N / 2;
-  float2 e[H], o[H];
-#pragma unroll
-  for (int i = 0; i < H; i++) {
-    e[i] = add2(x[i], x[N - 1 - i]);
-    o[i] = fma2(x[N - 1 - i], make_float2(-1.f, -1.f), x[i]);
-  }
-#pragma unroll
-  for (int m = 0; m < N; m++) y[m] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int i = 0; i < H; i++)
-#pragma unroll
-    for (int m = 0; m < N; m++) y[m] = fma2(c_dst_f2[dst_off(N) + m * N + i], (m & 1) ? o[i] : e[i], y[m]);
-}
-
-// As k_angular with each thread on two adjacent lateral points (one 8-byte
-// load per row) and the transforms on FP32x2 pairs; kF2X threads (2 kF2X
-// lateral points) per slab row, so that a warp covers two rows of 128 bytes
-// and several CTAs fit an SM (one CTA's loads overlap another's transforms).
-// nyz must be even.
-constexpr int kF2X = 16;
 template <int NU, int NV, bool EXACT>
 __global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV))
     k_angular_f2(float *__restrict__ psi, const float *__restrict__ rho_yz, const float *__restrict__ ts, int nyz,
                  int ng, float hq, long long kgc0, const __grid_constant__ AngTables<float> tb) {
-  constexpr int NA = NU * NV;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2(*tile)[kF2X] = reinterpret_cast<float2(*)[kF2X]>(smem_raw);
-  const int x = threadIdx.x;
-  const int t = threadIdx.y;
-  const long long kgc = kgc0 + blockIdx.y;  // (k * ng + g) * 2 + c
-  const int g = (int)((kgc / 2) % ng);
-  const int yz = (blockIdx.x * kF2X + x) * 2;
-  const bool active = yz < nyz;
-  float *base = psi + kgc * (long long)NA * nyz + yz;
-  if (t < NV) {
-    float2 r[NU], y[NU];
-#pragma unroll
-    for (int i = 0; i < NU; i++)
-      r[i] = active ? *reinterpret_cast<const float2 *>(base + (long long)(t * NU + i) * nyz) : make_float2(0.f, 0.f);
-    dst_apply2<NU>(r, y);
-#pragma unroll
-    for (int i = 0; i < NU; i++) tile[t * NU + i][x] = y[i];
-  }
-  __syncthreads();
-  if (t < NU) {
-    float2 q = make_float2(0.f, 0.f);
-    if (active) {
-      const float2 rr = *reinterpret_cast<const float2 *>(rho_yz + yz);
-      const float w = hq * ts[g];
-      q = make_float2(w * rr.x, w * rr.y);  // h kappa / 4
-    }
-    float2 c[NV], y[NV];
-#pragma unroll
-    for (int j = 0; j < NV; j++) c[j] = tile[j * NU + t][x];
-    dst_apply2<NV>(c, y);
-#pragma unroll
-    for (int n = 0; n < NV; n++) {
-      const float l = tb.lam[n * NU + t];
-      y[n].x *= mode_scale<EXACT>(q.x * l);
-      y[n].y *= mode_scale<EXACT>(q.y * l);
-    }
-    dst_apply2<NV>(y, c);
-#pragma unroll
-    for (int j = 0; j < NV; j++) tile[j * NU + t][x] = c[j];
-  }
-  __syncthreads();
-  if (t < NV) {
-    float2 r[NU], y[NU];
-#pragma unroll
-    for (int i = 0; i < NU; i++) r[i] = tile[t * NU + i][x];
-    dst_apply2<NU>(r, y);
-    if (active) {
-#pragma unroll
-      for (int i = 0; i < NU; i++) *reinterpret_cast<float2 *>(base + (long long)(t * NU + i) * nyz) = y[i];
-    }
-  }
+  angular_f2_tile<NU, NV, EXACT>(psi, rho_yz, ts, nyz, ng, hq, kgc0 + blockIdx.y, blockIdx.x, threadIdx.x, threadIdx.y,
+                                 smem_raw, tb);
 }
 
 template <int NU, int NV, bool EXACT>
@@ -437,15 +342,6 @@ cudaError_t go_tma(const LaunchCtx &lc, const Dims &d, real *psi, const real *rh
   return cudaGetLastError();
 }
 
-template <typename real>
-void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv) {
-  const double pi = 3.14159265358979323846;
-  for (int n = 0; n < nv; n++)
-    for (int m = 0; m < nu; m++)
-      tb.lam[n * nu + m] = (real)((2.0 * std::cos(pi * (m + 1) / (nu + 1)) - 2.0) / (du * du) +
-                                  (2.0 * std::cos(pi * (n + 1) / (nv + 1)) - 2.0) / (dv * dv));
-}
-
 template <typename real, int NU, int NV, bool EXACT>
 cudaError_t go_exact(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts, double h,
                      const AngTables<real> &tb) {
@@ -509,7 +405,6 @@ cudaError_t launch_angular(const LaunchCtx &lc, const Dims &d, real *psi, const 
 cudaError_t angular_init_tables() {
   static float hf[kDstEntries];
   static double hd[kDstEntries];
-  static float2 hf2[kDstEntries];
   const double pi = 3.14159265358979323846;
   for (int n = 2; n <= kMaxAngle; n += 2)
     for (int m = 0; m < n; m++)
@@ -518,11 +413,10 @@ cudaError_t angular_init_tables() {
         const int at = dst_off(n) + m * n + i;
         hd[at] = v;
         hf[at] = (float)v;
-        hf2[at] = make_float2((float)v, (float)v);
       }
   cudaError_t e = cudaMemcpyToSymbol(c_dst_f, hf, sizeof(hf));
   if (e != cudaSuccess) return e;
-  if ((e = cudaMemcpyToSymbol(c_dst_f2, hf2, sizeof(hf2))) != cudaSuccess) return e;
+  if ((e = upload_dst_f2()) != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_dst_d, hd, sizeof(hd));
 }
 

@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     if (lane == 0 && count > 0) {
       const uint32_t idesc = idesc_bf16(kTM, kTN);
       const uint32_t lbo = 128, sbo = (uint32_t)kcm * 128;
-      int issued = 0, cur_gb = -1, consumed = 0;
+      int issued = 0, cur_gb = -1, consumed = 0, committed = 0;
       unsigned a_phase = 0;
       bool ok = true, a_pending = false;
       for (int i = 0; i < count && ok; i++) {
@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         }
         mma_commit(&empty_b[s]);
         mma_commit(&acc_full[acc]);
+        committed = i + 1;
       }
       if (!ok) {
         *reinterpret_cast<volatile int *>(&s_abort) = 1;
@@ -412,8 +413,10 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         for (int k = consumed; k < issued; k++)
           mbar_wait_bounded(&full_b[k % nstages], (unsigned)((k / nstages) & 1), kPipeWait / 8);
       }
-      // the last commit covers every MMA issued: wait for it before TMEM is released
-      if (count > 0) mbar_wait_bounded(&acc_full[(count - 1) & 1], (unsigned)(((count - 1) >> 1) & 1), kPipeWait);
+      // the last commit covers every MMA issued (tile committed - 1; fewer than
+      // count after a timeout): wait for it before TMEM is released
+      if (committed > 0)
+        mbar_wait_bounded(&acc_full[(committed - 1) & 1], (unsigned)(((committed - 1) >> 1) & 1), kPipeWait);
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of each M half,

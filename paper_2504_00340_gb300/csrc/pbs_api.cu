@@ -49,6 +49,20 @@ struct pbs_ctx {
   double rho_max = 0.0;      // densest voxel of the material (explicit straggling bound)
   double strag_bound = 0.0;  // Gershgorin row bound of the straggling blocks
   bool have_tables = false, have_material = false, have_beam = false;
+  // lateral part of a beam decomposed along y (pbs_set_lateral_part): rows
+  // 0..ny-1 of this context are rows part_y0..part_y0+ny-1 of a grid of
+  // part_nyg rows; the first halo_lo and the last halo_hi rows are copies of
+  // the neighbouring parts' rows, refreshed before every transport substep
+  bool part = false;
+  int part_y0 = 0, part_nyg = 0, halo_lo = 0, halo_hi = 0;
+  int stage = 0;                    // next stage of the staged step (pbs_step_stage)
+  cudaEvent_t xev = nullptr;        // orders halo copies between parts on different streams
+  // persistent batch led by this context (pbs_run_batch): the key of the
+  // descriptors last uploaded, and the recorded graph of the batch
+  unsigned long long batch_key = 0;
+  cudaGraphExec_t batch_graph = nullptr;
+  long long batch_graph_kernels = 0;
+  unsigned long long material_hash = 0;  // FNV-1a of the density last set (checkpoint consistency)
   int n_slabs = 0;
   int steps_done = 0;
   bool pending = false;  // closing E(h/2) of the last step not applied yet
@@ -81,6 +95,8 @@ struct pbs_ctx {
     for (auto e : pool) cudaEventDestroy(e);
     if (graph) cudaGraphExecDestroy(graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (xev) cudaEventDestroy(xev);
+    if (batch_graph) cudaGraphExecDestroy(batch_graph);
   }
 };
 
@@ -102,6 +118,12 @@ pbs_status cuda_fail(pbs_ctx *c, cudaError_t e, const char *where) {
   } while (0)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Rows a lateral part needs from each neighbour before a transport substep:
+// the two stages of the explicit trapezoid each reach two cells upstream
+// (upwind-biased limited reconstruction), so a cell's update depends on the
+// four rows on either side of it (either side: the speed's sign varies).
+constexpr int kHaloRows = 4;
 
 size_t init_stride(const pbs_ctx *c) { return (size_t)(2 * c->ng + c->na + c->ny + c->nz); }
 
@@ -584,9 +606,13 @@ void beam_factors(const pbs_ctx *c, const pbs_beam &b, std::vector<double> &out)
       fa[j * c->nu + i] = pu * pv;
       nang += pu * pv * c->du * c->dv;
     }
-  for (int p = 0; p < c->ny; p++) {
-    fy[p] = normal_mass((p - 0.5 * c->ny) * c->dy, (p + 1 - 0.5 * c->ny) * c->dy, b.y0, b.sigma_y) / c->dy;
-    nyy += fy[p] * c->dy;
+  // rows of the whole grid (a lateral part projects its rows of it, with the
+  // whole grid's normalisation, so that it holds exactly the whole grid's values)
+  const int nyg = c->part ? c->part_nyg : c->ny, y0 = c->part ? c->part_y0 : 0;
+  for (int pg = 0; pg < nyg; pg++) {
+    const double f = normal_mass((pg - 0.5 * nyg) * c->dy, (pg + 1 - 0.5 * nyg) * c->dy, b.y0, b.sigma_y) / c->dy;
+    if (pg >= y0 && pg < y0 + c->ny) fy[pg - y0] = f;
+    nyy += f * c->dy;
   }
   for (int q = 0; q < c->nz; q++) {
     fz[q] = normal_mass((q - 0.5 * c->nz) * c->dz, (q + 1 - 0.5 * c->nz) * c->dz, b.z0, b.sigma_z) / c->dz;
@@ -748,28 +774,113 @@ pbs_status flush_impl(pbs_ctx *c) {
 // opening E(h/2) of the next (same arithmetic, one pass over psi instead of
 // two); any read or substep call applies a deferred half first.  Beams whose
 // depth ends at step s - 1 get the closing half alone.
+// The four stages of depth step s = steps_done, with act beams marching it:
+//   0  E(h/2) opening step s (fused with the deferred closing half of s-1)
+//   1  T(h/2)      2  A(h)      3  T(h/2), then the closing half is deferred
+// A lateral part of a decomposed beam needs fresh halo rows before stages 1
+// and 3; every other stage is local to each lateral point.
+template <typename real, typename st>
+pbs_status stage_impl(pbs_ctx *c, int stage) {
+  const int s = c->steps_done;
+  const int act = active_at(c, s);
+  pbs_status r = PBS_OK;
+  switch (stage) {
+    case 0:
+      if (c->pending) {
+        const int prev = active_at(c, s - 1);
+        r = energy_run<real, st>(c, 0.5 * c->dx, s - 1, s, s, 0, act);  // close step s-1, open step s
+        if (r == PBS_OK) r = energy_run<real, st>(c, 0.5 * c->dx, s - 1, -1, s, act, prev);  // close only
+      } else {
+        r = energy_run<real, st>(c, 0.5 * c->dx, s, -1, -1, 0, act);
+      }
+      c->pending = false;
+      return r;
+    case 1:
+      return transport_run<real>(c, 0.5 * c->dx, act);
+    case 2:
+      return angular_run<real>(c, c->dx, s, act);
+    default:
+      if ((r = transport_run<real>(c, 0.5 * c->dx, act)) != PBS_OK) return r;
+      c->pending = act > 0;
+      c->steps_done++;
+      return PBS_OK;
+  }
+}
+
 template <typename real, typename st>
 pbs_status step_impl(pbs_ctx *c, int n) {
-  for (int i = 0; i < n; i++) {
-    const int s = c->steps_done;
-    const int act = active_at(c, s);
-    pbs_status r;
-    if (c->pending) {
-      const int prev = active_at(c, s - 1);
-      r = energy_run<real, st>(c, 0.5 * c->dx, s - 1, s, s, 0, act);  // close step s-1, open step s
-      if (r == PBS_OK) r = energy_run<real, st>(c, 0.5 * c->dx, s - 1, -1, s, act, prev);  // close only
-    } else {
-      r = energy_run<real, st>(c, 0.5 * c->dx, s, -1, -1, 0, act);
+  for (int i = 0; i < n; i++)
+    for (int stage = 0; stage < 4; stage++) {
+      pbs_status r = stage_impl<real, st>(c, stage);
+      if (r != PBS_OK) return r;
     }
-    c->pending = false;
-    if (r != PBS_OK) return r;
-    if ((r = transport_run<real>(c, 0.5 * c->dx, act)) != PBS_OK) return r;
-    if ((r = angular_run<real>(c, c->dx, s, act)) != PBS_OK) return r;
-    if ((r = transport_run<real>(c, 0.5 * c->dx, act)) != PBS_OK) return r;
-    c->pending = act > 0;
-    c->steps_done++;
+  return PBS_OK;
+}
+
+// Halo rows of the lateral parts P[0..n-1] (ordered by row): each interior
+// interface copies the rows each side needs from the other's own rows into
+// its own workspace, for every (component, group, coefficient, angle) plane:
+// two strided copies (cudaMemcpy2DAsync) per interface.  Parts on other
+// streams or devices are ordered by event waits before and after the copies,
+// so that neither side's next transport overwrites rows still being read.
+pbs_status join_streams(pbs_ctx *a, pbs_ctx *b) {
+  if (a->stream == b->stream && a->dev == b->dev) return PBS_OK;
+  for (pbs_ctx *x : {a, b}) {
+    pbs_ctx *y = x == a ? b : a;
+    PBS_CUDA(x, cudaSetDevice(x->dev));
+    if (!x->xev) PBS_CUDA(x, cudaEventCreateWithFlags(&x->xev, cudaEventDisableTiming));
+    PBS_CUDA(x, cudaEventRecord(x->xev, x->stream));
+    PBS_CUDA(x, cudaSetDevice(y->dev));
+    PBS_CUDA(x, cudaStreamWaitEvent(y->stream, x->xev, 0));
   }
   return PBS_OK;
+}
+
+pbs_status copy_rows(pbs_ctx *dst, int dst_row, pbs_ctx *src, int src_row, int rows) {
+  if (rows <= 0) return PBS_OK;
+  const size_t rs = dst->rsize, row = (size_t)dst->nz * rs;
+  const size_t planes = (size_t)dst->d.ncomp * dst->ng * 2 * dst->na;
+  unsigned char *d = at<unsigned char>(dst, dst->off_psi) + (size_t)dst_row * row;
+  const unsigned char *q = at<unsigned char>(src, src->off_psi) + (size_t)src_row * row;
+  const size_t dp = (size_t)dst->ny * row, sp = (size_t)src->ny * row;
+  PBS_CUDA(dst, cudaSetDevice(dst->dev));
+  for (size_t p0 = 0; p0 < planes; p0 += 32768) {  // in chunks of planes
+    const size_t np = std::min<size_t>(32768, planes - p0);
+    PBS_CUDA(dst, cudaMemcpy2DAsync(d + p0 * dp, dp, q + p0 * sp, sp, (size_t)rows * row, np, cudaMemcpyDefault,
+                                    dst->stream));
+  }
+  return PBS_OK;
+}
+
+pbs_status exchange_halos(pbs_ctx *const *P, int n) {
+  for (int i = 0; i + 1 < n; i++) {
+    pbs_ctx *lo = P[i], *hi = P[i + 1];
+    pbs_status r = join_streams(lo, hi);
+    if (r != PBS_OK) return r;
+    // lo's upper halo <- hi's rows; hi's lower halo <- lo's rows
+    const int lo_halo_g = lo->part_y0 + lo->ny - lo->halo_hi;  // first global row of lo's upper halo
+    if ((r = copy_rows(lo, lo->ny - lo->halo_hi, hi, lo_halo_g - hi->part_y0, lo->halo_hi)) != PBS_OK) return r;
+    if ((r = copy_rows(hi, 0, lo, hi->part_y0 - lo->part_y0, hi->halo_lo)) != PBS_OK) return r;
+    if ((r = join_streams(lo, hi)) != PBS_OK) return r;
+  }
+  return PBS_OK;
+}
+
+template <typename real, typename st>
+pbs_status domain_step_impl(pbs_ctx *const *P, int n, int n_steps) {
+  int dev0 = 0;
+  cudaGetDevice(&dev0);
+  pbs_status r = PBS_OK;
+  for (int i = 0; i < n_steps && r == PBS_OK; i++)
+    for (int stage = 0; stage < 4 && r == PBS_OK; stage++) {
+      if (stage == 1 || stage == 3) r = exchange_halos(P, n);
+      for (int j = 0; j < n && r == PBS_OK; j++) {
+        if (cudaSetDevice(P[j]->dev) != cudaSuccess) r = fail(P[j], PBS_ERR_CUDA, "cudaSetDevice");
+        else r = stage_impl<real, st>(P[j], stage);
+      }
+    }
+  cudaSetDevice(dev0);
+  return r;
 }
 
 // Restart every beam from its projection (factors already on the device):
@@ -798,6 +909,7 @@ pbs_status reinit_impl(pbs_ctx *c) {
   }
   c->steps_done = 0;
   c->pending = false;
+  c->stage = 0;
   return PBS_OK;
 }
 
@@ -1043,18 +1155,198 @@ pbs_status autotune_impl(pbs_ctx *c, int reps) {
 
 // Checkpoint layout: CkptHeader, then psi (ncomp * comp_elems * rsize), dose
 // (B * nx * nyz doubles), fluence (B * (nx + 1) * nyz doubles), beam factors
-// (B * init_stride doubles), beam depth ranges (B ints).
+// (B * init_stride doubles), beam depth ranges (B ints).  The header also
+// records what the saved state was marched with but does not contain: the
+// method options, a hash of the FP64 host tables and of the density field;
+// a restore into a context that differs in any of them is refused.
 struct CkptHeader {
   char magic[8];
   int version, precision, ny, nz, ng, nu, nv, nx, K, B, steps_done, pending, have_beam, n_slabs_at_save;
+  int angular_integrator, transport_integrator, straggling_integrator, pad;
+  unsigned long long tables_hash, material_hash;
 };
 
 namespace {
+// FNV-1a with 64-bit words in place of bytes (the tables are doubles; a
+// consistency check, not a cryptographic one), continuing from h.
+unsigned long long fnv1a(unsigned long long h, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  size_t i = 0;
+  for (; i + 8 <= n; i += 8) {
+    unsigned long long w;
+    std::memcpy(&w, b + i, 8);
+    h ^= w;
+    h *= 1099511628211ULL;
+  }
+  for (; i < n; i++) {
+    h ^= b[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+unsigned long long tables_hash(const pbs_ctx *c) {
+  unsigned long long h = 14695981039346656037ULL;
+  for (const std::vector<double> *v : {&c->e_faces, &c->s_face, &c->s_base, &c->t_face, &c->ts, &c->sig, &c->p1,
+                                       &c->p2, &c->q1, &c->decay})
+    h = fnv1a(h, v->data(), v->size() * sizeof(double));
+  return h;
+}
+
 size_t ckpt_bytes(const pbs_ctx *c) {
   const size_t nyz = (size_t)c->ny * c->nz;
   return sizeof(CkptHeader) + (size_t)c->d.ncomp * c->d.comp_elems * c->rsize + (size_t)c->B * c->nx * nyz * 8 +
          (size_t)c->B * (c->nx + 1) * nyz * 8 + (size_t)c->B * init_stride(c) * 8 + (size_t)c->B * sizeof(int);
 }
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------- persistent batch
+
+int beam_passes(int steps) { return steps > 0 ? 4 * steps + 1 : 0; }
+
+struct BatchLayout {
+  size_t off_beams, off_tasks, off_queue, off_done, off_next, total;
+  long long ntasks;
+};
+
+BatchLayout batch_layout(pbs_ctx *const *P, int n) {
+  BatchLayout L{};
+  long long nt = 0;
+  for (int i = 0; i < n; i++) nt += beam_passes(beam_depth(P[i], 0));
+  L.ntasks = nt;
+  size_t o = 0;
+  L.off_beams = o; o = align256(o + sizeof(BatchBeam) * (size_t)n);
+  L.off_tasks = o; o = align256(o + sizeof(BatchTask) * (size_t)nt);
+  L.off_queue = o; o = align256(o + sizeof(BatchQueue));
+  L.off_done = o; o = align256(o + 8 * (size_t)n);
+  L.off_next = o; o = align256(o + 8 * (size_t)nt);
+  L.total = o;
+  return L;
+}
+
+// What the persistent kernel handles: FP32 psi (FP32 or mixed precision, no
+// scattered component, so the mixed form runs in FP32 too), one beam per
+// context, the default integrators, no straggling, even ny*nz, rows a
+// multiple of 4 columns, angle grids of at most 8 x 8 shared by the batch,
+// all contexts on one device and stream, launched and not mid-step.
+pbs_status batch_check(pbs_ctx *const *P, int n) {
+  pbs_ctx *c0 = P[0];
+  for (int i = 0; i < n; i++) {
+    pbs_ctx *c = P[i];
+    if (!ready_to_march(c)) return fail(c0, PBS_ERR_STATE, "every beam needs a workspace, tables, material and a launched beam");
+    if (c->stage != 0) return fail(c0, PBS_ERR_STATE, "a staged step is in progress on a beam");
+    if (c->precision == PBS_FP64 || c->K != 0 || c->B != 1 || c->strag || c->opts.angular_integrator != 0 ||
+        c->opts.transport_integrator != 0 || ((c->ny * c->nz) & 1) || c->nz % 4 != 0 || !batch_supported(c->nu, c->nv))
+      return fail(c0, PBS_ERR_UNSUPPORTED,
+                  "the persistent batch takes FP32/mixed beams with K = 0, one beam per context, the default "
+                  "integrators, no straggling, even ny*nz, nz a multiple of 4 and at most 8 x 8 angles");
+    if (c->dev != c0->dev || c->stream != c0->stream)
+      return fail(c0, PBS_ERR_ARG, "the beams of a batch share one device and one stream");
+    if (c->nu != c0->nu || c->nv != c0->nv || c->u_max != c0->u_max || c->v_max != c0->v_max)
+      return fail(c0, PBS_ERR_ARG, "the beams of a batch share one angle grid");
+    for (int j = 0; j < i; j++)
+      if (P[j] == c) return fail(c0, PBS_ERR_ARG, "a context appears twice in the batch");
+    if (batch_shape(c->d).smem > 160 * 1024) return fail(c0, PBS_ERR_UNSUPPORTED, "too many energy groups for the batch");
+  }
+  return PBS_OK;
+}
+
+// Descriptors of the batch (beams, round-robin task list) in host memory.
+void batch_descriptors(pbs_ctx *const *P, int n, const BatchLayout &L, int hold_beam, std::vector<BatchBeam> &beams,
+                       std::vector<BatchTask> &tasks, size_t &smem) {
+  beams.assign(n, BatchBeam{});
+  tasks.clear();
+  tasks.reserve((size_t)L.ntasks);
+  smem = 0;
+  std::vector<BatchShape> shape(n);
+  int max_passes = 0;
+  for (int b = 0; b < n; b++) {
+    pbs_ctx *c = P[b];
+    const BatchShape sh = batch_shape(c->d);
+    shape[b] = sh;
+    smem = std::max(smem, sh.smem);
+    BatchBeam &m = beams[b];
+    m.psi = at<float>(c, c->off_psi);
+    m.rho = at<float>(c, c->off_rho);
+    m.coef = at<GroupCoef<float>>(c, c->off_coef);
+    m.ts = at<float>(c, c->off_ts);
+    m.dose = at<double>(c, c->off_dose);
+    m.flu = at<double>(c, c->off_flu);
+    m.err = at<int>(c, c->off_err);
+    m.d = c->d;
+    m.n_steps = beam_depth(c, 0);
+    // the constants of the per-substep launches, rounded the same way
+    const double h = 0.5 * c->dx;
+    m.c = (float)(0.5 * h);
+    m.hq = (float)(0.25 * c->dx);
+    m.ky = (float)(h / c->dy);
+    m.kz = (float)(h / c->dz);
+    m.du = (float)c->du;
+    m.dv = (float)c->dv;
+    m.dose_scale = c->du * c->dv / c->dx;
+    m.flu_scale = c->du * c->dv;
+    m.e_bx = sh.e_bx;
+    m.a_bx = sh.a_bx;
+    m.tr_nseg = sh.tr_nseg;
+    m.tr_segw = sh.tr_segw;
+    m.tr_gw = sh.tr_gw;
+    m.tr_stacks = sh.tr_stacks;
+    max_passes = std::max(max_passes, beam_passes(m.n_steps));
+  }
+  std::vector<long long> need(n, 0);
+  for (int r = 0; r < max_passes; r++)
+    for (int b = 0; b < n; b++) {
+      if (r >= beam_passes(beams[b].n_steps)) continue;
+      const int kind = (r == 4 * beams[b].n_steps || (r & 3) == 0) ? 0 : ((r & 3) == 2 ? 2 : 1);
+      const long long nt = kind == 0 ? shape[b].e_tiles : (kind == 1 ? shape[b].t_tiles : shape[b].a_tiles);
+      // the test hook: one tile more than the earlier passes hold, so no wait on it ends
+      const long long extra = (b == hold_beam && r == 1) ? 1 : 0;
+      tasks.push_back(BatchTask{b, r, nt, need[b] + extra});
+      need[b] += nt;
+    }
+}
+
+unsigned long long batch_key(pbs_ctx *const *P, int n, void *ws, size_t bytes, long long wait_cycles, int hold) {
+  unsigned long long h = 14695981039346656037ULL;
+  for (int i = 0; i < n; i++) {
+    const void *ptr = P[i];
+    const int depth = beam_depth(P[i], 0);
+    h = fnv1a(h, &ptr, sizeof(ptr));
+    h = fnv1a(h, &P[i]->ws, sizeof(void *));
+    h = fnv1a(h, &depth, sizeof(depth));
+  }
+  h = fnv1a(h, &n, sizeof(n));
+  h = fnv1a(h, &ws, sizeof(ws));
+  h = fnv1a(h, &bytes, sizeof(bytes));
+  h = fnv1a(h, &wait_cycles, sizeof(wait_cycles));
+  h = fnv1a(h, &hold, sizeof(hold));
+  return h;
+}
+
+// The batch's device work, issued on the lead context's stream: every beam
+// restarted from its projection, the queue counters cleared, the
+// persistent launch.
+pbs_status batch_issue(pbs_ctx *const *P, int n, unsigned char *ws, const BatchLayout &L, long long wait_cycles,
+                       size_t smem) {
+  pbs_ctx *c0 = P[0];
+  for (int b = 0; b < n; b++) {
+    pbs_status r = P[b]->precision == PBS_FP32 ? reinit_impl<float, float>(P[b])
+                                               : reinit_impl<float, __nv_bfloat16>(P[b]);
+    if (r != PBS_OK) return r;
+  }
+  PBS_CUDA(c0, cudaMemsetAsync(ws + L.off_queue, 0, L.total - L.off_queue, c0->stream));
+  LaunchCtx lc = lctx(c0);
+  cudaError_t e = launch_batch(lc, c0->nu, c0->nv, reinterpret_cast<const BatchBeam *>(ws + L.off_beams), n,
+                               reinterpret_cast<const BatchTask *>(ws + L.off_tasks), (int)L.ntasks,
+                               reinterpret_cast<BatchQueue *>(ws + L.off_queue),
+                               reinterpret_cast<unsigned long long *>(ws + L.off_done),
+                               reinterpret_cast<unsigned long long *>(ws + L.off_next), wait_cycles, smem, c0->du,
+                               c0->dv);
+  return e == cudaSuccess ? PBS_OK : cuda_fail(c0, e, "batch kernel");
+}
+
 }  // namespace
 
 #define PBS_DISPATCH(c, FN, ...)                                                    \
@@ -1242,6 +1534,7 @@ pbs_status pbs_set_material(pbs_ctx *c, const double *rho, int n) {
   if (r != PBS_OK) return r;
   c->rho_max = 0.0;
   for (size_t e = 0; e < (size_t)n * c->ny * c->nz; e++) c->rho_max = std::max(c->rho_max, rho[e]);
+  c->material_hash = fnv1a(14695981039346656037ULL, rho, (size_t)n * c->ny * c->nz * sizeof(double));
   c->n_slabs = n;
   c->have_material = true;
   return PBS_OK;
@@ -1285,6 +1578,7 @@ pbs_status pbs_set_beam_steps(pbs_ctx *c, const int *steps, int n) {
 pbs_status pbs_run(pbs_ctx *c, int use_graph) {
   if (!c) return PBS_ERR_ARG;
   if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
+  if (c->stage != 0) return fail(c, PBS_ERR_STATE, "a staged step is in progress (pbs_step_stage)");
   { pbs_status gr = strag_guard(c, 0.5 * c->dx); if (gr != PBS_OK) return gr; }
   if (use_graph) return PBS_DISPATCH(c, run_graph_impl, c);
   return PBS_DISPATCH(c, run_impl, c);
@@ -1340,9 +1634,199 @@ pbs_status pbs_get_tuning(const pbs_ctx *c, pbs_tuning *t) {
 pbs_status pbs_step(pbs_ctx *c, int n) {
   if (!c || n < 0) return fail(c, PBS_ERR_ARG, "bad step count");
   if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
+  if (c->stage != 0) return fail(c, PBS_ERR_STATE, "a staged step is in progress (pbs_step_stage)");
   if (c->steps_done + n > c->n_slabs) return fail(c, PBS_ERR_ARG, "march would pass the last material slab");
   { pbs_status gr = strag_guard(c, 0.5 * c->dx); if (gr != PBS_OK) return gr; }
   return PBS_DISPATCH(c, step_impl, c, n);
+}
+
+pbs_status pbs_step_stage(pbs_ctx *c, int stage) {
+  if (!c || stage < 0 || stage > 3) return fail(c, PBS_ERR_ARG, "stage must be 0..3");
+  if (!ready_to_march(c)) return fail(c, PBS_ERR_STATE, "launch a beam (with workspace, physics, material) first");
+  if (stage != c->stage) return fail(c, PBS_ERR_STATE, "stages of a step run in order 0, 1, 2, 3");
+  if (stage == 0) {
+    if (c->steps_done + 1 > c->n_slabs) return fail(c, PBS_ERR_ARG, "march would pass the last material slab");
+    pbs_status gr = strag_guard(c, 0.5 * c->dx);
+    if (gr != PBS_OK) return gr;
+  }
+  pbs_status r = PBS_DISPATCH(c, stage_impl, c, stage);
+  if (r == PBS_OK) c->stage = (stage + 1) & 3;
+  return r;
+}
+
+pbs_status pbs_set_lateral_part(pbs_ctx *c, int y_offset, int ny_global, int halo_lo, int halo_hi) {
+  if (!c) return PBS_ERR_ARG;
+  if (c->B != 1) return fail(c, PBS_ERR_UNSUPPORTED, "a lateral part holds one beam (n_beams = 1)");
+  if (ny_global < c->ny || y_offset < 0 || y_offset + c->ny > ny_global || halo_lo < 0 || halo_hi < 0 ||
+      halo_lo + halo_hi >= c->ny || (y_offset == 0) != (halo_lo == 0) ||
+      (y_offset + c->ny == ny_global) != (halo_hi == 0))
+    return fail(c, PBS_ERR_ARG,
+                "bad lateral part: rows must lie inside the grid, with halo rows exactly on the interior sides");
+  if (c->have_beam) return fail(c, PBS_ERR_STATE, "declare the lateral part before launching the beam");
+  c->part = !(y_offset == 0 && ny_global == c->ny);
+  c->part_y0 = y_offset;
+  c->part_nyg = ny_global;
+  c->halo_lo = halo_lo;
+  c->halo_hi = halo_hi;
+  return PBS_OK;
+}
+
+pbs_status pbs_copy_rows(pbs_ctx *c, int first_row, int n_rows, int to_buffer, void *dev_buf) {
+  if (!c || !dev_buf || first_row < 0 || n_rows < 0 || first_row + n_rows > c->ny)
+    return fail(c, PBS_ERR_ARG, "rows out of range or null buffer");
+  if (!c->ws) return fail(c, PBS_ERR_STATE, "no workspace");
+  if (n_rows == 0) return PBS_OK;
+  const size_t row = (size_t)c->nz * c->rsize, pitch = (size_t)c->ny * row;
+  const size_t planes = (size_t)c->d.ncomp * c->ng * 2 * c->na;
+  unsigned char *w = at<unsigned char>(c, c->off_psi) + (size_t)first_row * row;
+  unsigned char *b = static_cast<unsigned char *>(dev_buf);
+  const size_t width = (size_t)n_rows * row;
+  for (size_t p0 = 0; p0 < planes; p0 += 32768) {
+    const size_t np = std::min<size_t>(32768, planes - p0);
+    if (to_buffer)
+      PBS_CUDA(c, cudaMemcpy2DAsync(b + p0 * width, width, w + p0 * pitch, pitch, width, np, cudaMemcpyDefault,
+                                    c->stream));
+    else
+      PBS_CUDA(c, cudaMemcpy2DAsync(w + p0 * pitch, pitch, b + p0 * width, width, width, np, cudaMemcpyDefault,
+                                    c->stream));
+  }
+  return PBS_OK;
+}
+
+pbs_status pbs_domain_step(pbs_ctx *const *parts, int n_parts, int n_steps) {
+  if (!parts || n_parts < 1 || n_steps < 0) return PBS_ERR_ARG;
+  for (int i = 0; i < n_parts; i++)
+    if (!parts[i]) return PBS_ERR_ARG;
+  pbs_ctx *c0 = parts[0];
+  const int nyg = c0->part ? c0->part_nyg : c0->ny;
+  int owned_end = 0;
+  for (int i = 0; i < n_parts; i++) {
+    pbs_ctx *c = parts[i];
+    if (!ready_to_march(c)) return fail(c0, PBS_ERR_STATE, "every part needs a launched beam, material and tables");
+    if (c->stage != 0) return fail(c0, PBS_ERR_STATE, "a staged step is in progress on a part");
+    if (c->B != 1 || c->precision != c0->precision || c->nz != c0->nz || c->ng != c0->ng || c->na != c0->na ||
+        c->K != c0->K || c->dx != c0->dx || c->dy != c0->dy || c->dz != c0->dz || c->u_max != c0->u_max ||
+        c->v_max != c0->v_max)
+      return fail(c0, PBS_ERR_ARG, "parts differ in grid, precision or scattering order");
+    if (std::memcmp(&c->opts, &c0->opts, sizeof(pbs_options)) != 0)
+      return fail(c0, PBS_ERR_ARG, "parts differ in method options");
+    if (c->opts.transport_integrator != 0)
+      return fail(c0, PBS_ERR_UNSUPPORTED,
+                  "the Crank-Nicolson transport sweeps whole rows: no finite halo; use the explicit trapezoid");
+    if (c->steps_done != c0->steps_done || c->pending != c0->pending || beam_depth(c, 0) != beam_depth(c0, 0))
+      return fail(c0, PBS_ERR_STATE, "parts are at different depths");
+    if (n_parts > 1 && (!c->part || c->part_nyg != nyg))
+      return fail(c0, PBS_ERR_ARG, "declare every part with pbs_set_lateral_part on one grid");
+    // owned rows tile the grid in order; interior halos cover the transport's reach
+    const int y0 = n_parts > 1 ? c->part_y0 : 0;
+    if (y0 + c->halo_lo != owned_end) return fail(c0, PBS_ERR_ARG, "parts must follow one another in y");
+    owned_end = y0 + c->ny - c->halo_hi;
+    const int owned = c->ny - c->halo_lo - c->halo_hi;
+    if ((i > 0 && c->halo_lo < kHaloRows) || (i + 1 < n_parts && c->halo_hi < kHaloRows))
+      return fail(c0, PBS_ERR_ARG, "interior halos need at least 4 rows (the reach of the two transport stages)");
+    if ((i > 0 && parts[i - 1]->halo_hi > owned) || (i + 1 < n_parts && parts[i + 1]->halo_lo > owned))
+      return fail(c0, PBS_ERR_ARG, "a neighbour's halo is wider than this part's own rows");
+    if (c->steps_done + n_steps > c->n_slabs) return fail(c0, PBS_ERR_ARG, "march would pass the last material slab");
+    pbs_status gr = strag_guard(c, 0.5 * c->dx);
+    if (gr != PBS_OK) return gr;
+  }
+  if (owned_end != nyg) return fail(c0, PBS_ERR_ARG, "the parts do not cover the grid");
+  return PBS_DISPATCH(c0, domain_step_impl, parts, n_parts, n_steps);
+}
+
+pbs_status pbs_batch_workspace_size(pbs_ctx *const *beams, int n_beams, size_t *bytes) {
+  if (!beams || n_beams < 1 || !bytes) return PBS_ERR_ARG;
+  for (int i = 0; i < n_beams; i++)
+    if (!beams[i]) return PBS_ERR_ARG;
+  *bytes = batch_layout(beams, n_beams).total;
+  return PBS_OK;
+}
+
+pbs_status pbs_run_batch(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_t bytes, const pbs_batch_options *o) {
+  if (!beams || n_beams < 1 || n_beams > 65535) return PBS_ERR_ARG;
+  for (int i = 0; i < n_beams; i++)
+    if (!beams[i]) return PBS_ERR_ARG;
+  pbs_ctx *c0 = beams[0];
+  const pbs_batch_options def{0, 0.0, -1};
+  const pbs_batch_options &opt = o ? *o : def;
+  if (opt.hold_beam < -1 || opt.hold_beam >= n_beams) return fail(c0, PBS_ERR_ARG, "hold_beam out of range");
+  pbs_status r = batch_check(beams, n_beams);
+  if (r != PBS_OK) return r;
+  const BatchLayout L = batch_layout(beams, n_beams);
+  if (!dev_ws || bytes < L.total || ((uintptr_t)dev_ws & 255))
+    return fail(c0, PBS_ERR_ARG, "batch workspace missing, smaller than pbs_batch_workspace_size or not 256-byte aligned");
+  if (L.ntasks > INT_MAX) return fail(c0, PBS_ERR_UNSUPPORTED, "too many passes in the batch");
+  int khz = 0;
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c0->dev) != cudaSuccess || khz <= 0) khz = 2000000;
+  const double ms = opt.wait_limit_ms > 0 ? opt.wait_limit_ms : 2000.0;
+  const long long wait_cycles = (long long)(ms * khz);
+  unsigned char *ws = static_cast<unsigned char *>(dev_ws);
+  const unsigned long long key = batch_key(beams, n_beams, dev_ws, bytes, wait_cycles, opt.hold_beam);
+  std::vector<BatchBeam> hb;
+  std::vector<BatchTask> ht;
+  size_t smem = 0;
+  batch_descriptors(beams, n_beams, L, opt.hold_beam, hb, ht, smem);
+  if (key != c0->batch_key) {  // new batch: upload its descriptors, forget its graph
+    PBS_CUDA(c0, batch_init_tables());
+    PBS_CUDA(c0, cudaMemcpyAsync(ws + L.off_beams, hb.data(), sizeof(BatchBeam) * hb.size(), cudaMemcpyHostToDevice,
+                                 c0->stream));
+    if (!ht.empty())
+      PBS_CUDA(c0, cudaMemcpyAsync(ws + L.off_tasks, ht.data(), sizeof(BatchTask) * ht.size(), cudaMemcpyHostToDevice,
+                                   c0->stream));
+    PBS_CUDA(c0, cudaStreamSynchronize(c0->stream));  // the host copies die here
+    if (c0->batch_graph) cudaGraphExecDestroy(c0->batch_graph);
+    c0->batch_graph = nullptr;
+    c0->batch_key = key;
+  }
+  if (!opt.use_graph) {
+    r = batch_issue(beams, n_beams, ws, L, wait_cycles, smem);
+    if (r != PBS_OK) return r;
+  } else {
+    if (!c0->batch_graph) {
+      if (!c0->cap_stream) PBS_CUDA(c0, cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t user = c0->stream;
+      std::vector<long long> before(n_beams);
+      for (int b = 0; b < n_beams; b++) {
+        before[b] = beams[b]->launches;
+        beams[b]->stream = c0->cap_stream;
+        beams[b]->capturing = true;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c0->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        r = batch_issue(beams, n_beams, ws, L, wait_cycles, smem);
+        cudaError_t e2 = cudaStreamEndCapture(c0->cap_stream, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      long long kernels = 0;
+      for (int b = 0; b < n_beams; b++) {
+        beams[b]->stream = user;
+        beams[b]->capturing = false;
+        kernels += beams[b]->launches - before[b];
+        beams[b]->launches = before[b];
+      }
+      if (r != PBS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess) return cuda_fail(c0, e, "batch graph capture");
+      e = cudaGraphInstantiate(&c0->batch_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        c0->batch_graph = nullptr;
+        return cuda_fail(c0, e, "batch graph instantiate");
+      }
+      c0->batch_graph_kernels = kernels;
+    }
+    PBS_CUDA(c0, cudaGraphLaunch(c0->batch_graph, c0->stream));
+    c0->launches += c0->batch_graph_kernels;
+  }
+  for (int b = 0; b < n_beams; b++) {
+    beams[b]->steps_done = beam_depth(beams[b], 0);
+    beams[b]->pending = false;
+    beams[b]->stage = 0;
+  }
+  return PBS_OK;
 }
 
 pbs_status pbs_flush(pbs_ctx *c) {
@@ -1364,13 +1848,18 @@ pbs_status pbs_checkpoint_save(pbs_ctx *c, void *host, size_t bytes) {
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "PBSCKPT1", 8);
-  h.version = 1;
+  h.version = 2;
   h.precision = c->precision;
   h.ny = c->ny; h.nz = c->nz; h.ng = c->ng; h.nu = c->nu; h.nv = c->nv; h.nx = c->nx; h.K = c->K; h.B = c->B;
   h.steps_done = c->steps_done;
   h.pending = c->pending ? 1 : 0;
   h.have_beam = c->have_beam ? 1 : 0;
   h.n_slabs_at_save = c->n_slabs;
+  h.angular_integrator = c->opts.angular_integrator;
+  h.transport_integrator = c->opts.transport_integrator;
+  h.straggling_integrator = c->opts.straggling_integrator;
+  h.tables_hash = c->have_tables ? tables_hash(c) : 0;
+  h.material_hash = c->have_material ? c->material_hash : 0;
   unsigned char *p = static_cast<unsigned char *>(host);
   std::memcpy(p, &h, sizeof(h));
   p += sizeof(h);
@@ -1394,7 +1883,7 @@ pbs_status pbs_checkpoint_load(pbs_ctx *c, const void *host, size_t bytes) {
   if (bytes < sizeof(CkptHeader)) return fail(c, PBS_ERR_ARG, "not a checkpoint");
   CkptHeader h;
   std::memcpy(&h, host, sizeof(h));
-  if (std::memcmp(h.magic, "PBSCKPT1", 8) != 0 || h.version != 1) return fail(c, PBS_ERR_ARG, "not a checkpoint");
+  if (std::memcmp(h.magic, "PBSCKPT1", 8) != 0 || h.version != 2) return fail(c, PBS_ERR_ARG, "not a checkpoint");
   if (h.precision != c->precision || h.ny != c->ny || h.nz != c->nz || h.ng != c->ng || h.nu != c->nu ||
       h.nv != c->nv || h.nx != c->nx || h.K != c->K || h.B != c->B)
     return fail(c, PBS_ERR_ARG, "checkpoint of another grid, precision or batch");
@@ -1405,6 +1894,19 @@ pbs_status pbs_checkpoint_load(pbs_ctx *c, const void *host, size_t bytes) {
     if (steps[b] < 0 || steps[b] > c->nx || (b > 0 && steps[b] > steps[b - 1]))
       return fail(c, PBS_ERR_ARG, "corrupt checkpoint (beam depths)");
   if (h.steps_done < 0 || h.steps_done > c->nx) return fail(c, PBS_ERR_ARG, "corrupt checkpoint (depth)");
+  if ((h.pending != 0 && h.pending != 1) || (h.have_beam != 0 && h.have_beam != 1))
+    return fail(c, PBS_ERR_ARG, "corrupt checkpoint (flags)");
+  // a deferred closing half belongs to step steps_done - 1 of a beam that marched it
+  if (h.pending && (h.steps_done < 1 || h.steps_done > steps[0] || !h.have_beam))
+    return fail(c, PBS_ERR_ARG, "corrupt checkpoint (deferred half without a marched step)");
+  if (!c->have_tables || !c->have_material)
+    return fail(c, PBS_ERR_STATE, "set the tables and the material before restoring a checkpoint");
+  if (h.angular_integrator != c->opts.angular_integrator || h.transport_integrator != c->opts.transport_integrator ||
+      h.straggling_integrator != c->opts.straggling_integrator)
+    return fail(c, PBS_ERR_ARG, "checkpoint marched with other method options (pbs_set_options)");
+  if (h.tables_hash != tables_hash(c)) return fail(c, PBS_ERR_ARG, "checkpoint marched with other tables");
+  if (h.material_hash != c->material_hash || h.n_slabs_at_save != c->n_slabs)
+    return fail(c, PBS_ERR_ARG, "checkpoint marched through another density field");
   const unsigned char *p = static_cast<const unsigned char *>(host) + sizeof(h);
   const size_t nyz = (size_t)c->ny * c->nz;
   const size_t parts[4][2] = {{c->off_psi, (size_t)c->d.ncomp * c->d.comp_elems * c->rsize},

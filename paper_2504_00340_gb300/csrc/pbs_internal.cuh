@@ -57,7 +57,7 @@ struct Dims {
 };
 
 // Device status word: slot 0 counts timeouts, slot 1 records where.
-enum : int { kErrTimeoutSourceMma = 2, kErrTimeoutAngular = 3 };
+enum : int { kErrTimeoutSourceMma = 2, kErrTimeoutAngular = 3, kErrTimeoutBatch = 4 };
 
 // ----------------------------------------------------------------------------
 // PTX helpers: shared-memory addresses, mbarriers, 1-D bulk (TMA) copies.
@@ -250,6 +250,51 @@ cudaError_t launch_source(const LaunchCtx &lc, const Dims &d, const st *p2, cons
 // R of one state for pbs_eval_source; precision as pbs_precision.
 cudaError_t launch_source_input(const LaunchCtx &lc, const Dims &d, const void *psi_k, const void *rho_yz,
                                 const void *coef, void *r_out, int precision);
+
+// Persistent batch march (k_batch.cu).  One beam of the batch: its psi,
+// density, tables, tallies, status word and the constants of its substeps
+// (FP32), with the tile counts of its passes.
+struct BatchBeam {
+  float *psi;
+  const float *rho;
+  const GroupCoef<float> *coef;
+  const float *ts;
+  double *dose, *flu;
+  int *err;
+  Dims d;
+  int n_steps;
+  float c, hq, ky, kz, du, dv;  // E(h/2) CN factor, h/4 of A(h), transport tau/dy, tau/dz, angle spacings
+  double dose_scale, flu_scale;
+  int e_bx, a_bx, tr_nseg, tr_segw, tr_gw;
+  long long tr_stacks;
+};
+// One (beam, pass) of the queue: its tiles, and the beam's tiles in earlier passes.
+struct BatchTask {
+  int beam, pass;
+  long long ntiles, need;
+};
+// Device counters of one launch (zeroed before it): the task being handed
+// out and the abort word (per-beam completed tiles and per-task handed-out
+// tiles are arrays of their own).
+struct BatchQueue {
+  unsigned long long cur;
+  int abort, pad;
+};
+// Tile counts and shared memory of one beam's passes in the batch kernel.
+struct BatchShape {
+  int e_bx, e_by;
+  long long e_tiles, tr_stacks, t_tiles;
+  int tr_nseg, tr_segw, tr_gw;
+  int a_bx;
+  long long a_tiles;
+  size_t smem;
+};
+BatchShape batch_shape(const Dims &d);
+bool batch_supported(int nu, int nv);
+cudaError_t batch_init_tables();
+cudaError_t launch_batch(const LaunchCtx &lc, int nu, int nv, const BatchBeam *beams, int nbeams,
+                         const BatchTask *tasks, int ntasks, BatchQueue *q, unsigned long long *done,
+                         unsigned long long *next, long long wait_cycles, size_t smem, double du, double dv);
 
 template <typename real>
 cudaError_t launch_init(const LaunchCtx &lc, const Dims &d, real *psi0, const double *fe, const double *fa,

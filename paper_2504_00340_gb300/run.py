@@ -3,6 +3,7 @@
     python -m paper_2504_00340_gb300.run --workload water150_128x128_g256_a16x16 \
         [--ny 64 --nz 64] [--ng G] [--steps N] [--precision fp32|fp64|mixed] [--autotune] [--vs-fp64]
     python -m paper_2504_00340_gb300.run --spots 256 [--max-gb 48] [--no-graph] [--no-autotune]
+    python -m paper_2504_00340_gb300.run --spots-vs-fp64 3
 
 Sizes may be overridden to make reduced cases of the same kernels (e.g. for
 profiling).  Prints the per-kernel device times of the march.  --spots runs
@@ -62,6 +63,28 @@ def run_spots(a) -> dict:
     return out
 
 
+def spots_vs_fp64(binding, n):
+    """Dose and fluence error of the mixed-precision march against its FP64
+    form for n spots of the seeded batch (lowest, highest and evenly spaced
+    energies in between), each alone on its own full grid and depth."""
+    from .workloads import spot_batch
+    sp = sorted(spot_batch(), key=lambda w: w.beam["e0"])
+    pick = sorted({round(i * (len(sp) - 1) / max(1, n - 1)) for i in range(n)})
+    rows = []
+    for i in pick:
+        w = sp[i]
+        beam = {k: v for k, v in w.beam.items() if k not in ("yc", "zc")}
+        w = w.with_(beam=beam)
+        mixed, dose, flu = march(binding, w, w.n_steps, "mixed", profile=False)
+        ref, dose64, flu64 = march(binding, w, w.n_steps, "fp64", profile=False)
+        rows.append({"spot": w.name, "e0": round(w.beam["e0"], 3), "lateral": w.ny, "groups": w.ng,
+                     "steps": w.n_steps, "mixed_cell_updates_per_s": mixed["cell_updates_per_s"],
+                     "fp64_cell_updates_per_s": ref["cell_updates_per_s"],
+                     "dose_err_vs_fp64": float(np.abs(dose - dose64).max() / np.abs(dose64).max()),
+                     "fluence_err_vs_fp64": float(np.abs(flu - flu64).max() / np.abs(flu64).max())})
+    return rows
+
+
 def main(argv=None):
     from . import binding
     from .workloads import WORKLOADS
@@ -89,7 +112,15 @@ def main(argv=None):
     p.add_argument("--no-profile", action="store_true", help="no per-kernel event pairs in the timed march")
     p.add_argument("--vs-fp64", action="store_true",
                    help="also march the same workload in FP64 and report the dose and fluence error against it")
+    p.add_argument("--spots-vs-fp64", type=int, default=0,
+                   help="mixed vs FP64 dose error of N spots of the batch, each on its own full grid")
     a = p.parse_args(argv)
+    if a.spots_vs_fp64:
+        import torch
+        torch.cuda.set_device(0)
+        for row in spots_vs_fp64(binding, a.spots_vs_fp64):
+            print(json.dumps(row), flush=True)
+        return
     if a.spots:
         out = run_spots(a)
         if out is not None:

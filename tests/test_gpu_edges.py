@@ -152,6 +152,74 @@ def test_checkpoint_resume(orc, precision):
         s.close()
 
 
+# byte offsets of fields in the checkpoint header: magic[8], then 4-byte ints
+# version, precision, ny, nz, ng, nu, nv, nx, K, B, steps_done, pending,
+# have_beam, n_slabs_at_save, angular, transport, straggling integrators, pad,
+# then the 8-byte table and material hashes
+_CK_STEPS, _CK_PENDING, _CK_HAVE_BEAM, _CK_ANGULAR = 48, 52, 56, 64
+
+
+def _put_int(buf, off, v):
+    out = buf.copy()
+    out[off:off + 4] = np.frombuffer(np.int32(v).tobytes(), dtype=np.uint8)
+    return out
+
+
+def test_checkpoint_rejects_inconsistent_headers():
+    """A checkpoint whose header cannot describe a marched state, or that was
+    marched with other options, tables or density, is refused before any
+    device work; the context stays usable and a good checkpoint still
+    restores."""
+    grid = _grid(6, 8, 4, 4, 12)
+    nx, dx = 4, 0.05
+    rho = np.random.default_rng(2).uniform(0.5, 1.5, size=(nx, 6, 8))
+    a = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision="fp64")
+    a.set_material(rho)
+    a.launch_beam(e0=40.0, sigma_e=1.0, sigma_y=0.25, sigma_z=0.25)
+    a.step(2)
+    ck = a.checkpoint()  # pending closing half of step 1
+    assert int(np.frombuffer(ck[_CK_PENDING:_CK_PENDING + 4].tobytes(), dtype=np.int32)[0]) == 1
+    b = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision="fp64")
+    b.set_material(rho)
+    bad = [
+        _put_int(_put_int(ck, _CK_STEPS, 0), _CK_PENDING, 1),   # deferred half with no marched step
+        _put_int(ck, _CK_PENDING, 2),                           # flag out of range
+        _put_int(ck, _CK_HAVE_BEAM, 7),
+        _put_int(ck, _CK_STEPS, nx + 1),                        # depth beyond the grid
+        _put_int(ck, _CK_STEPS, -1),
+        _put_int(ck, _CK_ANGULAR, 1),                           # marched with the exact angular integrator
+    ]
+    for i, buf in enumerate(bad):
+        with pytest.raises(binding.PbsError):
+            b.restore(buf)
+        assert b.depth == 0, i
+    # another density field
+    c = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision="fp64")
+    c.set_material(rho * 1.01)
+    with pytest.raises(binding.PbsError):
+        c.restore(ck)
+    # other options on the restoring side
+    b.set_options(angular_integrator="exact")
+    with pytest.raises(binding.PbsError):
+        b.restore(ck)
+    b.set_options(angular_integrator="cn")
+    # other tables (a different removal cross section)
+    t = a.tables()
+    d = binding.Solver(grid, nx=nx, dx=dx, n_scatter=1, precision="fp64")
+    d.set_tables(t["s_face"], t["ts"], t["sig"] * 2.0, 0.05, t["p2"])
+    d.set_material(rho)
+    with pytest.raises(binding.PbsError):
+        d.restore(ck)
+    # the good one restores and continues like the original
+    b.restore(ck)
+    assert b.depth == 2
+    a.step(2)
+    b.step(2)
+    assert _relerr(b.read_dose(), a.read_dose()) < 1e-12
+    for s in (a, b, c, d):
+        s.close()
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
 def test_maximum_group_count(orc, precision, tol):
     """ng = 2048, the largest group count the library accepts: the group table

@@ -67,7 +67,7 @@ def test_binding_structs_match_the_header(tmp_path):
 
     from paper_2504_00340_gb300 import binding as B
     structs = {"pbs_grid": B.PbsGrid, "pbs_physics": B.PbsPhysics, "pbs_beam": B.PbsBeam,
-               "pbs_options": B.PbsOptions, "pbs_tuning": B.PbsTuning}
+               "pbs_options": B.PbsOptions, "pbs_tuning": B.PbsTuning, "pbs_batch_options": B.PbsBatchOptions}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pbs.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
