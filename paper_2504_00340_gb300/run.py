@@ -3,6 +3,7 @@
     python -m paper_2504_00340_gb300.run --workload water150_128x128_g256_a16x16 \
         [--ny 64 --nz 64] [--ng G] [--steps N] [--precision fp32|fp64|mixed] [--autotune] [--vs-fp64]
     python -m paper_2504_00340_gb300.run --spots 256 [--max-gb 48] [--no-graph] [--no-autotune]
+    python -m paper_2504_00340_gb300.run --spots 256 --persistent [--no-graph]
     python -m paper_2504_00340_gb300.run --spots-vs-fp64 3
 
 Sizes may be overridden to make reduced cases of the same kernels (e.g. for
@@ -33,6 +34,17 @@ def run_spots(a) -> dict:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     sp = spot_batch()[:a.spots]
+    if a.persistent:
+        if world > 1:
+            raise SystemExit("--persistent runs on one GPU")
+        t0 = time.perf_counter()
+        doses, st = S.run_persistent(sp, use_graph=not a.no_graph,
+                                     max_bytes=int(a.max_gb * (1 << 30)) if a.max_gb_set else None)
+        useful = float(st["cell_updates"])
+        return {"spots": len(sp), "persistent_launches": st["launches"], "device_ms": st["device_ms"],
+                "wall_s": time.perf_counter() - t0, "cell_updates": useful,
+                "cell_updates_per_s": useful / (st["device_ms"] * 1e-3), "kernels": st["kernels"],
+                "graph": st["graph"], "max_dose": float(max(np.abs(d).max() for d in doses.values()))}
     t0 = time.perf_counter()
     doses, st = S.run_shard(sp, rank, world, max_bytes=int(a.max_gb * (1 << 30)), use_graph=not a.no_graph,
                             autotune=not a.no_autotune)
@@ -105,7 +117,11 @@ def main(argv=None):
     p.add_argument("--straggling-integrator", choices=["explicit", "cn"], default="explicit",
                    help="straggling inside the CN energy step explicitly (default) or in the CN step")
     p.add_argument("--spots", type=int, default=0, help="run the first N spots of the 256-spot batch")
-    p.add_argument("--max-gb", type=float, default=48.0, help="device workspace per spot bucket (GiB)")
+    p.add_argument("--max-gb", type=float, default=None,
+                   help="device workspace per spot bucket (GiB, default 48), or per persistent launch "
+                        "(default: the free device memory)")
+    p.add_argument("--persistent", action="store_true",
+                   help="--spots through the persistent batch launch (each spot on its own grid)")
     p.add_argument("--no-graph", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--autotune", action="store_true", help="autotune launch shapes before a workload march")
@@ -115,6 +131,9 @@ def main(argv=None):
     p.add_argument("--spots-vs-fp64", type=int, default=0,
                    help="mixed vs FP64 dose error of N spots of the batch, each on its own full grid")
     a = p.parse_args(argv)
+    a.max_gb_set = a.max_gb is not None
+    if a.max_gb is None:
+        a.max_gb = 48.0
     if a.spots_vs_fp64:
         import torch
         torch.cuda.set_device(0)

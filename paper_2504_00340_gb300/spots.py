@@ -218,5 +218,71 @@ def run_shard(spots: list[Workload], rank: int = 0, world_size: int = 1, *, max_
     return doses, stats
 
 
+def plan_waves(spots: list[Workload], max_bytes: int) -> list[list[int]]:
+    """Spots of the persistent batch, longest depth first (they lead every
+    round of the device queue), cut into waves whose workspaces fit
+    max_bytes together; each wave is one persistent launch (the whole batch
+    when it fits)."""
+    order = sorted(range(len(spots)), key=lambda i: (-spots[i].n_steps, i))
+    waves, cur, used = [], [], 0
+    for i in order:
+        w = spots[i]
+        b = workspace_bytes(w.ny, w.nz, w.nu, w.nv, w.ng, w.n_steps, w.n_scatter, 1, w.precision)
+        if b > max_bytes:
+            raise ValueError(f"spot {w.name} alone needs more than max_bytes")
+        if cur and used + b > max_bytes:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append(i)
+        used += b
+    if cur:
+        waves.append(cur)
+    return waves
+
+
+def run_persistent(spots: list[Workload], *, max_bytes: int | None = None, use_graph: bool = False):
+    """March the spots through the persistent batch (pbs_run_batch): every
+    spot its own context on its own grid (its own energy groups, no bucket
+    and no empty groups), as few launches as memory allows.  Returns
+    ({spot: dose [steps][ny][nz]}, stats with the device time of the timed
+    launches (CUDA events on the stream)."""
+    import torch
+
+    from . import binding
+    if max_bytes is None:
+        max_bytes = torch.cuda.mem_get_info()[0] - (6 << 30)
+    waves = plan_waves(spots, max_bytes)
+    doses: dict = {}
+    stats = dict(launches=len(waves), device_ms=0.0, kernels=0, cell_updates=useful_cost(spots),
+                 graph=use_graph)
+    for wave in waves:
+        solvers = []
+        try:
+            for i in wave:
+                w = spots[i]
+                s = binding.Solver(w.grid(), nx=w.n_steps, dx=w.dx, n_scatter=w.n_scatter, precision=w.precision,
+                                   physics=w.physics)
+                solvers.append(s)
+                s.set_material(w.density())
+                s.launch_beam(**{k: v for k, v in w.beam.items() if k not in ("yc", "zc")})
+            ws = binding.run_batch(solvers, use_graph=True) if use_graph else None  # records the graph
+            k0 = sum(s.kernel_launches for s in solvers)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(solvers[0].stream)
+            ws = binding.run_batch(solvers, use_graph=use_graph, workspace=ws)
+            e1.record(solvers[0].stream)
+            e1.synchronize()
+            stats["device_ms"] += e0.elapsed_time(e1)
+            stats["kernels"] += sum(s.kernel_launches for s in solvers) - k0
+            for s, i in zip(solvers, wave):
+                doses[i] = s.read_dose()
+        finally:
+            for s in solvers:
+                s.close()
+            torch.cuda.empty_cache()
+    return dict(sorted(doses.items())), stats
+
+
 __all__ = ["Bucket", "plan_buckets", "shard_buckets", "bucket_cost", "useful_cost", "workspace_bytes",
-           "bucket_grid", "run_bucket", "total_dose", "gather_doses", "run_shard"]
+           "bucket_grid", "run_bucket", "total_dose", "gather_doses", "run_shard", "plan_waves", "run_persistent"]
