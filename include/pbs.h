@@ -325,11 +325,22 @@ pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
  *                  starts afresh.
  *   hold_beam      failure-detection test hook (-1 in normal use): beam
  *                  hold_beam's second pass waits for one tile more than its
- *                  first pass has, so its waits can only run out. */
+ *                  first pass has, so its waits can only run out.
+ *   shape          CTA shape of the launch (same results, different speed):
+ *                  0  256 threads, two per SM (16-angle energy tiles, 4
+ *                     transport columns per lane);
+ *                  1  128 threads, three per SM (8-angle energy tiles, 4 or 6
+ *                     transport columns).
+ *   transport_cols 4 or 6 columns per lane of the transport tiles (6 only with
+ *                  shape 1 and rows that split evenly into 6-column lanes,
+ *                  else 4), or 0 for the default rule (6 where that fills the
+ *                  warps better).  pbs_batch_autotune picks shape and columns. */
 typedef struct {
   int use_graph;
   double wait_limit_ms;
   int hold_beam;
+  int shape;
+  int transport_cols;
 } pbs_batch_options;
 
 /* Bytes of the device workspace pbs_run_batch needs for these beams with
@@ -350,6 +361,16 @@ pbs_status pbs_batch_workspace_size(pbs_ctx *const *beams, int n_beams, size_t *
  * them per context). */
 pbs_status pbs_run_batch(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_t bytes,
                          const pbs_batch_options *opts);
+
+/* Batch autotuner: times the CTA shapes and transport column counts of
+ * pbs_batch_options (best of two trials each) on the batch with every beam
+ * cut to at most `steps` depth steps, with CUDA events on the beams' stream,
+ * and writes the fastest into opts->shape and opts->transport_cols (the
+ * other fields are kept).  The trials march the beams, so they restart from
+ * their projections afterwards.  dev_ws as for pbs_run_batch.
+ * Synchronises. */
+pbs_status pbs_batch_autotune(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_t bytes, int steps,
+                              pbs_batch_options *opts);
 
 /* Method options (each changes the computed result, unlike pbs_tuning):
  *   angular_integrator    time integration of each sine mode of the angular
@@ -518,14 +539,22 @@ typedef enum {
   PBS_KERNEL_TRANSPORT = 1,  /* lateral transport substep                    */
   PBS_KERNEL_ANGULAR = 2,    /* angular substep                              */
   PBS_KERNEL_SOURCE = 3,     /* catastrophic-source angle contraction        */
-  PBS_KERNEL_KINDS = 4
+  PBS_KERNEL_QUEUE = 4,      /* persistent batch: claiming tiles and waiting
+                                for a beam's earlier passes                 */
+  PBS_KERNEL_KINDS = 5
 } pbs_kernel_kind;
 
 /* Per-kernel timing.  pbs_set_profiling(ctx, 1) clears the totals and makes
  * every later kernel launch of the march be bracketed by a CUDA event pair
  * recorded on the context's stream (0 stops recording).  pbs_profile_read
  * synchronises the stream and returns, for one pbs_kernel_kind, the number of
- * launches timed and their summed device time in milliseconds. */
+ * launches timed and their summed device time in milliseconds.  A persistent
+ * batch (pbs_run_batch) led by a profiling context is one launch, so its time
+ * is split by tile kind instead: the kernel sums the SM clocks its CTAs spend
+ * in energy, transport and angular tiles and in claiming and waiting
+ * (PBS_KERNEL_QUEUE), and pbs_profile_read reports, per kind, the tiles run
+ * and those clocks per CTA converted to milliseconds at the device's
+ * nominal SM clock (kinds sum to about the launch's duration). */
 pbs_status pbs_set_profiling(pbs_ctx *ctx, int on);
 pbs_status pbs_profile_read(pbs_ctx *ctx, int kind, long long *launches, double *total_ms);
 

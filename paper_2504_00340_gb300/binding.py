@@ -60,7 +60,8 @@ class PbsOptions(ctypes.Structure):
 
 
 class PbsBatchOptions(ctypes.Structure):
-    _fields_ = [("use_graph", ctypes.c_int), ("wait_limit_ms", ctypes.c_double), ("hold_beam", ctypes.c_int)]
+    _fields_ = [("use_graph", ctypes.c_int), ("wait_limit_ms", ctypes.c_double), ("hold_beam", ctypes.c_int),
+                ("shape", ctypes.c_int), ("transport_cols", ctypes.c_int)]
 
 
 class PbsError(RuntimeError):
@@ -98,6 +99,8 @@ SIGNATURES = [
     ("pbs_batch_workspace_size", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
     ("pbs_run_batch", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_size_t,
                                      ctypes.POINTER(PbsBatchOptions)]),
+    ("pbs_batch_autotune", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_size_t, ctypes.c_int,
+                                          ctypes.POINTER(PbsBatchOptions)]),
     ("pbs_get_depth", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     ("pbs_checkpoint_size", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
     ("pbs_checkpoint_save", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
@@ -283,10 +286,21 @@ def pbs_batch_workspace_size(ctxs) -> int:
 
 
 def pbs_run_batch(ctxs, dev_ptr: int, nbytes: int, use_graph: bool = False, wait_limit_ms: float = 0.0,
-                  hold_beam: int = -1) -> None:
+                  hold_beam: int = -1, shape: int = 0, transport_cols: int = 0) -> None:
     arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
-    opts = PbsBatchOptions(int(bool(use_graph)), float(wait_limit_ms), int(hold_beam))
+    opts = PbsBatchOptions(int(bool(use_graph)), float(wait_limit_ms), int(hold_beam), int(shape),
+                           int(transport_cols))
     _check(ctxs[0], load_library().pbs_run_batch(arr, len(ctxs), _VP(dev_ptr), nbytes, ctypes.byref(opts)))
+
+
+def pbs_batch_autotune(ctxs, dev_ptr: int, nbytes: int, steps: int = 6) -> dict:
+    """The batch shape and transport columns the autotuner picks (see
+    pbs_batch_autotune); the beams restart from their projections."""
+    arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
+    opts = PbsBatchOptions(0, 0.0, -1, 0, 0)
+    _check(ctxs[0], load_library().pbs_batch_autotune(arr, len(ctxs), _VP(dev_ptr), nbytes, int(steps),
+                                                      ctypes.byref(opts)))
+    return {"shape": opts.shape, "transport_cols": opts.transport_cols}
 
 
 def pbs_checkpoint_size(ctx) -> int:
@@ -362,7 +376,7 @@ def pbs_kernel_launches(ctx) -> int:
     return n.value
 
 
-KERNEL_KINDS = {"energy": 0, "transport": 1, "angular": 2, "source": 3}
+KERNEL_KINDS = {"energy": 0, "transport": 1, "angular": 2, "source": 3, "queue": 4}
 
 
 def pbs_set_profiling(ctx, on: bool) -> None:
@@ -392,18 +406,30 @@ _BEAM_DEFAULTS = dict(e0=100.0, sigma_e=1.0, y0=0.0, z0=0.0, sigma_y=0.3, sigma_
                       sigma_u=1e-6, sigma_v=1e-6)
 
 
-def run_batch(solvers, use_graph: bool = False, wait_limit_ms: float = 0.0, hold_beam: int = -1, workspace=None):
+def _batch_workspace(solvers, workspace):
+    import torch
+    nbytes = pbs_batch_workspace_size([s.ctx for s in solvers])
+    if workspace is None or workspace.numel() < nbytes:
+        workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
+    return workspace
+
+
+def run_batch(solvers, use_graph: bool = False, wait_limit_ms: float = 0.0, hold_beam: int = -1, workspace=None,
+              shape: int = 0, transport_cols: int = 0):
     """March every Solver of the list (one beam each, see pbs_run_batch) in
     one persistent launch on their common stream.  The batch workspace is a
     torch tensor allocated here unless given (keep it alive while the batch
     runs: it is returned)."""
-    import torch
-    ctxs = [s.ctx for s in solvers]
-    nbytes = pbs_batch_workspace_size(ctxs)
-    if workspace is None or workspace.numel() < nbytes:
-        workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device="cuda")
-    pbs_run_batch(ctxs, workspace.data_ptr(), workspace.numel(), use_graph, wait_limit_ms, hold_beam)
+    workspace = _batch_workspace(solvers, workspace)
+    pbs_run_batch([s.ctx for s in solvers], workspace.data_ptr(), workspace.numel(), use_graph, wait_limit_ms,
+                  hold_beam, shape, transport_cols)
     return workspace
+
+
+def autotune_batch(solvers, steps: int = 6, workspace=None):
+    """(options picked by pbs_batch_autotune, workspace)."""
+    workspace = _batch_workspace(solvers, workspace)
+    return pbs_batch_autotune([s.ctx for s in solvers], workspace.data_ptr(), workspace.numel(), steps), workspace
 
 
 class Solver:

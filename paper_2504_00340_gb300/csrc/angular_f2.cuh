@@ -151,6 +151,87 @@ __device__ __forceinline__ void angular_f2_tile(float *__restrict__ psi, const f
   }
 }
 
+// R slab stacks kgc0 + r * kstride (r < R; those >= nkgc are skipped) at one
+// lateral block, each exactly as angular_f2_tile, interleaved phase by phase
+// so that the loads of the R stacks are in flight together (latency hidden
+// by independent work instead of by more resident warps).  smem_raw holds R
+// tiles.
+template <int NU, int NV, bool EXACT, int R>
+__device__ __forceinline__ void angular_f2_tiles(float *__restrict__ psi, const float *__restrict__ rho_yz,
+                                                 const float *__restrict__ ts, int nyz, int ng, float hq,
+                                                 long long kgc0, long long kstride, long long nkgc, int bx, int x,
+                                                 int t, unsigned char *smem_raw, const AngTables<float> &tb) {
+  constexpr int NA = NU * NV;
+  const int yz = (bx * kF2X + x) * 2;
+  float *base[R];
+  bool active[R];
+  float2(*tile[R])[kF2X];
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    const long long kgc = kgc0 + r * kstride;
+    active[r] = yz < nyz && kgc < nkgc;
+    base[r] = psi + (active[r] ? kgc : 0) * (long long)NA * nyz + yz;
+    tile[r] = reinterpret_cast<float2(*)[kF2X]>(smem_raw + (size_t)r * sizeof(float2) * NA * kF2X);
+  }
+  if (t < NV) {
+    float2 rr[R][NU];
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+      for (int i = 0; i < NU; i++)
+        rr[r][i] = active[r] ? *reinterpret_cast<const float2 *>(base[r] + (long long)(t * NU + i) * nyz)
+                             : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      float2 y[NU];
+      dst_apply2<NU>(rr[r], y);
+#pragma unroll
+      for (int i = 0; i < NU; i++) tile[r][t * NU + i][x] = y[i];
+    }
+  }
+  __syncthreads();
+  if (t < NU) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const long long kgc = kgc0 + r * kstride;
+      const int g = (int)(((kgc < nkgc ? kgc : 0) / 2) % ng);
+      float2 q = make_float2(0.f, 0.f);
+      if (active[r]) {
+        const float2 rh = *reinterpret_cast<const float2 *>(rho_yz + yz);
+        const float w = hq * ts[g];
+        q = make_float2(w * rh.x, w * rh.y);  // h kappa / 4
+      }
+      float2 c[NV], y[NV];
+#pragma unroll
+      for (int j = 0; j < NV; j++) c[j] = tile[r][j * NU + t][x];
+      dst_apply2<NV>(c, y);
+#pragma unroll
+      for (int n = 0; n < NV; n++) {
+        const float l = tb.lam[n * NU + t];
+        y[n].x *= mode_scale<EXACT>(q.x * l);
+        y[n].y *= mode_scale<EXACT>(q.y * l);
+      }
+      dst_apply2<NV>(y, c);
+#pragma unroll
+      for (int j = 0; j < NV; j++) tile[r][j * NU + t][x] = c[j];
+    }
+  }
+  __syncthreads();
+  if (t < NV) {
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      float2 rr[NU], y[NU];
+#pragma unroll
+      for (int i = 0; i < NU; i++) rr[i] = tile[r][t * NU + i][x];
+      dst_apply2<NU>(rr, y);
+      if (active[r]) {
+#pragma unroll
+        for (int i = 0; i < NU; i++) *reinterpret_cast<float2 *>(base[r] + (long long)(t * NU + i) * nyz) = y[i];
+      }
+    }
+  }
+}
+
 }  // namespace ang
 }  // namespace
 }  // namespace pbs

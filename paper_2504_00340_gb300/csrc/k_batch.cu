@@ -32,11 +32,43 @@ namespace pbs {
 
 namespace {
 
-constexpr int kBThreads = 128;  // the energy block (32 x 4), the angular block (16 x 8), four transport warps
-constexpr int kBWarps = kBThreads / 32;
-constexpr int kBKV = 4;         // transport columns per lane
-constexpr int kBEnergyY = 4;    // energy block rows: 8 angles per block
-constexpr int kBAngRep = 16;    // angular slab stacks per tile
+// CTA shapes (pbs_batch_options.shape), both 16 warps' worth of work per SM:
+//   0  256 threads, two CTAs per SM at 128 registers: an energy block of
+//      32 x 8 threads (16 angles x 64 lateral points), eight transport warps
+//      (4 columns per lane), two angular sub-blocks of 16 x 8;
+//   1  128 threads, three CTAs per SM at up to 170 registers: an energy block
+//      of 32 x 4 (8 angles), four transport warps (4 or 6 columns: the
+//      6-column march needs ~144 registers), one angular sub-block.
+// The angular tile needs few registers but many loads in flight, so each
+// sub-block works on four independent slab stacks at a time.
+template <int SHAPE>
+struct BShape {
+  static constexpr int kThreads = SHAPE == 0 ? 256 : 128;
+  static constexpr int kMinBlocks = SHAPE == 0 ? 2 : 3;
+  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kEnergyY = kThreads / 32;
+  static constexpr int kAngSub = kThreads / 128;  // angular sub-blocks of 16 x 8
+};
+constexpr int kBAngR = 4;       // slab stacks at a time per angular sub-block
+constexpr int kBAngRep = 32;    // angular slab stacks per tile
+
+// Ask the L2 for the rows of R slab stacks kgc0 + r (r < R, those < nkgc) at
+// lateral block bx: one hint per 128-byte line (16 threads share a line).
+template <int NU, int NV, int R>
+__device__ __forceinline__ void prefetch_stacks(const float *psi, int nyz, long long kgc0, long long nkgc, int bx,
+                                                int x, int t) {
+  if (x != 0 || t >= NV) return;
+  const int yz = bx * ang::kF2X * 2;
+  if (yz >= nyz) return;
+#pragma unroll
+  for (int r = 0; r < R; r++) {
+    if (kgc0 + r >= nkgc) break;
+    const float *base = psi + (kgc0 + r) * (long long)(NU * NV) * nyz + yz;
+#pragma unroll
+    for (int i = 0; i < NU; i++)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (long long)(t * NU + i) * nyz));
+  }
+}
 
 // Pass kinds of a beam's chain.
 enum : int { kPassEOpen = 0, kPassEPair = 1, kPassEClose = 2, kPassT = 3, kPassA = 4 };
@@ -73,9 +105,10 @@ __device__ void batch_abort(const BatchBeam *beams, int nbeams, int *abort_word,
   }
 }
 
-template <int NU, int NV>
+template <int NU, int NV, int SHAPE>
 __device__ __forceinline__ void run_tile(const BatchBeam &bm, int kind, int step, long long tile, unsigned char *smem,
                                          const ang::AngTables<float> &tb) {
+  using S = BShape<SHAPE>;
   const Dims &d = bm.d;
   const int tid = threadIdx.x;
   const size_t nyz = (size_t)d.nyz;
@@ -87,13 +120,13 @@ __device__ __forceinline__ void run_tile(const BatchBeam &bm, int kind, int step
     // fluence after the closing half
     const int sa = kind == kPassEOpen ? 0 : step - 1;
     if (kind == kPassEPair) {
-      en::energy_f2_tile<float, false, false, true, kBEnergyY>(
+      en::energy_f2_tile<float, false, false, true, S::kEnergyY>(
           bx, by, 0, tid & 31, tid >> 5, smem, d, bm.psi, nullptr, nullptr, nullptr, nullptr, bm.rho + sa * nyz,
           bm.rho + (size_t)step * nyz, bm.coef, bm.dose + sa * nyz, bm.dose + (size_t)step * nyz,
           bm.flu + (size_t)step * nyz, bm.c, bm.c, bm.dose_scale, bm.flu_scale, bs);
     } else {
       double *flu = kind == kPassEClose ? bm.flu + (size_t)bm.n_steps * nyz : nullptr;
-      en::energy_f2_tile<float, false, false, false, kBEnergyY>(
+      en::energy_f2_tile<float, false, false, false, S::kEnergyY>(
           bx, by, 0, tid & 31, tid >> 5, smem, d, bm.psi, nullptr, nullptr, nullptr, nullptr, bm.rho + sa * nyz,
           nullptr, bm.coef, bm.dose + sa * nyz, nullptr, flu, bm.c, bm.c, bm.dose_scale, bm.flu_scale, bs);
     }
@@ -106,38 +139,51 @@ __device__ __forceinline__ void run_tile(const BatchBeam &bm, int kind, int step
     const int a0 = fz ? a_split : 0, na_half = fz ? d.na - a_split : a_split;
     float *psi = bm.psi + stack * (long long)d.na * d.nyz;
     const int lane = tid & 31, warp = tid >> 5;
-    float *ring = reinterpret_cast<float *>(smem) + (size_t)warp * tr::kR * 32 * kBKV;
-    if (fz)
-      tr::transport_tasks<float, true, true, kBKV, false>(psi, na_half, d.ny, d.nz, d.na, a0, na_half, d.nu, d.nv,
-                                                          bm.du, bm.dv, bm.ky, bm.kz, bm.tr_nseg, bm.tr_segw,
-                                                          bm.tr_gw, lane, warp, kBWarps, ring, tr::NoCnMarch{});
-    else
-      tr::transport_tasks<float, true, false, kBKV, false>(psi, na_half, d.ny, d.nz, d.na, a0, na_half, d.nu, d.nv,
-                                                           bm.du, bm.dv, bm.ky, bm.kz, bm.tr_nseg, bm.tr_segw,
-                                                           bm.tr_gw, lane, warp, kBWarps, ring, tr::NoCnMarch{});
+#define PBS_BT(KV, FZ)                                                                                            \
+  tr::transport_tasks<float, true, FZ, KV, false>(psi, na_half, d.ny, d.nz, d.na, a0, na_half, d.nu, d.nv, bm.du, \
+                                                  bm.dv, bm.ky, bm.kz, bm.tr_nseg, bm.tr_segw, bm.tr_gw, lane,   \
+                                                  warp, S::kWarps,                                                \
+                                                  reinterpret_cast<float *>(smem) + (size_t)warp * tr::kR * 32 * KV, \
+                                                  tr::NoCnMarch{})
+    if (SHAPE == 1 && bm.tr_kv == 6) {
+      if (fz) PBS_BT(6, true); else PBS_BT(6, false);
+    } else {
+      if (fz) PBS_BT(4, true); else PBS_BT(4, false);
+    }
+#undef PBS_BT
   } else {  // kPassA: kBAngRep consecutive slab stacks at one lateral block
     const int bx = (int)(tile % bm.a_bx);
     const long long k0 = (tile / bm.a_bx) * kBAngRep;
     const long long nkgc = (long long)d.ncomp * d.ng * 2;
-    for (int r = 0; r < kBAngRep && k0 + r < nkgc; r++) {
-      ang::angular_f2_tile<NU, NV, false>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq, k0 + r, bx,
-                                         tid & 15, tid >> 4, smem, tb);
-      __syncthreads();  // the next stack reuses the shared tile
+    constexpr int kPer = S::kAngSub * kBAngR;  // stacks per round of the CTA
+    const int sub = tid >> 7;
+    unsigned char *sm = smem + (size_t)sub * kBAngR * sizeof(float2) * NU * NV * ang::kF2X;
+    for (int it = 0; it < kBAngRep / kPer && k0 + kPer * it < nkgc; it++) {
+      // the next round's rows travel to the L2 while this round computes
+      if (it + 1 < kBAngRep / kPer)
+        prefetch_stacks<NU, NV, kBAngR>(bm.psi, d.nyz, k0 + kPer * (it + 1) + kBAngR * sub, nkgc, bx, tid & 15,
+                                        (tid >> 4) & 7);
+      ang::angular_f2_tiles<NU, NV, false, kBAngR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
+                                                   k0 + kPer * it + kBAngR * sub, 1, nkgc, bx, tid & 15,
+                                                   (tid >> 4) & 7, sm, tb);
+      __syncthreads();  // the next stacks reuse the shared tiles
     }
   }
 }
 
-template <int NU, int NV>
-__global__ void __launch_bounds__(kBThreads, 4)
+template <int NU, int NV, int SHAPE>
+__global__ void __launch_bounds__(BShape<SHAPE>::kThreads, BShape<SHAPE>::kMinBlocks)
     k_batch(const BatchBeam *__restrict__ beams, int nbeams, const BatchTask *__restrict__ tasks, int ntasks,
             BatchQueue *q, unsigned long long *done_ctr, unsigned long long *next_ctr, long long wait_cycles,
-            const __grid_constant__ ang::AngTables<float> tb) {
+            unsigned long long *prof, const __grid_constant__ ang::AngTables<float> tb) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_task, s_go;
   __shared__ long long s_tile;
   const int tid = threadIdx.x;
+  long long t_claim = 0, t_start = 0;
   for (;;) {
     if (tid == 0) {
+      if (prof) t_claim = clock64();
       int go = 0, t = 0;
       long long tile = 0;
       for (;;) {
@@ -175,38 +221,50 @@ __global__ void __launch_bounds__(kBThreads, 4)
       s_task = t;
       s_tile = tile;
       s_go = go;
+      if (prof) {
+        t_start = clock64();
+        atomicAdd(&prof[3], (unsigned long long)(t_start - t_claim));
+      }
     }
     __syncthreads();
     if (!s_go) break;
     const BatchTask tk = tasks[s_task];
     const BatchBeam &bm = beams[tk.beam];
-    run_tile<NU, NV>(bm, pass_kind(tk.pass, bm.n_steps), tk.pass >> 2, s_tile, smem, tb);
+    const int kind = pass_kind(tk.pass, bm.n_steps);
+    run_tile<NU, NV, SHAPE>(bm, kind, tk.pass >> 2, s_tile, smem, tb);
     __syncthreads();  // every thread's writes of this tile are done
     if (tid == 0) {
       __threadfence();
       atomicAdd(&done_ctr[tk.beam], 1ULL);
+      if (prof) {
+        const int k = kind == kPassT ? 1 : (kind == kPassA ? 2 : 0);
+        atomicAdd(&prof[k], (unsigned long long)(clock64() - t_start));
+        atomicAdd(&prof[4 + k], 1ULL);
+      }
     }
   }
 }
 
-template <int NU, int NV>
+template <int NU, int NV, int SHAPE>
 cudaError_t go_batch(const LaunchCtx &lc, const BatchBeam *beams, int nbeams, const BatchTask *tasks, int ntasks,
                      BatchQueue *q, unsigned long long *done, unsigned long long *next, long long wait_cycles,
-                     size_t smem, double du, double dv) {
-  auto kern = k_batch<NU, NV>;
+                     size_t smem, double du, double dv, unsigned long long *prof, int *ctas) {
+  auto kern = k_batch<NU, NV, SHAPE>;
+  constexpr int kThreads = BShape<SHAPE>::kThreads;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBThreads, smem)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   ang::AngTables<float> tb;
   ang::fill_tables(tb, NU, NV, du, dv);
   // A CTA only ever waits for tiles that left the queue before its own, that
   // is, for tiles held by CTAs already running: the launch needs no
   // co-residency guarantee (and so stays capturable in a graph).
-  kern<<<(unsigned)(per_sm * lc.num_sms), kBThreads, smem, lc.stream>>>(beams, nbeams, tasks, ntasks, q, done, next,
-                                                                        wait_cycles, tb);
+  *ctas = per_sm * lc.num_sms;
+  kern<<<(unsigned)(per_sm * lc.num_sms), kThreads, smem, lc.stream>>>(beams, nbeams, tasks, ntasks, q, done, next,
+                                                                        wait_cycles, prof, tb);
   ++*lc.launches;
   return cudaGetLastError();
 }
@@ -215,45 +273,71 @@ cudaError_t go_batch(const LaunchCtx &lc, const BatchBeam *beams, int nbeams, co
 
 cudaError_t batch_init_tables() { return ang::upload_dst_f2(); }
 
-BatchShape batch_shape(const Dims &d) {
+// Transport columns per lane of a beam: want = 4 or 6 (6 where rows split
+// evenly into 6-column lanes, else 4), or 0 for the per-substep kernel's
+// default rule: 6 where that fills the warps better than 4.
+static int batch_kv(int nz, int want, int &nseg, int &seg_w, int &gw) {
+  auto use = [&](int kv, int &ns, int &sw, int &g) {
+    int lanes;
+    if (nz <= 32 * kv) {
+      ns = 1;
+      sw = nz;
+      lanes = (nz + kv - 1) / kv;
+    } else {  // rows cut into segments as in the per-substep kernel
+      const int wmax = (32 - 2) * kv;
+      ns = (nz + wmax - 1) / wmax;
+      sw = ((nz + ns - 1) / ns + kv - 1) / kv * kv;
+      lanes = sw / kv + 2;
+    }
+    g = 1;
+    while (g < lanes) g <<= 1;
+    return (double)nz / ((double)ns * g * kv);
+  };
+  int n4, s4, g4, n6 = 1, s6 = 0, g6 = 1;
+  const double u4 = use(4, n4, s4, g4);
+  const double u6 = (want != 4 && nz % 6 == 0) ? use(6, n6, s6, g6) : 0.0;
+  if (want == 6 ? u6 > 0.0 : (want == 0 && u6 > u4 + 0.05)) {
+    nseg = n6; seg_w = s6; gw = g6;
+    return 6;
+  }
+  nseg = n4; seg_w = s4; gw = g4;
+  return 4;
+}
+
+BatchShape batch_shape(const Dims &d, int shape, int cols) {
   BatchShape s{};
+  const int threads = shape == 0 ? BShape<0>::kThreads : BShape<1>::kThreads;
+  const int ey = threads / 32, warps = threads / 32, asub = threads / 128;
   s.e_bx = (d.nyz / 2 + en::kX - 1) / en::kX;
-  s.e_by = (d.na + kBEnergyY * en::kA - 1) / (kBEnergyY * en::kA);
+  s.e_by = (d.na + ey * en::kA - 1) / (ey * en::kA);
   s.e_tiles = (long long)s.e_bx * s.e_by;
   s.tr_stacks = (long long)d.ncomp * d.ng * 2;
   s.t_tiles = 2 * s.tr_stacks;
-  int nseg, seg_w, lanes;
-  nseg = 1;
-  seg_w = d.nz;
-  lanes = (d.nz + kBKV - 1) / kBKV;
-  if (d.nz > 32 * kBKV) {  // rows cut into segments as in the per-substep kernel
-    const int wmax = (32 - 2) * kBKV;
-    nseg = (d.nz + wmax - 1) / wmax;
-    seg_w = ((d.nz + nseg - 1) / nseg + kBKV - 1) / kBKV * kBKV;
-    lanes = seg_w / kBKV + 2;
-  }
-  int gw = 1;
-  while (gw < lanes) gw <<= 1;
-  s.tr_nseg = nseg;
-  s.tr_segw = seg_w;
-  s.tr_gw = gw;
+  // 6 columns only on the shape with the registers for it, and where rows
+  // split evenly into 6-column lanes
+  const int want = shape == 1 ? cols : 4;
+  s.tr_kv = batch_kv(d.nz, want, s.tr_nseg, s.tr_segw, s.tr_gw);
   s.a_bx = (d.nyz / 2 + ang::kF2X - 1) / ang::kF2X;
   s.a_tiles = (long long)s.a_bx * (((long long)d.ncomp * d.ng * 2 + kBAngRep - 1) / kBAngRep);
   s.smem = std::max(sizeof(en::GroupPair) * (size_t)d.ng,
-                    std::max((size_t)kBWarps * tr::kR * 32 * kBKV * sizeof(float),
-                             sizeof(float2) * (size_t)d.nu * d.nv * ang::kF2X));
+                    std::max((size_t)warps * tr::kR * 32 * s.tr_kv * sizeof(float),
+                             (size_t)asub * kBAngR * sizeof(float2) * (size_t)d.nu * d.nv * ang::kF2X));
   return s;
 }
 
-bool batch_supported(int nu, int nv) { return nu <= 8 && nv <= 8 && angular_supported(nu, nv); }
+bool batch_supported(int nu, int nv) { return nu == nv && nu <= 8 && angular_supported(nu, nv); }
 
-cudaError_t launch_batch(const LaunchCtx &lc, int nu, int nv, const BatchBeam *beams, int nbeams,
+cudaError_t launch_batch(const LaunchCtx &lc, int shape, int nu, int nv, const BatchBeam *beams, int nbeams,
                          const BatchTask *tasks, int ntasks, BatchQueue *q, unsigned long long *done,
-                         unsigned long long *next, long long wait_cycles, size_t smem, double du, double dv) {
-#define PBS_B(A, B)                                                                                              \
-  if (nu == A && nv == B)                                                                                        \
-    return go_batch<A, B>(lc, beams, nbeams, tasks, ntasks, q, done, next, wait_cycles, smem, du, dv);
-  PBS_B(2, 2) PBS_B(4, 4) PBS_B(6, 6) PBS_B(8, 8) PBS_B(4, 8) PBS_B(8, 4) PBS_B(6, 4) PBS_B(4, 6)
+                         unsigned long long *next, long long wait_cycles, size_t smem, double du, double dv,
+                         unsigned long long *prof, int *ctas) {
+#define PBS_B(A, B)                                                                                           \
+  if (nu == A && nv == B)                                                                                     \
+    return shape == 0 ? go_batch<A, B, 0>(lc, beams, nbeams, tasks, ntasks, q, done, next, wait_cycles, smem, \
+                                          du, dv, prof, ctas)                                                 \
+                      : go_batch<A, B, 1>(lc, beams, nbeams, tasks, ntasks, q, done, next, wait_cycles, smem, \
+                                          du, dv, prof, ctas);
+  PBS_B(2, 2) PBS_B(4, 4) PBS_B(6, 6) PBS_B(8, 8)
 #undef PBS_B
   return cudaErrorNotSupported;
 }

@@ -62,6 +62,9 @@ struct pbs_ctx {
   unsigned long long batch_key = 0;
   cudaGraphExec_t batch_graph = nullptr;
   long long batch_graph_kernels = 0;
+  // tile-kind clocks of the last profiled batch (device counters, not yet folded)
+  const unsigned long long *batch_prof = nullptr;
+  int batch_ctas = 0;
   unsigned long long material_hash = 0;  // FNV-1a of the density last set (checkpoint consistency)
   int n_slabs = 0;
   int steps_done = 0;
@@ -224,6 +227,19 @@ struct ProfScope {
 };
 
 pbs_status fold_profile(pbs_ctx *c) {
+  if (c->batch_prof) {  // a profiled persistent batch: its tile-kind clocks per CTA
+    unsigned long long v[8] = {};
+    PBS_CUDA(c, cudaMemcpyAsync(v, c->batch_prof, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+    PBS_CUDA(c, cudaStreamSynchronize(c->stream));
+    int khz = 0;
+    if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->dev) != cudaSuccess || khz <= 0) khz = 2000000;
+    const int kinds[4] = {PBS_KERNEL_ENERGY, PBS_KERNEL_TRANSPORT, PBS_KERNEL_ANGULAR, PBS_KERNEL_QUEUE};
+    for (int k = 0; k < 4; k++) {
+      c->prof_ms[kinds[k]] += (double)v[k] / ((double)c->batch_ctas * khz);
+      if (k < 3) c->prof_count[kinds[k]] += (long long)v[4 + k];
+    }
+    c->batch_prof = nullptr;
+  }
   if (c->recs.empty()) return PBS_OK;
   PBS_CUDA(c, cudaStreamSynchronize(c->stream));
   for (auto &r : c->recs) {
@@ -1207,14 +1223,21 @@ namespace {
 int beam_passes(int steps) { return steps > 0 ? 4 * steps + 1 : 0; }
 
 struct BatchLayout {
-  size_t off_beams, off_tasks, off_queue, off_done, off_next, total;
+  size_t off_beams, off_tasks, off_queue, off_done, off_next, off_prof, total;
   long long ntasks;
 };
 
-BatchLayout batch_layout(pbs_ctx *const *P, int n) {
+// Depth a beam marches in the batch: its own, or at most max_steps (>= 0)
+// for the autotuner's short trials.
+int batch_depth(const pbs_ctx *c, int max_steps) {
+  const int d = beam_depth(c, 0);
+  return max_steps >= 0 ? std::min(d, max_steps) : d;
+}
+
+BatchLayout batch_layout(pbs_ctx *const *P, int n, int max_steps = -1) {
   BatchLayout L{};
   long long nt = 0;
-  for (int i = 0; i < n; i++) nt += beam_passes(beam_depth(P[i], 0));
+  for (int i = 0; i < n; i++) nt += beam_passes(batch_depth(P[i], max_steps));
   L.ntasks = nt;
   size_t o = 0;
   L.off_beams = o; o = align256(o + sizeof(BatchBeam) * (size_t)n);
@@ -1222,6 +1245,7 @@ BatchLayout batch_layout(pbs_ctx *const *P, int n) {
   L.off_queue = o; o = align256(o + sizeof(BatchQueue));
   L.off_done = o; o = align256(o + 8 * (size_t)n);
   L.off_next = o; o = align256(o + 8 * (size_t)nt);
+  L.off_prof = o; o = align256(o + 8 * 8);
   L.total = o;
   return L;
 }
@@ -1231,7 +1255,7 @@ BatchLayout batch_layout(pbs_ctx *const *P, int n) {
 // context, the default integrators, no straggling, even ny*nz, rows a
 // multiple of 4 columns, angle grids of at most 8 x 8 shared by the batch,
 // all contexts on one device and stream, launched and not mid-step.
-pbs_status batch_check(pbs_ctx *const *P, int n) {
+pbs_status batch_check(pbs_ctx *const *P, int n, const pbs_batch_options &opt) {
   pbs_ctx *c0 = P[0];
   for (int i = 0; i < n; i++) {
     pbs_ctx *c = P[i];
@@ -1248,14 +1272,16 @@ pbs_status batch_check(pbs_ctx *const *P, int n) {
       return fail(c0, PBS_ERR_ARG, "the beams of a batch share one angle grid");
     for (int j = 0; j < i; j++)
       if (P[j] == c) return fail(c0, PBS_ERR_ARG, "a context appears twice in the batch");
-    if (batch_shape(c->d).smem > 160 * 1024) return fail(c0, PBS_ERR_UNSUPPORTED, "too many energy groups for the batch");
+    if (batch_shape(c->d, opt.shape, opt.transport_cols).smem > 160 * 1024)
+      return fail(c0, PBS_ERR_UNSUPPORTED, "too many energy groups for the batch");
   }
   return PBS_OK;
 }
 
 // Descriptors of the batch (beams, round-robin task list) in host memory.
-void batch_descriptors(pbs_ctx *const *P, int n, const BatchLayout &L, int hold_beam, std::vector<BatchBeam> &beams,
-                       std::vector<BatchTask> &tasks, size_t &smem) {
+void batch_descriptors(pbs_ctx *const *P, int n, const BatchLayout &L, const pbs_batch_options &opt, int max_steps,
+                       std::vector<BatchBeam> &beams, std::vector<BatchTask> &tasks, size_t &smem) {
+  const int hold_beam = opt.hold_beam;
   beams.assign(n, BatchBeam{});
   tasks.clear();
   tasks.reserve((size_t)L.ntasks);
@@ -1264,7 +1290,7 @@ void batch_descriptors(pbs_ctx *const *P, int n, const BatchLayout &L, int hold_
   int max_passes = 0;
   for (int b = 0; b < n; b++) {
     pbs_ctx *c = P[b];
-    const BatchShape sh = batch_shape(c->d);
+    const BatchShape sh = batch_shape(c->d, opt.shape, opt.transport_cols);
     shape[b] = sh;
     smem = std::max(smem, sh.smem);
     BatchBeam &m = beams[b];
@@ -1276,7 +1302,7 @@ void batch_descriptors(pbs_ctx *const *P, int n, const BatchLayout &L, int hold_
     m.flu = at<double>(c, c->off_flu);
     m.err = at<int>(c, c->off_err);
     m.d = c->d;
-    m.n_steps = beam_depth(c, 0);
+    m.n_steps = batch_depth(c, max_steps);
     // the constants of the per-substep launches, rounded the same way
     const double h = 0.5 * c->dx;
     m.c = (float)(0.5 * h);
@@ -1289,6 +1315,7 @@ void batch_descriptors(pbs_ctx *const *P, int n, const BatchLayout &L, int hold_
     m.flu_scale = c->du * c->dv;
     m.e_bx = sh.e_bx;
     m.a_bx = sh.a_bx;
+    m.tr_kv = sh.tr_kv;
     m.tr_nseg = sh.tr_nseg;
     m.tr_segw = sh.tr_segw;
     m.tr_gw = sh.tr_gw;
@@ -1308,8 +1335,13 @@ void batch_descriptors(pbs_ctx *const *P, int n, const BatchLayout &L, int hold_
     }
 }
 
-unsigned long long batch_key(pbs_ctx *const *P, int n, void *ws, size_t bytes, long long wait_cycles, int hold) {
+unsigned long long batch_key(pbs_ctx *const *P, int n, void *ws, size_t bytes, long long wait_cycles,
+                             const pbs_batch_options &opt, int max_steps) {
   unsigned long long h = 14695981039346656037ULL;
+  const int hold = opt.hold_beam;
+  h = fnv1a(h, &opt.shape, sizeof(int));
+  h = fnv1a(h, &opt.transport_cols, sizeof(int));
+  h = fnv1a(h, &max_steps, sizeof(int));
   for (int i = 0; i < n; i++) {
     const void *ptr = P[i];
     const int depth = beam_depth(P[i], 0);
@@ -1329,7 +1361,7 @@ unsigned long long batch_key(pbs_ctx *const *P, int n, void *ws, size_t bytes, l
 // restarted from its projection, the queue counters cleared, the
 // persistent launch.
 pbs_status batch_issue(pbs_ctx *const *P, int n, unsigned char *ws, const BatchLayout &L, long long wait_cycles,
-                       size_t smem) {
+                       size_t smem, int shape) {
   pbs_ctx *c0 = P[0];
   for (int b = 0; b < n; b++) {
     pbs_status r = P[b]->precision == PBS_FP32 ? reinit_impl<float, float>(P[b])
@@ -1338,13 +1370,104 @@ pbs_status batch_issue(pbs_ctx *const *P, int n, unsigned char *ws, const BatchL
   }
   PBS_CUDA(c0, cudaMemsetAsync(ws + L.off_queue, 0, L.total - L.off_queue, c0->stream));
   LaunchCtx lc = lctx(c0);
-  cudaError_t e = launch_batch(lc, c0->nu, c0->nv, reinterpret_cast<const BatchBeam *>(ws + L.off_beams), n,
+  unsigned long long *prof = c0->profiling ? reinterpret_cast<unsigned long long *>(ws + L.off_prof) : nullptr;
+  int ctas = 0;
+  cudaError_t e = launch_batch(lc, shape, c0->nu, c0->nv, reinterpret_cast<const BatchBeam *>(ws + L.off_beams), n,
                                reinterpret_cast<const BatchTask *>(ws + L.off_tasks), (int)L.ntasks,
                                reinterpret_cast<BatchQueue *>(ws + L.off_queue),
                                reinterpret_cast<unsigned long long *>(ws + L.off_done),
                                reinterpret_cast<unsigned long long *>(ws + L.off_next), wait_cycles, smem, c0->du,
-                               c0->dv);
+                               c0->dv, prof, &ctas);
+  if (prof && !c0->capturing) {
+    c0->batch_prof = prof;
+    c0->batch_ctas = ctas;
+  }
   return e == cudaSuccess ? PBS_OK : cuda_fail(c0, e, "batch kernel");
+}
+
+pbs_status run_batch_impl(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_t bytes,
+                          const pbs_batch_options &opt, int max_steps) {
+  pbs_ctx *c0 = beams[0];
+  if (opt.hold_beam < -1 || opt.hold_beam >= n_beams) return fail(c0, PBS_ERR_ARG, "hold_beam out of range");
+  if (opt.shape < 0 || opt.shape > 1 || (opt.transport_cols != 0 && opt.transport_cols != 4 && opt.transport_cols != 6))
+    return fail(c0, PBS_ERR_ARG, "batch shape must be 0 or 1 and transport_cols 0, 4 or 6");
+  pbs_status r = batch_check(beams, n_beams, opt);
+  if (r != PBS_OK) return r;
+  const BatchLayout L = batch_layout(beams, n_beams, max_steps);
+  if (!dev_ws || bytes < L.total || ((uintptr_t)dev_ws & 255))
+    return fail(c0, PBS_ERR_ARG, "batch workspace missing, smaller than pbs_batch_workspace_size or not 256-byte aligned");
+  if (L.ntasks > INT_MAX) return fail(c0, PBS_ERR_UNSUPPORTED, "too many passes in the batch");
+  int khz = 0;
+  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c0->dev) != cudaSuccess || khz <= 0) khz = 2000000;
+  const double ms = opt.wait_limit_ms > 0 ? opt.wait_limit_ms : 2000.0;
+  const long long wait_cycles = (long long)(ms * khz);
+  unsigned char *ws = static_cast<unsigned char *>(dev_ws);
+  const unsigned long long key = batch_key(beams, n_beams, dev_ws, bytes, wait_cycles, opt, max_steps);
+  std::vector<BatchBeam> hb;
+  std::vector<BatchTask> ht;
+  size_t smem = 0;
+  batch_descriptors(beams, n_beams, L, opt, max_steps, hb, ht, smem);
+  if (key != c0->batch_key) {  // new batch: upload its descriptors, forget its graph
+    PBS_CUDA(c0, batch_init_tables());
+    PBS_CUDA(c0, cudaMemcpyAsync(ws + L.off_beams, hb.data(), sizeof(BatchBeam) * hb.size(), cudaMemcpyHostToDevice,
+                                 c0->stream));
+    if (!ht.empty())
+      PBS_CUDA(c0, cudaMemcpyAsync(ws + L.off_tasks, ht.data(), sizeof(BatchTask) * ht.size(), cudaMemcpyHostToDevice,
+                                   c0->stream));
+    PBS_CUDA(c0, cudaStreamSynchronize(c0->stream));  // the host copies die here
+    if (c0->batch_graph) cudaGraphExecDestroy(c0->batch_graph);
+    c0->batch_graph = nullptr;
+    c0->batch_key = key;
+  }
+  if (!opt.use_graph) {
+    r = batch_issue(beams, n_beams, ws, L, wait_cycles, smem, opt.shape);
+    if (r != PBS_OK) return r;
+  } else {
+    if (!c0->batch_graph) {
+      if (!c0->cap_stream) PBS_CUDA(c0, cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t user = c0->stream;
+      std::vector<long long> before(n_beams);
+      for (int b = 0; b < n_beams; b++) {
+        before[b] = beams[b]->launches;
+        beams[b]->stream = c0->cap_stream;
+        beams[b]->capturing = true;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c0->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        r = batch_issue(beams, n_beams, ws, L, wait_cycles, smem, opt.shape);
+        cudaError_t e2 = cudaStreamEndCapture(c0->cap_stream, &g);
+        if (e == cudaSuccess) e = e2;
+      }
+      long long kernels = 0;
+      for (int b = 0; b < n_beams; b++) {
+        beams[b]->stream = user;
+        beams[b]->capturing = false;
+        kernels += beams[b]->launches - before[b];
+        beams[b]->launches = before[b];
+      }
+      if (r != PBS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess) return cuda_fail(c0, e, "batch graph capture");
+      e = cudaGraphInstantiate(&c0->batch_graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        c0->batch_graph = nullptr;
+        return cuda_fail(c0, e, "batch graph instantiate");
+      }
+      c0->batch_graph_kernels = kernels;
+    }
+    PBS_CUDA(c0, cudaGraphLaunch(c0->batch_graph, c0->stream));
+    c0->launches += c0->batch_graph_kernels;
+  }
+  for (int b = 0; b < n_beams; b++) {
+    beams[b]->steps_done = batch_depth(beams[b], max_steps);
+    beams[b]->pending = false;
+    beams[b]->stage = 0;
+  }
+  return PBS_OK;
 }
 
 }  // namespace
@@ -1746,86 +1869,70 @@ pbs_status pbs_run_batch(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_
   if (!beams || n_beams < 1 || n_beams > 65535) return PBS_ERR_ARG;
   for (int i = 0; i < n_beams; i++)
     if (!beams[i]) return PBS_ERR_ARG;
+  const pbs_batch_options def{0, 0.0, -1, 0, 0};
+  return run_batch_impl(beams, n_beams, dev_ws, bytes, o ? *o : def, -1);
+}
+
+pbs_status pbs_batch_autotune(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_t bytes, int steps,
+                              pbs_batch_options *opts) {
+  if (!beams || n_beams < 1 || n_beams > 65535 || !opts || steps < 1) return PBS_ERR_ARG;
+  for (int i = 0; i < n_beams; i++)
+    if (!beams[i]) return PBS_ERR_ARG;
   pbs_ctx *c0 = beams[0];
-  const pbs_batch_options def{0, 0.0, -1};
-  const pbs_batch_options &opt = o ? *o : def;
-  if (opt.hold_beam < -1 || opt.hold_beam >= n_beams) return fail(c0, PBS_ERR_ARG, "hold_beam out of range");
-  pbs_status r = batch_check(beams, n_beams);
-  if (r != PBS_OK) return r;
-  const BatchLayout L = batch_layout(beams, n_beams);
-  if (!dev_ws || bytes < L.total || ((uintptr_t)dev_ws & 255))
-    return fail(c0, PBS_ERR_ARG, "batch workspace missing, smaller than pbs_batch_workspace_size or not 256-byte aligned");
-  if (L.ntasks > INT_MAX) return fail(c0, PBS_ERR_UNSUPPORTED, "too many passes in the batch");
-  int khz = 0;
-  if (cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c0->dev) != cudaSuccess || khz <= 0) khz = 2000000;
-  const double ms = opt.wait_limit_ms > 0 ? opt.wait_limit_ms : 2000.0;
-  const long long wait_cycles = (long long)(ms * khz);
-  unsigned char *ws = static_cast<unsigned char *>(dev_ws);
-  const unsigned long long key = batch_key(beams, n_beams, dev_ws, bytes, wait_cycles, opt.hold_beam);
-  std::vector<BatchBeam> hb;
-  std::vector<BatchTask> ht;
-  size_t smem = 0;
-  batch_descriptors(beams, n_beams, L, opt.hold_beam, hb, ht, smem);
-  if (key != c0->batch_key) {  // new batch: upload its descriptors, forget its graph
-    PBS_CUDA(c0, batch_init_tables());
-    PBS_CUDA(c0, cudaMemcpyAsync(ws + L.off_beams, hb.data(), sizeof(BatchBeam) * hb.size(), cudaMemcpyHostToDevice,
-                                 c0->stream));
-    if (!ht.empty())
-      PBS_CUDA(c0, cudaMemcpyAsync(ws + L.off_tasks, ht.data(), sizeof(BatchTask) * ht.size(), cudaMemcpyHostToDevice,
-                                   c0->stream));
-    PBS_CUDA(c0, cudaStreamSynchronize(c0->stream));  // the host copies die here
-    if (c0->batch_graph) cudaGraphExecDestroy(c0->batch_graph);
-    c0->batch_graph = nullptr;
-    c0->batch_key = key;
+  // the candidates: shape 0 (4 columns), shape 1 with 4 and, where some row
+  // splits into 6-column lanes, with 6 columns
+  bool six = false;
+  for (int i = 0; i < n_beams; i++) six = six || beams[i]->nz % 6 == 0;
+  const int cand[3][2] = {{0, 4}, {1, 4}, {1, 6}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PBS_CUDA(c0, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c0, PBS_ERR_CUDA, "event create");
   }
-  if (!opt.use_graph) {
-    r = batch_issue(beams, n_beams, ws, L, wait_cycles, smem);
-    if (r != PBS_OK) return r;
-  } else {
-    if (!c0->batch_graph) {
-      if (!c0->cap_stream) PBS_CUDA(c0, cudaStreamCreateWithFlags(&c0->cap_stream, cudaStreamNonBlocking));
-      cudaStream_t user = c0->stream;
-      std::vector<long long> before(n_beams);
-      for (int b = 0; b < n_beams; b++) {
-        before[b] = beams[b]->launches;
-        beams[b]->stream = c0->cap_stream;
-        beams[b]->capturing = true;
+  const bool prof = c0->profiling;
+  c0->profiling = false;
+  pbs_status r = PBS_OK;
+  float best = 1e30f;
+  pbs_batch_options pick = *opts, trial = *opts;
+  trial.use_graph = 0;
+  trial.hold_beam = -1;
+  for (int k = 0; k < 3 && r == PBS_OK; k++) {
+    if (cand[k][1] == 6 && !six) continue;
+    trial.shape = cand[k][0];
+    trial.transport_cols = cand[k][1];
+    for (int rep = 0; rep < 2 && r == PBS_OK; rep++) {
+      cudaEventRecord(e0, c0->stream);
+      r = run_batch_impl(beams, n_beams, dev_ws, bytes, trial, steps);
+      cudaEventRecord(e1, c0->stream);
+      if (r != PBS_OK) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { r = fail(c0, PBS_ERR_CUDA, "batch trial"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        pick.shape = trial.shape;
+        pick.transport_cols = trial.transport_cols;
       }
-      cudaGraph_t g = nullptr;
-      cudaError_t e = cudaStreamBeginCapture(c0->cap_stream, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        r = batch_issue(beams, n_beams, ws, L, wait_cycles, smem);
-        cudaError_t e2 = cudaStreamEndCapture(c0->cap_stream, &g);
-        if (e == cudaSuccess) e = e2;
-      }
-      long long kernels = 0;
-      for (int b = 0; b < n_beams; b++) {
-        beams[b]->stream = user;
-        beams[b]->capturing = false;
-        kernels += beams[b]->launches - before[b];
-        beams[b]->launches = before[b];
-      }
-      if (r != PBS_OK) {
-        if (g) cudaGraphDestroy(g);
-        return r;
-      }
-      if (e != cudaSuccess) return cuda_fail(c0, e, "batch graph capture");
-      e = cudaGraphInstantiate(&c0->batch_graph, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
-        c0->batch_graph = nullptr;
-        return cuda_fail(c0, e, "batch graph instantiate");
-      }
-      c0->batch_graph_kernels = kernels;
     }
-    PBS_CUDA(c0, cudaGraphLaunch(c0->batch_graph, c0->stream));
-    c0->launches += c0->batch_graph_kernels;
   }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c0->profiling = prof;
+  if (r != PBS_OK) return r;
+  // the trials marched the beams: restart them from their projections
   for (int b = 0; b < n_beams; b++) {
-    beams[b]->steps_done = beam_depth(beams[b], 0);
-    beams[b]->pending = false;
-    beams[b]->stage = 0;
+    pbs_status q = beams[b]->precision == PBS_FP32 ? reinit_impl<float, float>(beams[b])
+                                                   : reinit_impl<float, __nv_bfloat16>(beams[b]);
+    if (q != PBS_OK) return q;
   }
+  PBS_CUDA(c0, cudaStreamSynchronize(c0->stream));
+  for (int b = 0; b < n_beams; b++) {
+    pbs_status q = check_device_status(beams[b]);
+    if (q != PBS_OK) return q;
+  }
+  opts->shape = pick.shape;
+  opts->transport_cols = pick.transport_cols;
   return PBS_OK;
 }
 
@@ -2019,6 +2126,7 @@ pbs_status pbs_set_profiling(pbs_ctx *c, int on) {
   if (!c) return PBS_ERR_ARG;
   pbs_status r = fold_profile(c);
   if (r != PBS_OK) return r;
+  c->batch_prof = nullptr;
   c->profiling = on != 0;
   for (int k = 0; k < PBS_KERNEL_KINDS; k++) {
     c->prof_count[k] = 0;

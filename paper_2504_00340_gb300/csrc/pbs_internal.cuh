@@ -265,7 +265,7 @@ struct BatchBeam {
   int n_steps;
   float c, hq, ky, kz, du, dv;  // E(h/2) CN factor, h/4 of A(h), transport tau/dy, tau/dz, angle spacings
   double dose_scale, flu_scale;
-  int e_bx, a_bx, tr_nseg, tr_segw, tr_gw;
+  int e_bx, a_bx, tr_kv, tr_nseg, tr_segw, tr_gw;
   long long tr_stacks;
 };
 // One (beam, pass) of the queue: its tiles, and the beam's tiles in earlier passes.
@@ -284,17 +284,21 @@ struct BatchQueue {
 struct BatchShape {
   int e_bx, e_by;
   long long e_tiles, tr_stacks, t_tiles;
-  int tr_nseg, tr_segw, tr_gw;
+  int tr_kv, tr_nseg, tr_segw, tr_gw;
   int a_bx;
   long long a_tiles;
   size_t smem;
 };
-BatchShape batch_shape(const Dims &d);
+BatchShape batch_shape(const Dims &d, int shape, int cols);
 bool batch_supported(int nu, int nv);
 cudaError_t batch_init_tables();
-cudaError_t launch_batch(const LaunchCtx &lc, int nu, int nv, const BatchBeam *beams, int nbeams,
+// prof: NULL, or 8 counters the kernel adds to: SM clocks in energy,
+// transport, angular tiles and in claiming/waiting ([0..3]) and the tiles
+// run of each kind ([4..6]).  *ctas receives the launch's CTA count.
+cudaError_t launch_batch(const LaunchCtx &lc, int shape, int nu, int nv, const BatchBeam *beams, int nbeams,
                          const BatchTask *tasks, int ntasks, BatchQueue *q, unsigned long long *done,
-                         unsigned long long *next, long long wait_cycles, size_t smem, double du, double dv);
+                         unsigned long long *next, long long wait_cycles, size_t smem, double du, double dv,
+                         unsigned long long *prof, int *ctas);
 
 template <typename real>
 cudaError_t launch_init(const LaunchCtx &lc, const Dims &d, real *psi0, const double *fe, const double *fa,

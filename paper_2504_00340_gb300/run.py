@@ -38,13 +38,14 @@ def run_spots(a) -> dict:
         if world > 1:
             raise SystemExit("--persistent runs on one GPU")
         t0 = time.perf_counter()
-        doses, st = S.run_persistent(sp, use_graph=not a.no_graph,
+        doses, st = S.run_persistent(sp, use_graph=not a.no_graph, autotune=not a.no_autotune,
                                      max_bytes=int(a.max_gb * (1 << 30)) if a.max_gb_set else None)
         useful = float(st["cell_updates"])
         return {"spots": len(sp), "persistent_launches": st["launches"], "device_ms": st["device_ms"],
                 "wall_s": time.perf_counter() - t0, "cell_updates": useful,
                 "cell_updates_per_s": useful / (st["device_ms"] * 1e-3), "kernels": st["kernels"],
-                "graph": st["graph"], "max_dose": float(max(np.abs(d).max() for d in doses.values()))}
+                "graph": st["graph"], "shapes": st["shapes"],
+                "max_dose": float(max(np.abs(d).max() for d in doses.values()))}
     t0 = time.perf_counter()
     doses, st = S.run_shard(sp, rank, world, max_bytes=int(a.max_gb * (1 << 30)), use_graph=not a.no_graph,
                             autotune=not a.no_autotune)

@@ -240,12 +240,14 @@ def plan_waves(spots: list[Workload], max_bytes: int) -> list[list[int]]:
     return waves
 
 
-def run_persistent(spots: list[Workload], *, max_bytes: int | None = None, use_graph: bool = False):
+def run_persistent(spots: list[Workload], *, max_bytes: int | None = None, use_graph: bool = False,
+                   autotune: bool = True):
     """March the spots through the persistent batch (pbs_run_batch): every
     spot its own context on its own grid (its own energy groups, no bucket
-    and no empty groups), as few launches as memory allows.  Returns
-    ({spot: dose [steps][ny][nz]}, stats with the device time of the timed
-    launches (CUDA events on the stream)."""
+    and no empty groups), as few launches as memory allows, with the CTA
+    shape the batch autotuner picks on a few depth steps of the wave.
+    Returns ({spot: dose [steps][ny][nz]}, stats with the device time of the
+    timed launches (CUDA events on the stream))."""
     import torch
 
     from . import binding
@@ -254,7 +256,7 @@ def run_persistent(spots: list[Workload], *, max_bytes: int | None = None, use_g
     waves = plan_waves(spots, max_bytes)
     doses: dict = {}
     stats = dict(launches=len(waves), device_ms=0.0, kernels=0, cell_updates=useful_cost(spots),
-                 graph=use_graph)
+                 graph=use_graph, shapes=[])
     for wave in waves:
         solvers = []
         try:
@@ -265,12 +267,15 @@ def run_persistent(spots: list[Workload], *, max_bytes: int | None = None, use_g
                 solvers.append(s)
                 s.set_material(w.density())
                 s.launch_beam(**{k: v for k, v in w.beam.items() if k not in ("yc", "zc")})
-            ws = binding.run_batch(solvers, use_graph=True) if use_graph else None  # records the graph
+            opts, ws = binding.autotune_batch(solvers, steps=4) if autotune else ({}, None)
+            stats["shapes"].append(opts)
+            if use_graph:
+                ws = binding.run_batch(solvers, use_graph=True, workspace=ws, **opts)  # records the graph
             k0 = sum(s.kernel_launches for s in solvers)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(solvers[0].stream)
-            ws = binding.run_batch(solvers, use_graph=use_graph, workspace=ws)
+            ws = binding.run_batch(solvers, use_graph=use_graph, workspace=ws, **opts)
             e1.record(solvers[0].stream)
             e1.synchronize()
             stats["device_ms"] += e0.elapsed_time(e1)

@@ -47,9 +47,12 @@ def _results(s):
     return s.read_psi(0), s.read_dose(), s.read_fluence()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "mixed"])
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_equals_each_beams_own_march(precision, use_graph):
+@pytest.mark.parametrize("precision,use_graph,shape,cols", [
+    ("fp32", False, 0, 0), ("fp32", True, 0, 0), ("mixed", False, 0, 0), ("mixed", True, 1, 6),
+    ("fp32", False, 1, 4), ("fp32", False, 1, 6)])
+def test_batch_equals_each_beams_own_march(precision, use_graph, shape, cols):
+    """Both CTA shapes and both transport column counts: every shape runs the
+    same arithmetic per cell."""
     ref = []
     for i, spec in enumerate(BEAMS):
         s, *_ = _make(spec, precision, seed=i)
@@ -57,7 +60,7 @@ def test_batch_equals_each_beams_own_march(precision, use_graph):
         ref.append(_results(s))
         s.close()
     solvers = [_make(spec, precision, seed=i)[0] for i, spec in enumerate(BEAMS)]
-    ws = binding.run_batch(solvers, use_graph=use_graph)
+    ws = binding.run_batch(solvers, use_graph=use_graph, shape=shape, transport_cols=cols)
     for s, (psi, dose, flu) in zip(solvers, ref):
         assert s.depth == s.nx
         got = _results(s)
@@ -65,11 +68,28 @@ def test_batch_equals_each_beams_own_march(precision, use_graph):
         assert _relerr(got[1], dose) < 1e-13
         assert _relerr(got[2], flu) < 1e-13
     if use_graph:  # a replay of the recorded batch restarts every beam and gives the same
-        binding.run_batch(solvers, use_graph=True, workspace=ws)
+        binding.run_batch(solvers, use_graph=True, workspace=ws, shape=shape, transport_cols=cols)
         for s, (psi, dose, _) in zip(solvers, ref):
             assert np.array_equal(s.read_psi(0), psi)
             assert _relerr(s.read_dose(), dose) < 1e-13
     for s in solvers:
+        s.close()
+
+
+def test_batch_autotuner_picks_a_shape_and_restarts_the_beams():
+    ref = []
+    for i, spec in enumerate(BEAMS):
+        s, *_ = _make(spec, "fp32", seed=i)
+        s.run(use_graph=False)
+        ref.append(s.read_psi(0))
+        s.close()
+    solvers = [_make(spec, "fp32", seed=i)[0] for i, spec in enumerate(BEAMS)]
+    opts, ws = binding.autotune_batch(solvers, steps=3)
+    assert opts["shape"] in (0, 1) and opts["transport_cols"] in (4, 6)
+    assert all(s.depth == 0 for s in solvers)  # restarted from the projections
+    binding.run_batch(solvers, workspace=ws, **opts)
+    for s, psi in zip(solvers, ref):
+        assert np.array_equal(s.read_psi(0), psi)
         s.close()
 
 
