@@ -334,17 +334,29 @@ pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
  *   transport_cols 4 or 6 columns per lane of the transport tiles (6 only with
  *                  shape 1 and rows that split evenly into 6-column lanes,
  *                  else 4), or 0 for the default rule (6 where that fills the
- *                  warps better).  pbs_batch_autotune picks shape and columns. */
+ *                  warps better).
+ *   pipeline       0: a beam's passes follow one another whole.  1: the
+ *                  T(h/2) A(h) T(h/2) passes of a step are cut into chunks of
+ *                  32 slab stacks (component, group, coefficient), and the
+ *                  angular step of a chunk starts as soon as its first
+ *                  transport is done, its second transport as soon as its
+ *                  angular step is (the angular step couples only the angles
+ *                  of one stack, the transport only the cells of one plane):
+ *                  one beam's passes overlap, at the cost of more tasks.
+ *   pbs_batch_autotune picks shape, columns and pipeline.  16 x 16 angles
+ *   run with shape 0 only. */
 typedef struct {
   int use_graph;
   double wait_limit_ms;
   int hold_beam;
   int shape;
   int transport_cols;
+  int pipeline;
 } pbs_batch_options;
 
 /* Bytes of the device workspace pbs_run_batch needs for these beams with
- * their current depth ranges (descriptors, task list, queue counters). */
+ * their current depth ranges (descriptors, task list, queue counters), with
+ * or without pipelined passes. */
 pbs_status pbs_batch_workspace_size(pbs_ctx *const *beams, int n_beams, size_t *bytes);
 
 /* Restart every beam from its projection (as pbs_run does) and march all of
@@ -354,7 +366,8 @@ pbs_status pbs_batch_workspace_size(pbs_ctx *const *beams, int n_beams, size_t *
  * the batch runs; opts may be NULL (no graph, 2000 ms waits).  The beams
  * must be FP32 or mixed-precision contexts with n_scatter = 0 and n_beams =
  * 1, the default integrators and no straggling, ny*nz even, nz a multiple
- * of 4, one angle grid of at most 8 x 8 for all, one device and one stream
+ * of 4, one square angle grid for all (at most 8 x 8, or 16 x 16 with shape
+ * 0), one device and one stream
  * (PBS_ERR_UNSUPPORTED / PBS_ERR_ARG otherwise), each with a workspace,
  * tables, material and a launched beam (PBS_ERR_STATE otherwise).
  * Asynchronous; afterwards every beam's dose and fluence are final (read
@@ -362,11 +375,12 @@ pbs_status pbs_batch_workspace_size(pbs_ctx *const *beams, int n_beams, size_t *
 pbs_status pbs_run_batch(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_t bytes,
                          const pbs_batch_options *opts);
 
-/* Batch autotuner: times the CTA shapes and transport column counts of
- * pbs_batch_options (best of two trials each) on the batch with every beam
+/* Batch autotuner: times the CTA shapes, transport column counts and
+ * pipelined passes of pbs_batch_options (best of two trials each) on the
+ * batch with every beam
  * cut to at most `steps` depth steps, with CUDA events on the beams' stream,
- * and writes the fastest into opts->shape and opts->transport_cols (the
- * other fields are kept).  The trials march the beams, so they restart from
+ * and writes the fastest into opts->shape, opts->transport_cols and
+ * opts->pipeline (the other fields are kept).  The trials march the beams, so they restart from
  * their projections afterwards.  dev_ws as for pbs_run_batch.
  * Synchronises. */
 pbs_status pbs_batch_autotune(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_t bytes, int steps,

@@ -61,7 +61,7 @@ class PbsOptions(ctypes.Structure):
 
 class PbsBatchOptions(ctypes.Structure):
     _fields_ = [("use_graph", ctypes.c_int), ("wait_limit_ms", ctypes.c_double), ("hold_beam", ctypes.c_int),
-                ("shape", ctypes.c_int), ("transport_cols", ctypes.c_int)]
+                ("shape", ctypes.c_int), ("transport_cols", ctypes.c_int), ("pipeline", ctypes.c_int)]
 
 
 class PbsError(RuntimeError):
@@ -286,10 +286,10 @@ def pbs_batch_workspace_size(ctxs) -> int:
 
 
 def pbs_run_batch(ctxs, dev_ptr: int, nbytes: int, use_graph: bool = False, wait_limit_ms: float = 0.0,
-                  hold_beam: int = -1, shape: int = 0, transport_cols: int = 0) -> None:
+                  hold_beam: int = -1, shape: int = 0, transport_cols: int = 0, pipeline: int = 0) -> None:
     arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
     opts = PbsBatchOptions(int(bool(use_graph)), float(wait_limit_ms), int(hold_beam), int(shape),
-                           int(transport_cols))
+                           int(transport_cols), int(pipeline))
     _check(ctxs[0], load_library().pbs_run_batch(arr, len(ctxs), _VP(dev_ptr), nbytes, ctypes.byref(opts)))
 
 
@@ -297,10 +297,10 @@ def pbs_batch_autotune(ctxs, dev_ptr: int, nbytes: int, steps: int = 6) -> dict:
     """The batch shape and transport columns the autotuner picks (see
     pbs_batch_autotune); the beams restart from their projections."""
     arr = (_VP * len(ctxs))(*[_VP(c) for c in ctxs])
-    opts = PbsBatchOptions(0, 0.0, -1, 0, 0)
+    opts = PbsBatchOptions(0, 0.0, -1, 0, 0, 0)
     _check(ctxs[0], load_library().pbs_batch_autotune(arr, len(ctxs), _VP(dev_ptr), nbytes, int(steps),
                                                       ctypes.byref(opts)))
-    return {"shape": opts.shape, "transport_cols": opts.transport_cols}
+    return {"shape": opts.shape, "transport_cols": opts.transport_cols, "pipeline": opts.pipeline}
 
 
 def pbs_checkpoint_size(ctx) -> int:
@@ -415,14 +415,14 @@ def _batch_workspace(solvers, workspace):
 
 
 def run_batch(solvers, use_graph: bool = False, wait_limit_ms: float = 0.0, hold_beam: int = -1, workspace=None,
-              shape: int = 0, transport_cols: int = 0):
+              shape: int = 0, transport_cols: int = 0, pipeline: int = 0):
     """March every Solver of the list (one beam each, see pbs_run_batch) in
     one persistent launch on their common stream.  The batch workspace is a
     torch tensor allocated here unless given (keep it alive while the batch
     runs: it is returned)."""
     workspace = _batch_workspace(solvers, workspace)
     pbs_run_batch([s.ctx for s in solvers], workspace.data_ptr(), workspace.numel(), use_graph, wait_limit_ms,
-                  hold_beam, shape, transport_cols)
+                  hold_beam, shape, transport_cols, pipeline)
     return workspace
 
 

@@ -32,6 +32,8 @@ namespace pbs {
 
 namespace {
 
+using namespace batch_pass;
+
 // CTA shapes (pbs_batch_options.shape), both 16 warps' worth of work per SM:
 //   0  256 threads, two CTAs per SM at 128 registers: an energy block of
 //      32 x 8 threads (16 angles x 64 lateral points), eight transport warps
@@ -47,10 +49,14 @@ struct BShape {
   static constexpr int kMinBlocks = SHAPE == 0 ? 2 : 3;
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kEnergyY = kThreads / 32;
-  static constexpr int kAngSub = kThreads / 128;  // angular sub-blocks of 16 x 8
 };
-constexpr int kBAngR = 4;       // slab stacks at a time per angular sub-block
-constexpr int kBAngRep = 32;    // angular slab stacks per tile
+// Angular sub-blocks of 16 x NT threads per CTA (16 x 16 angles need a whole
+// 256-thread CTA), and slab stacks worked at a time per sub-block.
+template <int SHAPE, int NT>
+__host__ __device__ constexpr int ang_subs() { return BShape<SHAPE>::kThreads / (16 * NT); }
+template <int NT>
+__host__ __device__ constexpr int ang_r() { return NT <= 8 ? 4 : 1; }
+constexpr int kBAngRep = 32;    // angular slab stacks per tile (and per chunk of a pipelined pass)
 
 // Ask the L2 for the rows of R slab stacks kgc0 + r (r < R, those < nkgc) at
 // lateral block bx: one hint per 128-byte line (16 threads share a line).
@@ -70,17 +76,6 @@ __device__ __forceinline__ void prefetch_stacks(const float *psi, int nyz, long 
   }
 }
 
-// Pass kinds of a beam's chain.
-enum : int { kPassEOpen = 0, kPassEPair = 1, kPassEClose = 2, kPassT = 3, kPassA = 4 };
-
-__device__ __forceinline__ int pass_kind(int pass, int n_steps) {
-  if (pass == 4 * n_steps) return kPassEClose;
-  switch (pass & 3) {
-    case 0: return pass == 0 ? kPassEOpen : kPassEPair;
-    case 2: return kPassA;
-    default: return kPassT;
-  }
-}
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
   unsigned long long v;
@@ -106,8 +101,9 @@ __device__ void batch_abort(const BatchBeam *beams, int nbeams, int *abort_word,
 }
 
 template <int NU, int NV, int SHAPE>
-__device__ __forceinline__ void run_tile(const BatchBeam &bm, int kind, int step, long long tile, unsigned char *smem,
+__device__ __forceinline__ void run_tile(const BatchBeam &bm, const BatchTask &tk, long long tile, unsigned char *smem,
                                          const ang::AngTables<float> &tb) {
+  const int kind = tk.kind, step = tk.step;
   using S = BShape<SHAPE>;
   const Dims &d = bm.d;
   const int tid = threadIdx.x;
@@ -131,10 +127,11 @@ __device__ __forceinline__ void run_tile(const BatchBeam &bm, int kind, int step
           nullptr, bm.coef, bm.dose + sa * nyz, nullptr, flu, bm.c, bm.c, bm.dose_scale, bm.flu_scale, bs);
     }
   } else if (kind == kPassT) {
-    // one slab stack (component, g, c) of one mirror class per tile
-    const long long nst = bm.tr_stacks;
+    // one slab stack (component, g, c) of one mirror class per tile: the
+    // task's stacks of the class v < 0, then of the class v >= 0
+    const long long nst = tk.nstacks;
     const int fz = tile >= nst ? 1 : 0;
-    const long long stack = fz ? tile - nst : tile;
+    const long long stack = tk.first + (fz ? tile - nst : tile);
     const int a_split = (d.nv / 2) * d.nu;
     const int a0 = fz ? a_split : 0, na_half = fz ? d.na - a_split : a_split;
     float *psi = bm.psi + stack * (long long)d.na * d.nyz;
@@ -151,21 +148,23 @@ __device__ __forceinline__ void run_tile(const BatchBeam &bm, int kind, int step
       if (fz) PBS_BT(4, true); else PBS_BT(4, false);
     }
 #undef PBS_BT
-  } else {  // kPassA: kBAngRep consecutive slab stacks at one lateral block
+  } else {  // kPassA: kBAngRep consecutive slab stacks of the task at one lateral block
+    constexpr int NT = NU > NV ? NU : NV;
+    constexpr int kSub = ang_subs<SHAPE, NT>(), kR = ang_r<NT>();
     const int bx = (int)(tile % bm.a_bx);
-    const long long k0 = (tile / bm.a_bx) * kBAngRep;
-    const long long nkgc = (long long)d.ncomp * d.ng * 2;
-    constexpr int kPer = S::kAngSub * kBAngR;  // stacks per round of the CTA
-    const int sub = tid >> 7;
-    unsigned char *sm = smem + (size_t)sub * kBAngR * sizeof(float2) * NU * NV * ang::kF2X;
-    for (int it = 0; it < kBAngRep / kPer && k0 + kPer * it < nkgc; it++) {
+    const long long k0 = tk.first + (tile / bm.a_bx) * kBAngRep;
+    const long long kend = tk.first + tk.nstacks;  // the task's stacks end here
+    constexpr int kPer = kSub * kR;  // stacks per round of the CTA
+    const int sub = tid / (16 * NT);
+    const int x = tid & 15, t = (tid >> 4) % NT;
+    unsigned char *sm = smem + (size_t)sub * kR * sizeof(float2) * NU * NV * ang::kF2X;
+#pragma unroll 1
+    for (int it = 0; it < kBAngRep / kPer && k0 + kPer * it < kend; it++) {
       // the next round's rows travel to the L2 while this round computes
       if (it + 1 < kBAngRep / kPer)
-        prefetch_stacks<NU, NV, kBAngR>(bm.psi, d.nyz, k0 + kPer * (it + 1) + kBAngR * sub, nkgc, bx, tid & 15,
-                                        (tid >> 4) & 7);
-      ang::angular_f2_tiles<NU, NV, false, kBAngR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
-                                                   k0 + kPer * it + kBAngR * sub, 1, nkgc, bx, tid & 15,
-                                                   (tid >> 4) & 7, sm, tb);
+        prefetch_stacks<NU, NV, kR>(bm.psi, d.nyz, k0 + kPer * (it + 1) + kR * sub, kend, bx, x, t);
+      ang::angular_f2_tiles<NU, NV, false, kR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
+                                               k0 + kPer * it + kR * sub, 1, kend, bx, x, t, sm, tb);
       __syncthreads();  // the next stacks reuse the shared tiles
     }
   }
@@ -197,11 +196,11 @@ __global__ void __launch_bounds__(BShape<SHAPE>::kThreads, BShape<SHAPE>::kMinBl
         }
         atomicCAS(&q->cur, (unsigned long long)t, (unsigned long long)t + 1);  // this task is handed out
       }
-      if (go) {
-        // the beam's earlier passes: every one of their tiles has completed
+      if (go && tasks[t].wait_ctr >= 0) {
+        // the tiles this task depends on (all of them earlier in the queue) have completed
         const BatchTask tk = tasks[t];
-        const unsigned long long need = (unsigned long long)tk.need;
-        unsigned long long *done = &done_ctr[tk.beam];
+        const unsigned long long need = (unsigned long long)tk.wait_need;
+        unsigned long long *done = &done_ctr[tk.wait_ctr];
         if (ld_acquire(done) < need) {
           const long long t0 = clock64();
           while (ld_acquire(done) < need) {
@@ -230,14 +229,13 @@ __global__ void __launch_bounds__(BShape<SHAPE>::kThreads, BShape<SHAPE>::kMinBl
     if (!s_go) break;
     const BatchTask tk = tasks[s_task];
     const BatchBeam &bm = beams[tk.beam];
-    const int kind = pass_kind(tk.pass, bm.n_steps);
-    run_tile<NU, NV, SHAPE>(bm, kind, tk.pass >> 2, s_tile, smem, tb);
+    run_tile<NU, NV, SHAPE>(bm, tk, s_tile, smem, tb);
     __syncthreads();  // every thread's writes of this tile are done
     if (tid == 0) {
       __threadfence();
-      atomicAdd(&done_ctr[tk.beam], 1ULL);
+      atomicAdd(&done_ctr[tk.sig_ctr], 1ULL);
       if (prof) {
-        const int k = kind == kPassT ? 1 : (kind == kPassA ? 2 : 0);
+        const int k = tk.kind == kPassT ? 1 : (tk.kind == kPassA ? 2 : 0);
         atomicAdd(&prof[k], (unsigned long long)(clock64() - t_start));
         atomicAdd(&prof[4 + k], 1ULL);
       }
@@ -307,7 +305,7 @@ static int batch_kv(int nz, int want, int &nseg, int &seg_w, int &gw) {
 BatchShape batch_shape(const Dims &d, int shape, int cols) {
   BatchShape s{};
   const int threads = shape == 0 ? BShape<0>::kThreads : BShape<1>::kThreads;
-  const int ey = threads / 32, warps = threads / 32, asub = threads / 128;
+  const int ey = threads / 32, warps = threads / 32;
   s.e_bx = (d.nyz / 2 + en::kX - 1) / en::kX;
   s.e_by = (d.na + ey * en::kA - 1) / (ey * en::kA);
   s.e_tiles = (long long)s.e_bx * s.e_by;
@@ -319,13 +317,15 @@ BatchShape batch_shape(const Dims &d, int shape, int cols) {
   s.tr_kv = batch_kv(d.nz, want, s.tr_nseg, s.tr_segw, s.tr_gw);
   s.a_bx = (d.nyz / 2 + ang::kF2X - 1) / ang::kF2X;
   s.a_tiles = (long long)s.a_bx * (((long long)d.ncomp * d.ng * 2 + kBAngRep - 1) / kBAngRep);
+  const int nt = std::max(d.nu, d.nv);
+  const int subs = std::max(1, threads / (16 * nt)), r = nt <= 8 ? 4 : 1;
   s.smem = std::max(sizeof(en::GroupPair) * (size_t)d.ng,
                     std::max((size_t)warps * tr::kR * 32 * s.tr_kv * sizeof(float),
-                             (size_t)asub * kBAngR * sizeof(float2) * (size_t)d.nu * d.nv * ang::kF2X));
+                             (size_t)subs * r * sizeof(float2) * (size_t)d.nu * d.nv * ang::kF2X));
   return s;
 }
 
-bool batch_supported(int nu, int nv) { return nu == nv && nu <= 8 && angular_supported(nu, nv); }
+bool batch_supported(int nu, int nv) { return nu == nv && (nu <= 8 || nu == 16) && angular_supported(nu, nv); }
 
 cudaError_t launch_batch(const LaunchCtx &lc, int shape, int nu, int nv, const BatchBeam *beams, int nbeams,
                          const BatchTask *tasks, int ntasks, BatchQueue *q, unsigned long long *done,
@@ -339,6 +339,9 @@ cudaError_t launch_batch(const LaunchCtx &lc, int shape, int nu, int nv, const B
                                           du, dv, prof, ctas);
   PBS_B(2, 2) PBS_B(4, 4) PBS_B(6, 6) PBS_B(8, 8)
 #undef PBS_B
+  // 16 x 16 angles: a whole 256-thread CTA per angular block (shape 0 only)
+  if (nu == 16 && nv == 16 && shape == 0)
+    return go_batch<16, 16, 0>(lc, beams, nbeams, tasks, ntasks, q, done, next, wait_cycles, smem, du, dv, prof, ctas);
   return cudaErrorNotSupported;
 }
 

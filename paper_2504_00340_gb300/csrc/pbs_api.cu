@@ -28,6 +28,7 @@
 #include <vector>
 
 using namespace pbs;
+using namespace pbs::batch_pass;
 
 struct pbs_ctx {
   int dev = 0;
@@ -1220,11 +1221,16 @@ namespace {
 
 // ---------------------------------------------------------------- persistent batch
 
-int beam_passes(int steps) { return steps > 0 ? 4 * steps + 1 : 0; }
+// Slab stacks per chunk of a pipelined transport / angular pass (the
+// angular tile's stack count): with pipeline on, the angular step of a chunk
+// starts as soon as the first transport of that chunk is done, and the second
+// transport of a chunk as soon as its angular step is, so the three passes of
+// one beam overlap; without, each pass is one chunk.
+constexpr long long kBatchChunk = 32;
 
 struct BatchLayout {
   size_t off_beams, off_tasks, off_queue, off_done, off_next, off_prof, total;
-  long long ntasks;
+  long long ntasks, nctr;
 };
 
 // Depth a beam marches in the batch: its own, or at most max_steps (>= 0)
@@ -1234,16 +1240,26 @@ int batch_depth(const pbs_ctx *c, int max_steps) {
   return max_steps >= 0 ? std::min(d, max_steps) : d;
 }
 
-BatchLayout batch_layout(pbs_ctx *const *P, int n, int max_steps = -1) {
+long long batch_chunks(const pbs_ctx *c, int pipeline) {
+  const long long nst = (long long)c->d.ncomp * c->ng * 2;
+  return pipeline ? (nst + kBatchChunk - 1) / kBatchChunk : 1;
+}
+
+BatchLayout batch_layout(pbs_ctx *const *P, int n, int pipeline, int max_steps = -1) {
   BatchLayout L{};
-  long long nt = 0;
-  for (int i = 0; i < n; i++) nt += beam_passes(batch_depth(P[i], max_steps));
+  long long nt = 0, nc = 0;
+  for (int i = 0; i < n; i++) {
+    const long long steps = batch_depth(P[i], max_steps), nch = batch_chunks(P[i], pipeline);
+    nt += steps > 0 ? steps * (1 + 3 * nch) + 1 : 0;  // per step E and, per chunk, T A T; then the closing E
+    nc += 2 + 2 * nch;                                // E, T1 per chunk, A per chunk, T2
+  }
   L.ntasks = nt;
+  L.nctr = nc;
   size_t o = 0;
   L.off_beams = o; o = align256(o + sizeof(BatchBeam) * (size_t)n);
   L.off_tasks = o; o = align256(o + sizeof(BatchTask) * (size_t)nt);
   L.off_queue = o; o = align256(o + sizeof(BatchQueue));
-  L.off_done = o; o = align256(o + 8 * (size_t)n);
+  L.off_done = o; o = align256(o + 8 * (size_t)nc);
   L.off_next = o; o = align256(o + 8 * (size_t)nt);
   L.off_prof = o; o = align256(o + 8 * 8);
   L.total = o;
@@ -1270,6 +1286,8 @@ pbs_status batch_check(pbs_ctx *const *P, int n, const pbs_batch_options &opt) {
       return fail(c0, PBS_ERR_ARG, "the beams of a batch share one device and one stream");
     if (c->nu != c0->nu || c->nv != c0->nv || c->u_max != c0->u_max || c->v_max != c0->v_max)
       return fail(c0, PBS_ERR_ARG, "the beams of a batch share one angle grid");
+    if (std::max(c->nu, c->nv) > 8 && opt.shape != 0)
+      return fail(c0, PBS_ERR_UNSUPPORTED, "16 x 16 angles need batch shape 0");
     for (int j = 0; j < i; j++)
       if (P[j] == c) return fail(c0, PBS_ERR_ARG, "a context appears twice in the batch");
     if (batch_shape(c->d, opt.shape, opt.transport_cols).smem > 160 * 1024)
@@ -1320,19 +1338,56 @@ void batch_descriptors(pbs_ctx *const *P, int n, const BatchLayout &L, const pbs
     m.tr_segw = sh.tr_segw;
     m.tr_gw = sh.tr_gw;
     m.tr_stacks = sh.tr_stacks;
-    max_passes = std::max(max_passes, beam_passes(m.n_steps));
+    max_passes = std::max(max_passes, m.n_steps);
   }
-  std::vector<long long> need(n, 0);
-  for (int r = 0; r < max_passes; r++)
-    for (int b = 0; b < n; b++) {
-      if (r >= beam_passes(beams[b].n_steps)) continue;
-      const int kind = (r == 4 * beams[b].n_steps || (r & 3) == 0) ? 0 : ((r & 3) == 2 ? 2 : 1);
-      const long long nt = kind == 0 ? shape[b].e_tiles : (kind == 1 ? shape[b].t_tiles : shape[b].a_tiles);
-      // the test hook: one tile more than the earlier passes hold, so no wait on it ends
-      const long long extra = (b == hold_beam && r == 1) ? 1 : 0;
-      tasks.push_back(BatchTask{b, r, nt, need[b] + extra});
-      need[b] += nt;
+  (void)max_passes;
+  // every beam's own task sequence (each wait names tiles earlier in it),
+  // then merged round-robin over the beams, which keeps each beam's order
+  std::vector<std::vector<BatchTask>> seq(n);
+  int ctr = 0;
+  size_t longest = 0;
+  for (int b = 0; b < n; b++) {
+    const BatchShape &sh = shape[b];
+    const long long steps = beams[b].n_steps, nst = sh.tr_stacks, nch = batch_chunks(P[b], opt.pipeline);
+    const long long csz = opt.pipeline ? kBatchChunk : nst;
+    const int cE = ctr, cT1 = ctr + 1, cA = ctr + 1 + (int)nch, cT2 = ctr + 1 + 2 * (int)nch;
+    ctr += 2 + 2 * (int)nch;
+    std::vector<long long> t_tiles(nch), a_tiles(nch);
+    long long t2tot = 0;
+    for (long long c = 0; c < nch; c++) {
+      const long long k = std::min(csz, nst - c * csz);
+      t_tiles[c] = 2 * k;
+      a_tiles[c] = (long long)sh.a_bx * ((k + 31) / 32);
+      t2tot += t_tiles[c];
     }
+    std::vector<BatchTask> &q = seq[b];
+    auto add = [&](int kind, int step, long long first, long long k, long long tiles, int wc, long long need, int sc) {
+      q.push_back(BatchTask{b, kind, step, wc, sc, 0, first, k, tiles, need});
+    };
+    for (long long st = 0; st < steps; st++) {
+      if (st == 0) add(kPassEOpen, 0, 0, 0, sh.e_tiles, -1, 0, cE);
+      else add(kPassEPair, (int)st, 0, 0, sh.e_tiles, cT2, st * t2tot, cE);
+      for (long long i = 0; i < nch + 2; i++) {
+        if (i < nch)
+          add(kPassT, (int)st, i * csz, t_tiles[i] / 2, t_tiles[i], cE, (st + 1) * sh.e_tiles, cT1 + (int)i);
+        if (i >= 1 && i - 1 < nch) {
+          const long long c = i - 1;
+          add(kPassA, (int)st, c * csz, t_tiles[c] / 2, a_tiles[c], cT1 + (int)c, (st + 1) * t_tiles[c], cA + (int)c);
+        }
+        if (i >= 2 && i - 2 < nch) {
+          const long long c = i - 2;
+          add(kPassT, (int)st, c * csz, t_tiles[c] / 2, t_tiles[c], cA + (int)c, (st + 1) * a_tiles[c], cT2);
+        }
+      }
+    }
+    if (steps > 0) add(kPassEClose, (int)steps, 0, 0, sh.e_tiles, cT2, steps * t2tot, cE);
+    // the test hook: one tile more than can complete, so no wait on it ends
+    if (b == hold_beam && q.size() > 1) q[1].wait_need += 1;
+    longest = std::max(longest, q.size());
+  }
+  for (size_t k = 0; k < longest; k++)
+    for (int b = 0; b < n; b++)
+      if (k < seq[b].size()) tasks.push_back(seq[b][k]);
 }
 
 unsigned long long batch_key(pbs_ctx *const *P, int n, void *ws, size_t bytes, long long wait_cycles,
@@ -1341,6 +1396,7 @@ unsigned long long batch_key(pbs_ctx *const *P, int n, void *ws, size_t bytes, l
   const int hold = opt.hold_beam;
   h = fnv1a(h, &opt.shape, sizeof(int));
   h = fnv1a(h, &opt.transport_cols, sizeof(int));
+  h = fnv1a(h, &opt.pipeline, sizeof(int));
   h = fnv1a(h, &max_steps, sizeof(int));
   for (int i = 0; i < n; i++) {
     const void *ptr = P[i];
@@ -1389,11 +1445,12 @@ pbs_status run_batch_impl(pbs_ctx *const *beams, int n_beams, void *dev_ws, size
                           const pbs_batch_options &opt, int max_steps) {
   pbs_ctx *c0 = beams[0];
   if (opt.hold_beam < -1 || opt.hold_beam >= n_beams) return fail(c0, PBS_ERR_ARG, "hold_beam out of range");
-  if (opt.shape < 0 || opt.shape > 1 || (opt.transport_cols != 0 && opt.transport_cols != 4 && opt.transport_cols != 6))
-    return fail(c0, PBS_ERR_ARG, "batch shape must be 0 or 1 and transport_cols 0, 4 or 6");
+  if (opt.shape < 0 || opt.shape > 1 || (opt.transport_cols != 0 && opt.transport_cols != 4 && opt.transport_cols != 6) ||
+      opt.pipeline < 0 || opt.pipeline > 1)
+    return fail(c0, PBS_ERR_ARG, "batch shape must be 0 or 1, transport_cols 0, 4 or 6, pipeline 0 or 1");
   pbs_status r = batch_check(beams, n_beams, opt);
   if (r != PBS_OK) return r;
-  const BatchLayout L = batch_layout(beams, n_beams, max_steps);
+  const BatchLayout L = batch_layout(beams, n_beams, opt.pipeline, max_steps);
   if (!dev_ws || bytes < L.total || ((uintptr_t)dev_ws & 255))
     return fail(c0, PBS_ERR_ARG, "batch workspace missing, smaller than pbs_batch_workspace_size or not 256-byte aligned");
   if (L.ntasks > INT_MAX) return fail(c0, PBS_ERR_UNSUPPORTED, "too many passes in the batch");
@@ -1861,7 +1918,8 @@ pbs_status pbs_batch_workspace_size(pbs_ctx *const *beams, int n_beams, size_t *
   if (!beams || n_beams < 1 || !bytes) return PBS_ERR_ARG;
   for (int i = 0; i < n_beams; i++)
     if (!beams[i]) return PBS_ERR_ARG;
-  *bytes = batch_layout(beams, n_beams).total;
+  // the larger of the two layouts (pipelined passes have more tasks and counters)
+  *bytes = std::max(batch_layout(beams, n_beams, 0).total, batch_layout(beams, n_beams, 1).total);
   return PBS_OK;
 }
 
@@ -1869,7 +1927,7 @@ pbs_status pbs_run_batch(pbs_ctx *const *beams, int n_beams, void *dev_ws, size_
   if (!beams || n_beams < 1 || n_beams > 65535) return PBS_ERR_ARG;
   for (int i = 0; i < n_beams; i++)
     if (!beams[i]) return PBS_ERR_ARG;
-  const pbs_batch_options def{0, 0.0, -1, 0, 0};
+  const pbs_batch_options def{0, 0.0, -1, 0, 0, 0};
   return run_batch_impl(beams, n_beams, dev_ws, bytes, o ? *o : def, -1);
 }
 
@@ -1883,7 +1941,9 @@ pbs_status pbs_batch_autotune(pbs_ctx *const *beams, int n_beams, void *dev_ws, 
   // splits into 6-column lanes, with 6 columns
   bool six = false;
   for (int i = 0; i < n_beams; i++) six = six || beams[i]->nz % 6 == 0;
-  const int cand[3][2] = {{0, 4}, {1, 4}, {1, 6}};
+  const int cand[6][3] = {{0, 4, 0}, {1, 4, 0}, {1, 6, 0}, {0, 4, 1}, {1, 4, 1}, {1, 6, 1}};
+  bool big = false;  // 16 x 16 angles: shape 0 only
+  for (int i = 0; i < n_beams; i++) big = big || std::max(beams[i]->nu, beams[i]->nv) > 8;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   PBS_CUDA(c0, cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1897,10 +1957,12 @@ pbs_status pbs_batch_autotune(pbs_ctx *const *beams, int n_beams, void *dev_ws, 
   pbs_batch_options pick = *opts, trial = *opts;
   trial.use_graph = 0;
   trial.hold_beam = -1;
-  for (int k = 0; k < 3 && r == PBS_OK; k++) {
+  for (int k = 0; k < 6 && r == PBS_OK; k++) {
     if (cand[k][1] == 6 && !six) continue;
+    if (big && cand[k][0] != 0) continue;
     trial.shape = cand[k][0];
     trial.transport_cols = cand[k][1];
+    trial.pipeline = cand[k][2];
     for (int rep = 0; rep < 2 && r == PBS_OK; rep++) {
       cudaEventRecord(e0, c0->stream);
       r = run_batch_impl(beams, n_beams, dev_ws, bytes, trial, steps);
@@ -1913,6 +1975,7 @@ pbs_status pbs_batch_autotune(pbs_ctx *const *beams, int n_beams, void *dev_ws, 
         best = ms;
         pick.shape = trial.shape;
         pick.transport_cols = trial.transport_cols;
+        pick.pipeline = trial.pipeline;
       }
     }
   }
@@ -1933,6 +1996,7 @@ pbs_status pbs_batch_autotune(pbs_ctx *const *beams, int n_beams, void *dev_ws, 
   }
   opts->shape = pick.shape;
   opts->transport_cols = pick.transport_cols;
+  opts->pipeline = pick.pipeline;
   return PBS_OK;
 }
 

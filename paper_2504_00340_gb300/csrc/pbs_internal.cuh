@@ -268,10 +268,13 @@ struct BatchBeam {
   int e_bx, a_bx, tr_kv, tr_nseg, tr_segw, tr_gw;
   long long tr_stacks;
 };
-// One (beam, pass) of the queue: its tiles, and the beam's tiles in earlier passes.
+// One task of the queue: pass `kind` of depth step `step` of a beam (for the
+// transport and angular passes only the slab stacks first .. first+nstacks-1),
+// split into ntiles tiles.  Its tiles start once counter wait_ctr has reached
+// wait_need (wait_ctr < 0: at once) and each adds one to counter sig_ctr.
 struct BatchTask {
-  int beam, pass;
-  long long ntiles, need;
+  int beam, kind, step, wait_ctr, sig_ctr, pad;
+  long long first, nstacks, ntiles, wait_need;
 };
 // Device counters of one launch (zeroed before it): the task being handed
 // out and the abort word (per-beam completed tiles and per-task handed-out
@@ -280,6 +283,11 @@ struct BatchQueue {
   unsigned long long cur;
   int abort, pad;
 };
+// Pass kinds of the batch queue.
+namespace batch_pass {
+enum : int { kPassEOpen = 0, kPassEPair = 1, kPassEClose = 2, kPassT = 3, kPassA = 4 };
+}
+
 // Tile counts and shared memory of one beam's passes in the batch kernel.
 struct BatchShape {
   int e_bx, e_by;

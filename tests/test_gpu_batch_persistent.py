@@ -47,12 +47,12 @@ def _results(s):
     return s.read_psi(0), s.read_dose(), s.read_fluence()
 
 
-@pytest.mark.parametrize("precision,use_graph,shape,cols", [
-    ("fp32", False, 0, 0), ("fp32", True, 0, 0), ("mixed", False, 0, 0), ("mixed", True, 1, 6),
-    ("fp32", False, 1, 4), ("fp32", False, 1, 6)])
-def test_batch_equals_each_beams_own_march(precision, use_graph, shape, cols):
-    """Both CTA shapes and both transport column counts: every shape runs the
-    same arithmetic per cell."""
+@pytest.mark.parametrize("precision,use_graph,shape,cols,pipeline", [
+    ("fp32", False, 0, 0, 0), ("fp32", True, 0, 0, 1), ("mixed", False, 0, 0, 0), ("mixed", True, 1, 6, 1),
+    ("fp32", False, 1, 4, 0), ("fp32", False, 1, 6, 1)])
+def test_batch_equals_each_beams_own_march(precision, use_graph, shape, cols, pipeline):
+    """Both CTA shapes, both transport column counts, whole and pipelined
+    passes: every variant runs the same arithmetic per cell."""
     ref = []
     for i, spec in enumerate(BEAMS):
         s, *_ = _make(spec, precision, seed=i)
@@ -60,7 +60,7 @@ def test_batch_equals_each_beams_own_march(precision, use_graph, shape, cols):
         ref.append(_results(s))
         s.close()
     solvers = [_make(spec, precision, seed=i)[0] for i, spec in enumerate(BEAMS)]
-    ws = binding.run_batch(solvers, use_graph=use_graph, shape=shape, transport_cols=cols)
+    ws = binding.run_batch(solvers, use_graph=use_graph, shape=shape, transport_cols=cols, pipeline=pipeline)
     for s, (psi, dose, flu) in zip(solvers, ref):
         assert s.depth == s.nx
         got = _results(s)
@@ -68,12 +68,32 @@ def test_batch_equals_each_beams_own_march(precision, use_graph, shape, cols):
         assert _relerr(got[1], dose) < 1e-13
         assert _relerr(got[2], flu) < 1e-13
     if use_graph:  # a replay of the recorded batch restarts every beam and gives the same
-        binding.run_batch(solvers, use_graph=True, workspace=ws, shape=shape, transport_cols=cols)
+        binding.run_batch(solvers, use_graph=True, workspace=ws, shape=shape, transport_cols=cols, pipeline=pipeline)
         for s, (psi, dose, _) in zip(solvers, ref):
             assert np.array_equal(s.read_psi(0), psi)
             assert _relerr(s.read_dose(), dose) < 1e-13
     for s in solvers:
         s.close()
+
+
+@pytest.mark.parametrize("pipeline", [0, 1])
+def test_single_beam_with_16x16_angles(pipeline):
+    """One beam with 16 x 16 angles (shape 0, one angular block per CTA),
+    enough groups for several 32-stack chunks of a pipelined pass."""
+    spec = (8, 12, 40, 64.0, 60.0, 7, 0.04)
+    s, *_ = _make(spec, "fp32", nu=16)
+    s.run(use_graph=False)
+    ref = _results(s)
+    s.close()
+    t, *_ = _make(spec, "fp32", nu=16)
+    binding.run_batch([t], shape=0, pipeline=pipeline)
+    got = _results(t)
+    assert np.array_equal(got[0], ref[0])
+    assert _relerr(got[1], ref[1]) < 1e-13
+    with pytest.raises(binding.PbsError) as e:
+        binding.run_batch([t], shape=1)
+    assert e.value.status == -6
+    t.close()
 
 
 def test_batch_autotuner_picks_a_shape_and_restarts_the_beams():
@@ -85,7 +105,7 @@ def test_batch_autotuner_picks_a_shape_and_restarts_the_beams():
         s.close()
     solvers = [_make(spec, "fp32", seed=i)[0] for i, spec in enumerate(BEAMS)]
     opts, ws = binding.autotune_batch(solvers, steps=3)
-    assert opts["shape"] in (0, 1) and opts["transport_cols"] in (4, 6)
+    assert opts["shape"] in (0, 1) and opts["transport_cols"] in (4, 6) and opts["pipeline"] in (0, 1)
     assert all(s.depth == 0 for s in solvers)  # restarted from the projections
     binding.run_batch(solvers, workspace=ws, **opts)
     for s, psi in zip(solvers, ref):
@@ -146,7 +166,7 @@ def test_batch_rejects_what_it_does_not_handle():
     assert e.value.status == -6
     s16, *_ = _make(BEAMS[2], "fp32", nu=16)
     with pytest.raises(binding.PbsError):
-        binding.run_batch([s_ok, s16])   # 16 x 16 angles (and another angle grid)
+        binding.run_batch([s_ok, s16])   # another angle grid
     with pytest.raises(binding.PbsError):
         binding.run_batch([s_ok, s_ok])  # the same context twice
     for s in (s_ok, s64, s16):
