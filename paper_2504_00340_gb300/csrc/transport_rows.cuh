@@ -33,10 +33,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// x with its sign flipped where s is negative.
-__device__ __forceinline__ float flip_by(float x, float s) {
-  return __uint_as_float(__float_as_uint(x) ^ (__float_as_uint(s) & 0x80000000u));
-}
+// x with its sign flipped where s is negative (the FP64 limiter).
 __device__ __forceinline__ double flip_by(double x, double s) {
   return __longlong_as_double(__double_as_longlong(x) ^ (__double_as_longlong(s) & (long long)0x8000000000000000ULL));
 }
@@ -47,19 +44,6 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
   return r;
 }
 __device__ __forceinline__ double max3(double a, double b, double c) { return fmax(a, fmax(b, c)); }
-
-// Upwind face value for flow from A through B to C:  B + slope / 2 with the
-// superbee slope of d1 = B - A, d2 = C - B:
-//   slope = sign(d2) max(0, min(2x, |d2|), min(x, 2|d2|)),  x = d1 sign(d2),
-// which is 0 when d1, d2 differ in sign (x < 0) and otherwise
-// sign(d2) max(min(2|d1|,|d2|), min(|d1|,2|d2|)) = d2 eta(d1/d2).
-template <typename real>
-__device__ __forceinline__ real face_value_d(real B, real d1, real d2) {
-  const real a2 = fabs(d2);
-  const real x = flip_by(d1, d2);
-  const real m = max3(real(0), fmin(x + x, a2), fmin(x, a2 + a2));
-  return fma(real(0.5), copysign(m, d2), B);
-}
 
 // KV columns of one row.  Elementwise arithmetic goes through the helpers
 // below, which issue the packed FP32x2 instructions for float (two columns
@@ -122,6 +106,57 @@ __device__ __forceinline__ Vk<real, KV> face4(real s, const Vk<real, KV> &B, con
   }
   return r;
 }
+// B + sl / 2: the upwind face value (a flux without its speed)
+template <typename real, int KV>
+__device__ __forceinline__ Vk<real, KV> fval4(const Vk<real, KV> &B, const Vk<real, KV> &sl) {
+  Vk<real, KV> r;
+  if constexpr (sizeof(real) == 4) {
+#pragma unroll
+    for (int j = 0; j < KV; j += 2) {
+      const float2 t = __ffma2_rn(pk(0.5f, 0.5f), pk(sl.v[j], sl.v[j + 1]), pk(B.v[j], B.v[j + 1]));
+      r.v[j] = t.x;
+      r.v[j + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < KV; j++) r.v[j] = fma(real(0.5), sl.v[j], B.v[j]);
+  }
+  return r;
+}
+// a + s b
+template <typename real, int KV>
+__device__ __forceinline__ Vk<real, KV> axpy4(real s, const Vk<real, KV> &b, const Vk<real, KV> &a) {
+  Vk<real, KV> r;
+  if constexpr (sizeof(real) == 4) {
+#pragma unroll
+    for (int j = 0; j < KV; j += 2) {
+      const float2 t = __ffma2_rn(pk(s, s), pk(b.v[j], b.v[j + 1]), pk(a.v[j], a.v[j + 1]));
+      r.v[j] = t.x;
+      r.v[j + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < KV; j++) r.v[j] = fma(s, b.v[j], a.v[j]);
+  }
+  return r;
+}
+// s a
+template <typename real, int KV>
+__device__ __forceinline__ Vk<real, KV> scale4(real s, const Vk<real, KV> &a) {
+  Vk<real, KV> r;
+  if constexpr (sizeof(real) == 4) {
+#pragma unroll
+    for (int j = 0; j < KV; j += 2) {
+      const float2 t = __fmul2_rn(pk(s, s), pk(a.v[j], a.v[j + 1]));
+      r.v[j] = t.x;
+      r.v[j + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < KV; j++) r.v[j] = s * a.v[j];
+  }
+  return r;
+}
 // a + (b - c) + e
 template <typename real, int KV>
 __device__ __forceinline__ Vk<real, KV> upd4(const Vk<real, KV> &a, const Vk<real, KV> &b, const Vk<real, KV> &c,
@@ -129,19 +164,43 @@ __device__ __forceinline__ Vk<real, KV> upd4(const Vk<real, KV> &a, const Vk<rea
   return add4(add4(a, sub4(b, c)), e);
 }
 
+// sign(a) xor sign(b) times min(|a|, |b|) (one min/max instruction).
+__device__ __forceinline__ float min_xorsign_abs(float a, float b) {
+  float r;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
 // Superbee slopes of the lane's columns from their differences d1 (behind)
 // and d2 (ahead): the packed part (2x, 2|d2|) and the per-column limiter.
+// FP32, four min/max-class instructions per column:
+//   u = sign(d1 d2) min(2|d1|, |d2|),  w = sign(d1 d2) min(|d1|, 2|d2|)
+//   (both >= 0 exactly when d1, d2 agree in sign), m = max(0, u, w), and the
+//   slope sign(d2) m = sign(2 d2) min(m, 2|d2|) since m <= 2|d2|: the same
+//   values as the form below (the sign flip and copysign are folded into the
+//   sign rule of the min).
+// FP64: x = d1 sign(d2), m = max(0, min(2x, |d2|), min(x, 2|d2|)), sign(d2) m.
 template <typename real, int KV>
 __device__ __forceinline__ Vk<real, KV> slope4(const Vk<real, KV> &d1, const Vk<real, KV> &d2) {
-  Vk<real, KV> x, x2, t2, r;
+  Vk<real, KV> r;
+  if constexpr (sizeof(real) == 4) {
+    const Vk<real, KV> x2 = add4(d1, d1), t2 = add4(d2, d2);
 #pragma unroll
-  for (int j = 0; j < KV; j++) x.v[j] = flip_by(d1.v[j], d2.v[j]);
-  x2 = add4(x, x);
-  t2 = add4(d2, d2);
+    for (int j = 0; j < KV; j++) {
+      const float u = min_xorsign_abs(x2.v[j], d2.v[j]), w = min_xorsign_abs(d1.v[j], t2.v[j]);
+      r.v[j] = min_xorsign_abs(max3(0.f, u, w), t2.v[j]);
+    }
+  } else {
+    Vk<real, KV> x, x2, t2;
 #pragma unroll
-  for (int j = 0; j < KV; j++) {
-    const real m = max3(real(0), fmin(x2.v[j], fabs(d2.v[j])), fmin(x.v[j], fabs(t2.v[j])));
-    r.v[j] = copysign(m, d2.v[j]);
+    for (int j = 0; j < KV; j++) x.v[j] = flip_by(d1.v[j], d2.v[j]);
+    x2 = add4(x, x);
+    t2 = add4(d2, d2);
+#pragma unroll
+    for (int j = 0; j < KV; j++) {
+      const real m = max3(real(0), fmin(x2.v[j], fabs(d2.v[j])), fmin(x.v[j], fabs(t2.v[j])));
+      r.v[j] = copysign(m, d2.v[j]);
+    }
   }
   return r;
 }
@@ -244,6 +303,26 @@ __device__ __forceinline__ void z_delta(const Vk<real, KV> &c, real gz, real zl,
   out = sub4(gl, g);
 }
 
+// As z_delta with unscaled face values: the difference (left face value -
+// right face value) of the lane's KV cells, to be multiplied by |v| h / dz.
+template <typename real, int KV>
+__device__ __forceinline__ void z_delta_v(const Vk<real, KV> &c, real zl, real zr, int gw, Vk<real, KV> &out) {
+  const real lft = zl * __shfl_up_sync(0xffffffffu, c.v[KV - 1], 1, gw);
+  const real rgt = zr * __shfl_down_sync(0xffffffffu, c.v[0], 1, gw);
+  Vk<real, KV> dl, dr;
+  dl.v[0] = c.v[0] - lft;
+#pragma unroll
+  for (int j = 0; j + 1 < KV; j++) dr.v[j] = dl.v[j + 1] = c.v[j + 1] - c.v[j];
+  dr.v[KV - 1] = rgt - c.v[KV - 1];
+  const Vk<real, KV> g = fval4(c, slope4(dl, dr));
+  const real glo = zl * __shfl_up_sync(0xffffffffu, g.v[KV - 1], 1, gw);
+  Vk<real, KV> gl;
+  gl.v[0] = glo;
+#pragma unroll
+  for (int j = 1; j < KV; j++) gl.v[j] = g.v[j - 1];
+  out = sub4(gl, g);
+}
+
 template <typename real, bool VEC, bool FZ, int KV>
 struct PlaneMarch {
   using IO = RowIO<real, VEC, FZ, KV>;
@@ -297,7 +376,7 @@ struct PlaneMarch {
     }
   }
   Vk<real, KV> w[4], st[4];  // psi rows i-3..i, psi* rows i-4..i-1 (march order)
-  Vk<real, KV> f1, f2;       // carried y face fluxes of stage 1 and stage 2
+  Vk<real, KV> f1, f2;       // carried y face values of stage 1 and stage 2 (fluxes for the CN form)
   Vk<real, KV> e1, e2;       // carried y differences of stage 1 and stage 2
 
   __device__ __forceinline__ int prow(int m) const { return fwd ? m : ny - 1 - m; }
@@ -339,18 +418,19 @@ struct PlaneMarch {
     for (int k = 0; k < 3; k++) w[k] = w[k + 1];
     w[3] = x;
 
+    // face values are kept without their speeds: psi* = psi + sy (F_lo - F_hi) + gz (G_lo - G_hi)
     if (S1) {  // row m = i-1 needs psi(m-2..m+1) = w[0..3]
       if (FIRST1) {
         const Vk<real, KV> d = sub4(w[2], w[1]);
-        f1 = face4(sy, w[1], slope4(sub4(w[1], w[0]), d));  // face m - 1/2
+        f1 = fval4(w[1], slope4(sub4(w[1], w[0]), d));  // face m - 1/2
         e1 = d;
       }
       Vk<real, KV> dz, s;
-      z_delta(w[2], gz, zl, zr, gw, dz);
+      z_delta_v(w[2], zl, zr, gw, dz);
       const Vk<real, KV> d = sub4(w[3], w[2]);
-      const Vk<real, KV> fh = face4(sy, w[2], slope4(e1, d));  // face m + 1/2
+      const Vk<real, KV> fh = fval4(w[2], slope4(e1, d));  // face m + 1/2
       e1 = d;
-      s = upd4(w[2], f1, fh, dz);
+      s = axpy4(gz, dz, axpy4(sy, sub4(f1, fh), w[2]));
       if (!IN1 || !VEC) {
 #pragma unroll
         for (int j = 0; j < KV; j++)
@@ -364,17 +444,15 @@ struct PlaneMarch {
     if (S2) {  // row m' = i-2 needs psi*(m'-2..m'+1) = st[0..3] and psi(m') = w[1]
       if (FIRST2) {
         const Vk<real, KV> d = sub4(st[2], st[1]);
-        f2 = face4(sy, st[1], slope4(sub4(st[1], st[0]), d));
+        f2 = fval4(st[1], slope4(sub4(st[1], st[0]), d));
         e2 = d;
       }
-      Vk<real, KV> dz, o;
-      z_delta(st[2], gz, zl, zr, gw, dz);
+      Vk<real, KV> dz;
+      z_delta_v(st[2], zl, zr, gw, dz);
       const Vk<real, KV> d = sub4(st[3], st[2]);
-      const Vk<real, KV> fh = face4(sy, st[2], slope4(e2, d));
+      const Vk<real, KV> fh = fval4(st[2], slope4(e2, d));
       e2 = d;
-      o = upd4(add4(w[1], st[2]), f2, fh, dz);
-#pragma unroll
-      for (int j = 0; j < KV; j++) o.v[j] *= real(0.5);
+      const Vk<real, KV> o = scale4(real(0.5), axpy4(gz, dz, axpy4(sy, sub4(f2, fh), add4(w[1], st[2]))));
       f2 = fh;
       store_row(i - 2, o);
     }

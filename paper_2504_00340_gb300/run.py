@@ -34,6 +34,8 @@ def run_spots(a) -> dict:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     sp = spot_batch()[:a.spots]
+    if a.spot_steps:  # a reduced case of the same spots (profiling): every depth cut to spot_steps
+        sp = [w.with_(n_steps=min(w.n_steps, a.spot_steps)) for w in sp]
     if a.persistent:
         if world > 1:
             raise SystemExit("--persistent runs on one GPU")
@@ -121,6 +123,7 @@ def main(argv=None):
     p.add_argument("--max-gb", type=float, default=None,
                    help="device workspace per spot bucket (GiB, default 48), or per persistent launch "
                         "(default: the free device memory)")
+    p.add_argument("--spot-steps", type=int, default=0, help="cut every spot's depth to this many steps")
     p.add_argument("--persistent", action="store_true",
                    help="--spots through the persistent batch launch (each spot on its own grid)")
     p.add_argument("--no-graph", action="store_true")
