@@ -436,8 +436,11 @@ pbs_status pbs_get_options(const pbs_ctx *ctx, pbs_options *options);
  *                   multiple of 6 and that fills the warps better, else 4)
  *   angular_form    angular substep: 0 direct, 1 TMA-staged persistent
  *                   (needs a row pitch of ny*nz elements that is a multiple of
- *                   16 bytes), 2 packed FP32x2 (FP32, ny*nz even); a form the
- *                   grid does not allow falls back to 0
+ *                   16 bytes), 2 packed FP32x2 (FP32, ny*nz even), 3 packed
+ *                   at 64 registers per thread (more CTAs per SM), 4 packed
+ *                   with two slab stacks per CTA (the second's rows prefetched
+ *                   into the L2 during the first); a form the grid does not
+ *                   allow falls back to 0
  *   source_form     BF16 source contraction on the tensor cores (mixed
  *                   precision, n_scatter > 0): 0 tile by tile, 1 pipelined
  *                   (TMA loads, MMAs and epilogue of consecutive tiles

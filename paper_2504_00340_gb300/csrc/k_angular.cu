@@ -27,6 +27,7 @@
 #include "pbs_internal.cuh"
 #include "angular_f2.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -139,36 +140,68 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
 
 // ---------------------------------------------------------------- packed FP32 form
 
-template <int NU, int NV, bool EXACT>
-__global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV))
+// MINB > 0: registers capped so that MINB CTAs fit an SM (more warps to hide
+// the load latency).  PAIR: each CTA takes two consecutive slab stacks, the
+// second's rows asked of the L2 while the first is transformed.
+template <int NU, int NV, bool EXACT, int MINB, bool PAIR>
+__global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV), MINB)
     k_angular_f2(float *__restrict__ psi, const float *__restrict__ rho_yz, const float *__restrict__ ts, int nyz,
-                 int ng, float hq, long long kgc0, const __grid_constant__ AngTables<float> tb) {
+                 int ng, float hq, long long kgc0, long long kgc_end, const __grid_constant__ AngTables<float> tb) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  angular_f2_tile<NU, NV, EXACT>(psi, rho_yz, ts, nyz, ng, hq, kgc0 + blockIdx.y, blockIdx.x, threadIdx.x, threadIdx.y,
-                                 smem_raw, tb);
+  if constexpr (PAIR) {
+    const long long k = kgc0 + 2 * (long long)blockIdx.y;
+    if (k + 1 < kgc_end && threadIdx.x == 0 && threadIdx.y < NV) {
+      const int yz = blockIdx.x * kF2X * 2;
+      const float *base = psi + (k + 1) * (long long)(NU * NV) * nyz + yz;
+#pragma unroll
+      for (int i = 0; i < NU; i++)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (long long)(threadIdx.y * NU + i) * nyz));
+    }
+    angular_f2_tile<NU, NV, EXACT>(psi, rho_yz, ts, nyz, ng, hq, k, blockIdx.x, threadIdx.x, threadIdx.y, smem_raw,
+                                   tb);
+    if (k + 1 < kgc_end) {
+      __syncthreads();  // the tile is reused
+      angular_f2_tile<NU, NV, EXACT>(psi, rho_yz, ts, nyz, ng, hq, k + 1, blockIdx.x, threadIdx.x, threadIdx.y,
+                                     smem_raw, tb);
+    }
+  } else {
+    angular_f2_tile<NU, NV, EXACT>(psi, rho_yz, ts, nyz, ng, hq, kgc0 + blockIdx.y, blockIdx.x, threadIdx.x,
+                                   threadIdx.y, smem_raw, tb);
+  }
 }
 
-template <int NU, int NV, bool EXACT>
-cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
-                  const AngTables<float> &tb) {
+template <int NU, int NV, bool EXACT, int MINB, bool PAIR>
+cudaError_t go_f2_form(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
+                       const AngTables<float> &tb) {
   constexpr int NT = NU > NV ? NU : NV;
+  auto kern = k_angular_f2<NU, NV, EXACT, MINB, PAIR>;
   const size_t smem = sizeof(float2) * NU * NV * kF2X;
   if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_angular_f2<NU, NV, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const long long total = (long long)d.ncomp * d.ng * 2;
-  for (long long k0 = 0; k0 < total; k0 += 65535) {
-    const long long cnt = total - k0 < 65535 ? total - k0 : 65535;
-    dim3 grid((d.nyz / 2 + kF2X - 1) / kF2X, (unsigned)cnt);
-    k_angular_f2<NU, NV, EXACT><<<grid, dim3(kF2X, NT), smem, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng,
-                                                                    (float)(0.25 * h), k0, tb);
+  const long long per = PAIR ? 2 : 1;  // slab stacks per CTA
+  for (long long k0 = 0; k0 < total; k0 += 65535 * per) {
+    const long long cnt = std::min(total - k0, 65535 * per);
+    dim3 grid((d.nyz / 2 + kF2X - 1) / kF2X, (unsigned)((cnt + per - 1) / per));
+    kern<<<grid, dim3(kF2X, NT), smem, lc.stream>>>(psi, rho_yz, ts, d.nyz, d.ng, (float)(0.25 * h), k0, k0 + cnt, tb);
     ++*lc.launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Packed FP32 forms (angular_form 2, 3, 4).
+template <int NU, int NV, bool EXACT>
+cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
+                  const AngTables<float> &tb) {
+  constexpr int NT = NU > NV ? NU : NV;
+  constexpr int kMinB = 1024 / (kF2X * NT);  // 64 registers per thread
+  if (lc.angular_form == 3) return go_f2_form<NU, NV, EXACT, kMinB, false>(lc, d, psi, rho_yz, ts, h, tb);
+  if (lc.angular_form == 4) return go_f2_form<NU, NV, EXACT, 0, true>(lc, d, psi, rho_yz, ts, h, tb);
+  return go_f2_form<NU, NV, EXACT, 0, false>(lc, d, psi, rho_yz, ts, h, tb);
 }
 
 // ---------------------------------------------------------------- TMA form
@@ -346,7 +379,7 @@ template <typename real, int NU, int NV, bool EXACT>
 cudaError_t go_exact(const LaunchCtx &lc, const Dims &d, real *psi, const real *rho_yz, const real *ts, double h,
                      const AngTables<real> &tb) {
   if constexpr (sizeof(real) == 4) {
-    if (lc.angular_form == 2 && (d.nyz % 2) == 0) return go_f2<NU, NV, EXACT>(lc, d, psi, rho_yz, ts, h, tb);
+    if (lc.angular_form >= 2 && (d.nyz % 2) == 0) return go_f2<NU, NV, EXACT>(lc, d, psi, rho_yz, ts, h, tb);
   }
   if (lc.angular_form == 1 && lc.err && angular_tma_ok<real>(d, psi))
     return go_tma<real, NU, NV, EXACT>(lc, d, psi, rho_yz, ts, h, tb);

@@ -115,6 +115,7 @@ def main(argv=None):
     p.add_argument("--physics-model", type=int, choices=[0, 1],
                    help="0: Bragg-Kleeman + Highland, 1: the paper's Appendix A tables")
     p.add_argument("--energy-form", type=int, choices=[0, 1], help="FP32 energy kernel form (default: tuned)")
+    p.add_argument("--angular-form", type=int, choices=[0, 1, 2, 3, 4], help="angular kernel form (default: tuned)")
     p.add_argument("--transport", choices=["heun", "cn"], default="heun",
                    help="transport integrator: explicit trapezoid (default) or CN with the slope lagged")
     p.add_argument("--straggling-integrator", choices=["explicit", "cn"], default="explicit",
@@ -165,7 +166,8 @@ def main(argv=None):
     import torch
     torch.cuda.set_device(0)
     out, dose, flu = march(binding, w, steps, prec, autotune=a.autotune, profile=not a.no_profile,
-                           energy_form=a.energy_form, transport=a.transport, strag_int=a.straggling_integrator)
+                           energy_form=a.energy_form, transport=a.transport, strag_int=a.straggling_integrator,
+                           angular_form=a.angular_form)
     out.update({"workload": w.name, "ny": w.ny, "nz": w.nz, "ng": w.ng, "n_scatter": w.n_scatter,
                 "medium": w.medium, "physics_model": w.physics.get("model", 0),
                 "straggling": w.physics.get("t_scale", 0.0), "transport": a.transport,
@@ -181,7 +183,7 @@ def main(argv=None):
 
 
 def march(binding, w, steps, prec, autotune=False, profile=True, energy_form=None, transport="heun",
-          strag_int="explicit"):
+          strag_int="explicit", angular_form=None):
     """The whole march of workload w (steps depth steps) in the given
     precision: device time by CUDA events around step + flush on the
     context's stream; per-kernel times when profiling."""
@@ -196,6 +198,8 @@ def march(binding, w, steps, prec, autotune=False, profile=True, energy_form=Non
             s.autotune(2)
         if energy_form is not None:
             s.set_tuning(energy_form=energy_form)
+        if angular_form is not None:
+            s.set_tuning(angular_form=angular_form)
         s.set_profiling(profile)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()

@@ -154,11 +154,15 @@ def test_transport_substep(orc, precision, tol, ny, nz, cols):
     s.close()
 
 
+@pytest.mark.parametrize("form", [2, 3, 4])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("nu,nv", [(8, 8), (16, 16), (4, 6)])
-def test_angular_substep(orc, precision, tol, nu, nv):
+def test_angular_substep(orc, precision, tol, nu, nv, form):
+    """Packed forms 2 (one slab stack per CTA), 3 (64 registers) and 4 (two
+    stacks per CTA); FP64 and the odd lateral count take the direct form."""
     grid = _grid(5, 9, nu, nv, 3)  # nyz = 45: ragged against the 32/16-point tiles
     s, o, rho = _pair(orc, grid, 2, 0.05, 1, precision)
+    s.set_tuning(angular_form=form)
     psi = [random_state((3, 2, nv, nu, 5, 9), seed=7 + k) for k in range(2)]
     for k in range(2):
         s.write_psi(k, psi[k])
@@ -169,7 +173,7 @@ def test_angular_substep(orc, precision, tol, nu, nv):
     s.close()
 
 
-@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("form", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("nu,nv", [(16, 16), (8, 8)])
 def test_angular_exact_integrator(orc, precision, tol, form, nu, nv):
