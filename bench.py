@@ -175,7 +175,7 @@ def run_ours(a):
     s.set_material(rho)
     s.launch_beam(**w.beam)
     # launch shapes and kernel forms from the library's autotuner (restarts the beam)
-    s.autotune(2)
+    s.autotune(4)
     tuning = s.tuning
     s.step(W)
     s.flush()

@@ -135,8 +135,12 @@ typedef struct pbs_ctx pbs_ctx;
  * ng > 2048). */
 pbs_status pbs_create(pbs_ctx **out, const pbs_grid *grid, int precision, void *stream);
 
-/* Bytes of device workspace the context needs (psi of all K+1 components,
- * source buffers, material, dose and fluence tallies, tables). */
+/* Bytes of device workspace the context needs: psi of all K+1 components
+ * (the primary and scattered fields of the source iteration, Section 3.1,
+ * Eq. pri-se, each with both DG coefficients of Section 3.2), the source
+ * buffers of Remark 1, the density slabs, the dose and fluence tallies of
+ * Section 4 and the coefficient tables.  The library's own addition: the
+ * paper names no memory layout. */
 pbs_status pbs_workspace_size(const pbs_ctx *ctx, size_t *bytes);
 
 /* Bind caller-owned device memory of at least pbs_workspace_size bytes,
@@ -197,7 +201,14 @@ pbs_status pbs_get_tables(const pbs_ctx *ctx, double *s_face, double *ts, double
                           double *u, double *v);
 
 /* Density rho[s][p][q] (g/cm^3) for depth steps s = 0..n_slabs-1
- * (n_slabs <= grid.nx).  Step s uses slab s in all five substeps. */
+ * (n_slabs <= grid.nx), host FP64, copied during the call.  The density
+ * multiplies the stopping power and the removal cross section of the energy
+ * operator (Eq. 0041-do) and the scattering power of the angular subsystem
+ * (Section 3.4); Section 4's heterogeneous phantoms (slabs, inserts) are
+ * density fields.  Step s uses slab s in all five substeps (the cell-centred
+ * reading of a depth step).  PBS_ERR_ARG for n_slabs out of range or a
+ * negative or non-finite density; PBS_ERR_STATE before a workspace is
+ * bound. */
 pbs_status pbs_set_material(pbs_ctx *ctx, const double *rho, int n_slabs);
 
 /* Project the beam of Eq. (bdy) onto psi_p (cell averages in y, z, u, v;
@@ -309,7 +320,7 @@ pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
  * different depth and size fill the GPU together with no bucketing and no
  * empty energy groups.  Every tile is the same device code as the matching
  * block of the per-substep kernels, so each beam's psi equals its own
- * pbs_run with the tuning {energy_angles 8, energy_form 1, angular_form 2}
+ * pbs_run with the tuning {energy_angles 8, energy_form 1, angular_form 2, 3 or 4}
  * bit for bit (the dose up to the order of its atomic FP64 sums).
  *   use_graph      nonzero: record the batch (every beam's restart from its
  *                  projection, the queue reset, the launch) into a CUDA graph
@@ -495,9 +506,13 @@ pbs_status pbs_get_depth(const pbs_ctx *ctx, int *steps_done);
 pbs_status pbs_read_dose(pbs_ctx *ctx, double *host_out, size_t n);
 
 /* Planar fluence F[b][s][p][q] = du dv sum_{k,g,a} psi^1 dE (protons/cm^2)
- * of beam b at depths s*dx, s = 0..n_planes-1 (s = 0 is the entrance); n
- * must equal n_beams*n_planes*ny*nz with n_planes <= steps done + 1.
- * Synchronises. */
+ * of beam b at depths s*dx, s = 0..n_planes-1 (s = 0 is the entrance): the
+ * zeroth angular and energy moment of the phase-space density of Section 2
+ * (integrating the DG expansion of Section 3.2 over each group leaves
+ * psi^1 dE), summed over the primary and scattered fields; the particle
+ * count whose loss the removal term of Eq. 0041-do drives.  n must equal
+ * n_beams*n_planes*ny*nz with n_planes <= steps done + 1 (PBS_ERR_ARG
+ * otherwise).  Synchronises. */
 pbs_status pbs_read_fluence(pbs_ctx *ctx, double *host_out, size_t n);
 
 /* Copy component k of psi to / from the host as FP64 in the logical layout

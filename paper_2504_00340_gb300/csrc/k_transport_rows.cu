@@ -184,8 +184,10 @@ struct MarchCn {
 //
 // CN: Crank-Nicolson with the slope lagged (Remark 3; see launch_transport_rows)
 // instead of the explicit trapezoid; one segment per row.
-template <typename real, bool VEC, bool FZ, int KV, bool CN>
-__global__ void __launch_bounds__(kWarps * 32) k_transport_rows(real *__restrict__ psi, long long nplanes, int ny, int nz,
+// MINB > 1: registers capped so that MINB CTAs fit an SM (the 8-column
+// march at three CTAs per SM).
+template <typename real, bool VEC, bool FZ, int KV, bool CN, int MINB = 1>
+__global__ void __launch_bounds__(kWarps * 32, MINB) k_transport_rows(real *__restrict__ psi, long long nplanes, int ny, int nz,
                                                                 int na, int a0, int na_half, int nu, int nv, real du,
                                                                 real dv, real ky, real kz, int nseg, int seg_w, int gw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -249,6 +251,15 @@ cudaError_t launch_kv(const LaunchCtx &lc, const Dims &d, real *psi, double tau,
     const long long nplanes = nstacks * na_half;
     auto kern = vec ? (fz ? k_transport_rows<real, true, true, KV, CN> : k_transport_rows<real, true, false, KV, CN>)
                     : (fz ? k_transport_rows<real, false, true, KV, CN> : k_transport_rows<real, false, false, KV, CN>);
+    // the FP32 march needs a few registers more than some residencies leave
+    // (4 columns: ~135, 8 columns: ~175): asked for 4 (4 columns) or 3 (8
+    // columns) CTAs per SM, take the form whose registers are capped for it
+    if (sizeof(real) == 4 && !CN && vec && ((KV == 4 && lc.transport_ctas == 4) || (KV == 8 && lc.transport_ctas == 3))) {
+      if (KV == 4)
+        kern = fz ? k_transport_rows<real, true, true, KV, CN, 4> : k_transport_rows<real, true, false, KV, CN, 4>;
+      else
+        kern = fz ? k_transport_rows<real, true, true, KV, CN, 3> : k_transport_rows<real, true, false, KV, CN, 3>;
+    }
     cudaError_t e;
     if (smem > 48 * 1024 &&
         (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)

@@ -78,7 +78,7 @@ struct pbs_ctx {
   size_t rsize, ssize;  // element sizes of real and of the source storage
   long long launches = 0;
   // launch shapes (pbs_autotune / pbs_set_tuning)
-  pbs_tuning tune{8, 1, 0, 0, 2, 1};
+  pbs_tuning tune{8, 1, 0, 0, 3, 1};
   pbs_options opts{0, 0, 0};
   // whole-march CUDA graph (pbs_run with use_graph)
   cudaStream_t cap_stream = nullptr;

@@ -116,6 +116,9 @@ def main(argv=None):
                    help="0: Bragg-Kleeman + Highland, 1: the paper's Appendix A tables")
     p.add_argument("--energy-form", type=int, choices=[0, 1], help="FP32 energy kernel form (default: tuned)")
     p.add_argument("--angular-form", type=int, choices=[0, 1, 2, 3, 4], help="angular kernel form (default: tuned)")
+    p.add_argument("--energy-angles", type=int, choices=[4, 8, 16], help="angles per energy block")
+    p.add_argument("--transport-cols", type=int, choices=[4, 6, 8], help="transport columns per lane")
+    p.add_argument("--transport-ctas", type=int, help="resident transport CTAs per SM (0: as many as fit)")
     p.add_argument("--transport", choices=["heun", "cn"], default="heun",
                    help="transport integrator: explicit trapezoid (default) or CN with the slope lagged")
     p.add_argument("--straggling-integrator", choices=["explicit", "cn"], default="explicit",
@@ -167,7 +170,9 @@ def main(argv=None):
     torch.cuda.set_device(0)
     out, dose, flu = march(binding, w, steps, prec, autotune=a.autotune, profile=not a.no_profile,
                            energy_form=a.energy_form, transport=a.transport, strag_int=a.straggling_integrator,
-                           angular_form=a.angular_form)
+                           angular_form=a.angular_form,
+                           tuning={k: getattr(a, k) for k in ("energy_angles", "transport_cols", "transport_ctas")
+                                   if getattr(a, k) is not None})
     out.update({"workload": w.name, "ny": w.ny, "nz": w.nz, "ng": w.ng, "n_scatter": w.n_scatter,
                 "medium": w.medium, "physics_model": w.physics.get("model", 0),
                 "straggling": w.physics.get("t_scale", 0.0), "transport": a.transport,
@@ -183,7 +188,7 @@ def main(argv=None):
 
 
 def march(binding, w, steps, prec, autotune=False, profile=True, energy_form=None, transport="heun",
-          strag_int="explicit", angular_form=None):
+          strag_int="explicit", angular_form=None, tuning=None):
     """The whole march of workload w (steps depth steps) in the given
     precision: device time by CUDA events around step + flush on the
     context's stream; per-kernel times when profiling."""
@@ -200,6 +205,8 @@ def march(binding, w, steps, prec, autotune=False, profile=True, energy_form=Non
             s.set_tuning(energy_form=energy_form)
         if angular_form is not None:
             s.set_tuning(angular_form=angular_form)
+        if tuning:
+            s.set_tuning(**tuning)
         s.set_profiling(profile)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
