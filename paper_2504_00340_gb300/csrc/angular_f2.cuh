@@ -51,6 +51,9 @@ void fill_tables(AngTables<real> &tb, int nu, int nv, double du, double dv) {
                                   (2.0 * std::cos(pi * (n + 1) / (nv + 1)) - 2.0) / (dv * dv));
 }
 
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 __device__ __forceinline__ double mode_factor(double den) { return 2.0 / den - 1.0; }
 __device__ __forceinline__ float mode_factor(float den) { return __fdividef(2.0f, den) - 1.0f; }
 
@@ -66,8 +69,24 @@ __device__ __forceinline__ float mode_scale(float ql) {
   return EXACT ? expf(2.0f * ql) : mode_factor(1.0f - ql);
 }
 
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// y *= the mode's factor at two lateral points (q = h kappa / 4 of each, l
+// the mode's eigenvalue).  Crank-Nicolson on FP32x2 pairs: den = 1 - q l
+// (one packed FMA), the two reciprocals, 2 / den - 1 (one packed FMA), one
+// packed multiply; the exact exponential per point.
+template <bool EXACT>
+__device__ __forceinline__ float2 scale_mode2(float2 y, float2 q, float l) {
+  if constexpr (EXACT) {
+    y.x *= mode_scale<true>(q.x * l);
+    y.y *= mode_scale<true>(q.y * l);
+    return y;
+  } else {
+    const float2 den = fma2(q, make_float2(-l, -l), make_float2(1.f, 1.f));
+    float2 r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(den.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(den.y));
+    return __fmul2_rn(y, fma2(make_float2(2.f, 2.f), r, make_float2(-1.f, -1.f)));
+  }
+}
 
 // dst_apply on pairs (two lateral points per register pair).
 template <int N>
@@ -131,8 +150,7 @@ __device__ __forceinline__ void angular_f2_tile(float *__restrict__ psi, const f
 #pragma unroll
     for (int n = 0; n < NV; n++) {
       const float l = tb.lam[n * NU + t];
-      y[n].x *= mode_scale<EXACT>(q.x * l);
-      y[n].y *= mode_scale<EXACT>(q.y * l);
+      y[n] = scale_mode2<EXACT>(y[n], q, l);
     }
     dst_apply2<NV>(y, c);
 #pragma unroll
@@ -208,8 +226,7 @@ __device__ __forceinline__ void angular_f2_tiles(float *__restrict__ psi, const 
 #pragma unroll
       for (int n = 0; n < NV; n++) {
         const float l = tb.lam[n * NU + t];
-        y[n].x *= mode_scale<EXACT>(q.x * l);
-        y[n].y *= mode_scale<EXACT>(q.y * l);
+        y[n] = scale_mode2<EXACT>(y[n], q, l);
       }
       dst_apply2<NV>(y, c);
 #pragma unroll
