@@ -80,6 +80,29 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
+// The NK MMAs (K = 16 each) of one accumulator tile: the first overwrites D,
+// the others accumulate.  A descriptor's start address (16-byte units, bits
+// 0-13; shared addresses stay below 2^18 bytes, so the field never carries
+// into the rest of the low word) steps by 256 bytes along K for A and by
+// BSTEP 16-byte units for B: one 32-bit add per descriptor per MMA.
+__device__ __forceinline__ void mma_bf16_w(uint32_t tmem_d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                           uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+      "mov.b64 da, {%1, %2};\n\t"
+      "mov.b64 db, {%3, %4};\n\t"
+      "setp.ne.b32 p, %6, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(tmem_d),
+      "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+template <int NK, uint32_t BSTEP>
+__device__ __forceinline__ void mma_chain(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc) {
+  const uint32_t alo = (uint32_t)ad, ahi = (uint32_t)(ad >> 32), blo = (uint32_t)bd, bhi = (uint32_t)(bd >> 32);
+#pragma unroll
+  for (int j = 0; j < NK; j++) mma_bf16_w(d, alo + 16u * j, ahi, blo + BSTEP * j, bhi, idesc, j > 0 ? 1u : 0u);
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
   asm volatile(
@@ -94,6 +117,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// 256-bit global store of eight 32-bit words (32-byte aligned address).
+__device__ __forceinline__ void st_global_v8(void *p, const uint32_t *w) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+               "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -244,20 +274,26 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
 
 // ---------------------------------------------------------------- pipelined form
 //
-// Warp-specialised and pipelined: lane 0 of warp 0 issues the TMA loads and
-// the MMAs, warps 1-8 drain the accumulators.  P^2_g (all M rows, whole K) is
+// Warp-specialised and pipelined: lane 0 of warp 0 issues the TMA loads, lane
+// 0 of warp 1 the MMAs, warps 2-9 drain the accumulators.  P^2_g (all M rows, whole K) is
 // loaded once per group by one 5-D TMA copy straight into the canonical K-major
 // core-matrix layout; each R tile (whole K x 64 lateral points) by one 3-D TMA
 // copy into the canonical MN-major layout, kPipeMax stages ahead; the MMAs of a
-// tile go into one of two TMEM accumulators while the epilogue warps read the
-// other, so loads, MMAs and stores of consecutive tiles overlap.  Two epilogue
-// warps share each TMEM lane quadrant, one per 32-column half of the tile.
+// tile go into one of four TMEM accumulators while the epilogue warps drain
+// the others, so loads, MMAs and stores of consecutive tiles overlap and the
+// MMAs run up to three tiles ahead of the stores.  Two epilogue warps share
+// each TMEM lane quadrant, one per 32-column half of the tile; each thread
+// writes its row's 32 BF16 values as two whole 32-byte sectors.  The MMAs of a
+// tile are issued from descriptors stepped by one 32-bit add each (the start
+// address field moves along K), so the issuing thread keeps the tensor pipe
+// fed; the loads wait on nothing but free stages.
 // Each CTA walks a contiguous range of (group, N-tile) tiles; every wait is
 // bounded.
 
 constexpr int kPipeMax = 4;                      // R stages (3 when na = 256: shared memory)
-constexpr int kPipeThreads = 288;                // warp 0: producer + MMA issue; warps 1-8: epilogue
-constexpr int kEpiThreads = kPipeThreads - 32;
+constexpr int kPipeThreads = 320;                // warp 0: TMA producer; warp 1: MMA issue; warps 2-9: epilogue
+constexpr int kEpiThreads = kPipeThreads - 64;
+constexpr int kAcc = 4;                          // TMEM accumulators (4 x 128 columns when na = 256)
 constexpr long long kPipeWait = 2000000000LL;    // ~1 s at 2 GHz
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
@@ -302,16 +338,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   const unsigned b_bytes = (unsigned)na * kTN * 2u;
   unsigned char *sA = smem_raw;
   unsigned char *sB = smem_raw + a_bytes;  // stage s at sB + s * b_bytes
-  __shared__ __align__(8) uint64_t full_b[kPipeMax], empty_b[kPipeMax], acc_full[2], acc_empty[2], a_full;
+  __shared__ __align__(8) uint64_t full_b[kPipeMax], empty_b[kPipeMax], acc_full[kAcc], acc_empty[kAcc], a_full, a_empty;
   __shared__ uint32_t tmem_base_s;
   __shared__ int s_abort;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int acc_cols = mh * kTN;  // columns of one accumulator (both M halves)
+  const uint32_t tmem_cols = (uint32_t)(kAcc * acc_cols);  // 512 (na = 256) or 256 (na = 128)
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
-                 "r"(2 * kTmemCols)
+                 "r"(tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -320,11 +357,12 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       mbar_init(&full_b[i], 1);
       mbar_init(&empty_b[i], 1);
     }
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < kAcc; i++) {
       mbar_init(&acc_full[i], 1);
       mbar_init(&acc_empty[i], kEpiThreads);
     }
     mbar_init(&a_full, 1);
+    mbar_init(&a_empty, 1);
     fence_mbar_init();
     s_abort = 0;
   }
@@ -342,61 +380,90 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 
   if (warp == 0) {
     if (lane == 0 && count > 0) {
-      const uint32_t idesc = idesc_bf16(kTM, kTN);
-      const uint32_t lbo = 128, sbo = (uint32_t)kcm * 128;
-      int issued = 0, cur_gb = -1, consumed = 0, committed = 0;
-      unsigned a_phase = 0;
+      // TMA producer: R tiles nstages ahead; P^2 of a new group once the MMAs
+      // reading the old one have completed (a_empty, committed by the MMA lane)
+      int issued = 0, cur_gb = -1, n_a = 0;
       bool ok = true, a_pending = false;
-      for (int i = 0; i < count && ok; i++) {
-        // keep the R loads nstages tiles ahead
-        while (ok && issued < count && issued < i + nstages) {
-          const int s = issued % nstages;
-          if (issued >= nstages)
-            ok = mbar_wait_bounded(&empty_b[s], (unsigned)((issued / nstages - 1) & 1), kPipeWait);
-          if (!ok) break;
-          const long long t = t_beg + issued;
-          const int gb = (int)(t / ntn), nt = (int)(t % ntn);
-          mbar_arrive_expect_tx(&full_b[s], b_bytes);
-          if (SWB)
-            tma_load_2d(sB + (size_t)s * b_bytes, &mapB, nt * kTN, gb * na, &full_b[s]);
-          else
-            tma_load_3d(sB + (size_t)s * b_bytes, &mapB, 0, gb * na, nt * (kTN / 8), &full_b[s]);
-          issued++;
-        }
+      for (; issued < count && ok; issued++) {
+        if (*reinterpret_cast<volatile int *>(&s_abort)) break;
+        const int s = issued % nstages;
+        if (issued >= nstages) ok = mbar_wait_bounded(&empty_b[s], (unsigned)((issued / nstages - 1) & 1), kPipeWait);
         if (!ok) break;
-        const long long t = t_beg + i;
-        const int gb = (int)(t / ntn);
+        const long long t = t_beg + issued;
+        const int gb = (int)(t / ntn), nt = (int)(t % ntn);
+        mbar_arrive_expect_tx(&full_b[s], b_bytes);
+        if (SWB)
+          tma_load_2d(sB + (size_t)s * b_bytes, &mapB, nt * kTN, gb * na, &full_b[s]);
+        else
+          tma_load_3d(sB + (size_t)s * b_bytes, &mapB, 0, gb * na, nt * (kTN / 8), &full_b[s]);
         if (gb != cur_gb) {
-          // P^2 of the new group: every MMA reading the old one has completed
-          if (i > 0) ok = mbar_wait_bounded(&acc_full[(i - 1) & 1], (unsigned)(((i - 1) >> 1) & 1), kPipeWait);
-          if (!ok) break;
+          if (n_a > 0) ok = mbar_wait_bounded(&a_empty, (unsigned)((n_a - 1) & 1), kPipeWait);
+          if (!ok) {
+            issued++;  // this tile's R copy is in flight
+            break;
+          }
           mbar_arrive_expect_tx(&a_full, a_bytes);
           tma_load_5d(sA, &mapA, 0, 0, 0, 0, gb % ng, &a_full);
           a_pending = true;
-          ok = mbar_wait_bounded(&a_full, a_phase, kPipeWait);
+          n_a++;
+          cur_gb = gb;
+        }
+      }
+      if (!ok) {
+        *reinterpret_cast<volatile int *>(&s_abort) = 1;
+        if (err) {
+          atomicAdd(err, 1);
+          atomicExch(err + 1, kErrTimeoutSourceMma);
+        }
+      }
+      // every copy this lane issued lands before the CTA exits (bounded): the
+      // last copy into each stage, and the last P^2 copy
+      for (int k = (issued > nstages ? issued - nstages : 0); k < issued; k++)
+        mbar_wait_bounded(&full_b[k % nstages], (unsigned)((k / nstages) & 1), kPipeWait / 8);
+      if (a_pending) mbar_wait_bounded(&a_full, (unsigned)((n_a - 1) & 1), kPipeWait / 8);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && count > 0) {
+      // MMA issue: one accumulator tile per R tile, four accumulators in turn
+      const uint32_t idesc = idesc_bf16(kTM, kTN);
+      const uint32_t lbo = 128, sbo = (uint32_t)kcm * 128;
+      const uint64_t adesc = smem_desc(smem_u32(sA), lbo, sbo);
+      int cur_gb = -1, n_a = 0, committed = 0;
+      bool ok = true;
+      for (int i = 0; i < count && ok; i++) {
+        const long long t = t_beg + i;
+        const int gb = (int)(t / ntn);
+        if (gb != cur_gb) {
+          // release the old P^2 (completes when every MMA issued so far has),
+          // then wait for the new one
+          if (n_a > 0) mma_commit(&a_empty);
+          ok = mbar_wait_bounded(&a_full, (unsigned)(n_a & 1), kPipeWait);
           if (!ok) break;
-          a_pending = false;
-          a_phase ^= 1u;
+          n_a++;
           cur_gb = gb;
         }
         const int s = i % nstages;
         ok = mbar_wait_bounded(&full_b[s], (unsigned)((i / nstages) & 1), kPipeWait);
         if (!ok) break;
-        consumed = i + 1;
-        const int acc = i & 1;
-        if (i >= 2) ok = mbar_wait_bounded(&acc_empty[acc], (unsigned)(((i >> 1) - 1) & 1), kPipeWait);
+        const int acc = i % kAcc;
+        if (i >= kAcc) ok = mbar_wait_bounded(&acc_empty[acc], (unsigned)((i / kAcc - 1) & 1), kPipeWait);
         if (!ok) break;
+        if (*reinterpret_cast<volatile int *>(&s_abort)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
+        // K = 16 per MMA: two 8-row groups of the B tile (2 x 1024 B swizzled,
+        // or 2 core matrices of 128 B) and 2 core matrices of A
         const uint32_t b0 = smem_u32(sB + (size_t)s * b_bytes);
+        const uint64_t bd0 = SWB ? smem_desc_sw128(b0, 0u, 1024u) : smem_desc(b0, lbo, sbo);
         for (int h = 0; h < mh; h++) {
-          const uint32_t a0 = smem_u32(sA) + (uint32_t)h * (kTM / 8) * kcm * 128u;
+          const uint64_t ad0 = adesc + (uint64_t)(((uint32_t)h * (kTM / 8) * kcm * 128u) >> 4);
           const uint32_t d = tmem + (uint32_t)(acc * acc_cols + h * kTN);
-          for (int j = 0; j < na / 16; j++) {
-            // K = 16 per MMA: two 8-row groups of the B tile (2 x 1024 B swizzled, or 2 core matrices of 128 B)
-            const uint64_t bd = SWB ? smem_desc_sw128(b0 + (uint32_t)j * 2048u, 0u, 1024u)
-                                    : smem_desc(b0 + (uint32_t)j * 256u, lbo, sbo);
-            mma_bf16(d, smem_desc(a0 + (uint32_t)j * 256u, lbo, sbo), bd, idesc, j > 0);
-          }
+          if (na == 256)
+            mma_chain<16, SWB ? 128u : 16u>(d, ad0, bd0, idesc);
+          else
+            mma_chain<8, SWB ? 128u : 16u>(d, ad0, bd0, idesc);
         }
         mma_commit(&empty_b[s]);
         mma_commit(&acc_full[acc]);
@@ -408,55 +475,52 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
           atomicAdd(err, 1);
           atomicExch(err + 1, kErrTimeoutSourceMma);
         }
-        // let the copies still in flight land (bounded) before the CTA exits
-        if (a_pending) mbar_wait_bounded(&a_full, a_phase, kPipeWait / 8);
-        for (int k = consumed; k < issued; k++)
-          mbar_wait_bounded(&full_b[k % nstages], (unsigned)((k / nstages) & 1), kPipeWait / 8);
       }
       // the last commit covers every MMA issued (tile committed - 1; fewer than
       // count after a timeout): wait for it before TMEM is released
       if (committed > 0)
-        mbar_wait_bounded(&acc_full[(committed - 1) & 1], (unsigned)(((committed - 1) >> 1) & 1), kPipeWait);
+        mbar_wait_bounded(&acc_full[(committed - 1) % kAcc], (unsigned)(((committed - 1) / kAcc) & 1), kPipeWait);
     }
   } else {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of each M half,
-    // columns 32 half .. +31 of the tile
+    // columns 32 half .. +31 of the tile (half = (w - 2) / 4)
     const int q = warp & 3;
-    const int half = (warp - 1) >> 2;
+    const int half = (warp - 2) >> 2;
+    // BF16 rows of a multiple of 32 bytes from a 32-byte aligned base
+    const bool sector_rows = (nyz & 15) == 0 && (reinterpret_cast<uintptr_t>(src) & 31) == 0;
     for (int i = 0; i < count; i++) {
-      const int acc = i & 1;
-      const bool ok = mbar_wait_bounded(&acc_full[acc], (unsigned)((i >> 1) & 1), kPipeWait);
+      const int acc = i % kAcc;
+      const bool ok = mbar_wait_bounded(&acc_full[acc], (unsigned)((i / kAcc) & 1), kPipeWait);
       // warp-uniform decision: the TMEM loads below are warp-collective
       if (!__all_sync(0xffffffffu, ok && *reinterpret_cast<volatile int *>(&s_abort) == 0)) break;
       tc_fence_after();
       const long long t = t_beg + i;
-      const int gb = (int)(t / ntn), n0 = (int)(t % ntn) * kTN;
+      const int gb = (int)(t / ntn);
+      const int n1 = (int)(t % ntn) * kTN + half * 32;  // first lateral point of this warp's columns
       for (int h = 0; h < mh; h++) {
         const int m = h * kTM + q * 32 + lane;
-        __nv_bfloat16 *out = src + ((long long)gb * na + m) * nyz + n0;
-        {
-          float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + h * kTN + half * 32), v);
-          const int nb = half * 32;
-          if (n0 + nb + 32 <= nyz) {
+        __nv_bfloat16 *out = src + ((long long)gb * na + m) * nyz + n1;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * acc_cols + h * kTN + half * 32), v);
+        if (n1 + 32 <= nyz) {
+          uint32_t w[16];
 #pragma unroll
-            for (int c = 0; c < 4; c++) {
-              uint4 pk;
-              __nv_bfloat162 h0 = __floats2bfloat162_rn(v[c * 8 + 0] * dudv, v[c * 8 + 1] * dudv);
-              __nv_bfloat162 h1 = __floats2bfloat162_rn(v[c * 8 + 2] * dudv, v[c * 8 + 3] * dudv);
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[c * 8 + 4] * dudv, v[c * 8 + 5] * dudv);
-              __nv_bfloat162 h3 = __floats2bfloat162_rn(v[c * 8 + 6] * dudv, v[c * 8 + 7] * dudv);
-              pk.x = *reinterpret_cast<uint32_t *>(&h0);
-              pk.y = *reinterpret_cast<uint32_t *>(&h1);
-              pk.z = *reinterpret_cast<uint32_t *>(&h2);
-              pk.w = *reinterpret_cast<uint32_t *>(&h3);
-              *reinterpret_cast<uint4 *>(out + nb + c * 8) = pk;
-            }
+          for (int c = 0; c < 16; c++) {
+            __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * c] * dudv, v[2 * c + 1] * dudv);
+            w[c] = *reinterpret_cast<uint32_t *>(&b);
+          }
+          if (sector_rows) {
+            st_global_v8(out, w);
+            st_global_v8(out + 16, w + 8);
           } else {
 #pragma unroll
-            for (int e = 0; e < 32; e++)
-              if (n0 + nb + e < nyz) out[nb + e] = __float2bfloat16_rn(v[e] * dudv);
+            for (int c = 0; c < 4; c++)
+              *reinterpret_cast<uint4 *>(out + c * 8) = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
           }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 32; e++)
+            if (n1 + e < nyz) out[e] = __float2bfloat16_rn(v[e] * dudv);
         }
       }
       tc_fence_before();
@@ -467,7 +531,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
   __syncthreads();
   tc_fence_after();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
 // Tensor maps of the pipelined form: P^2 as [g][m8][kc][m7][k8] (5-D box = one
@@ -526,7 +590,7 @@ cudaError_t launch_source_tc(const LaunchCtx &lc, const Dims &d, const __nv_bflo
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long ntot = (long long)d.ng * nbatch * ((d.nyz + kTN - 1) / kTN);
-    long long blocks = lc.num_sms;  // one CTA per SM (shared memory; TMEM 256 columns)
+    long long blocks = lc.num_sms;  // one CTA per SM (shared memory; TMEM up to all 512 columns)
     if (blocks > ntot) blocks = ntot;
     kern<<<(unsigned)blocks, kPipeThreads, smem, lc.stream>>>(ma, mb, src, d.na, d.nyz, d.ng, d.ng * nbatch, nstages,
                                                               (float)dudv, lc.err);

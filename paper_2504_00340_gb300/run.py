@@ -119,6 +119,8 @@ def main(argv=None):
     p.add_argument("--energy-angles", type=int, choices=[4, 8, 16], help="angles per energy block")
     p.add_argument("--transport-cols", type=int, choices=[4, 6, 8], help="transport columns per lane")
     p.add_argument("--transport-ctas", type=int, help="resident transport CTAs per SM (0: as many as fit)")
+    p.add_argument("--source-form", type=int, choices=(0, 1, 2),
+                   help="BF16 source contraction: 0 tile by tile, 1 pipelined, 2 pipelined with swizzled R tiles")
     p.add_argument("--transport", choices=["heun", "cn"], default="heun",
                    help="transport integrator: explicit trapezoid (default) or CN with the slope lagged")
     p.add_argument("--straggling-integrator", choices=["explicit", "cn"], default="explicit",
@@ -171,7 +173,8 @@ def main(argv=None):
     out, dose, flu = march(binding, w, steps, prec, autotune=a.autotune, profile=not a.no_profile,
                            energy_form=a.energy_form, transport=a.transport, strag_int=a.straggling_integrator,
                            angular_form=a.angular_form,
-                           tuning={k: getattr(a, k) for k in ("energy_angles", "transport_cols", "transport_ctas")
+                           tuning={k: getattr(a, k)
+                                   for k in ("energy_angles", "transport_cols", "transport_ctas", "source_form")
                                    if getattr(a, k) is not None})
     out.update({"workload": w.name, "ny": w.ny, "nz": w.nz, "ng": w.ng, "n_scatter": w.n_scatter,
                 "medium": w.medium, "physics_model": w.physics.get("model", 0),
