@@ -24,6 +24,27 @@ __global__ void k_init(real *__restrict__ psi0, const double *__restrict__ fe, c
   }
 }
 
+// The same product with the lateral factors converted once per block into
+// shared memory (ny + nz values) and the lateral points walked row by row:
+// no division and no FP64 conversion per element.  Same arithmetic order.
+template <typename real>
+__global__ void k_init_rows(real *__restrict__ psi0, const double *__restrict__ fe, const double *__restrict__ fa,
+                            const double *__restrict__ fy, const double *__restrict__ fz, Dims d) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real *sy = reinterpret_cast<real *>(smem_raw);
+  real *sz = sy + d.ny;
+  for (int i = threadIdx.x; i < d.ny; i += blockDim.x) sy[i] = (real)fy[i];
+  for (int i = threadIdx.x; i < d.nz; i += blockDim.x) sz[i] = (real)fz[i];
+  __syncthreads();
+  const int row = blockIdx.y, a = blockIdx.x;
+  const real f = (real)(fe[row] * fa[a]);
+  real *out = psi0 + (long long)row * d.lanes + (long long)a * d.nyz;
+  for (int p = 0; p < d.ny; p++) {
+    const real fp = f * sy[p];
+    for (int q = threadIdx.x; q < d.nz; q += blockDim.x) out[p * d.nz + q] = fp * sz[q];
+  }
+}
+
 // Planar fluence of the current state: flu[yz] += scale * sum_{k,g,a} dE_g psi^1
 // (one thread per (yz, a); the sum over k and g in the working precision).
 template <typename real>
@@ -140,7 +161,11 @@ template <typename real>
 cudaError_t launch_init(const LaunchCtx &lc, const Dims &d, real *psi0, const double *fe, const double *fa,
                         const double *fy, const double *fz) {
   dim3 grid((unsigned)d.na, (unsigned)(2 * d.ng));
-  k_init<real><<<grid, 256, 0, lc.stream>>>(psi0, fe, fa, fy, fz, d);
+  const size_t smem = (size_t)(d.ny + d.nz) * sizeof(real);
+  if (smem <= 48 * 1024)
+    k_init_rows<real><<<grid, d.nz >= 256 ? 256 : 128, smem, lc.stream>>>(psi0, fe, fa, fy, fz, d);
+  else
+    k_init<real><<<grid, 256, 0, lc.stream>>>(psi0, fe, fa, fy, fz, d);
   ++*lc.launches;
   return cudaGetLastError();
 }

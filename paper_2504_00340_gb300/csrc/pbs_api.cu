@@ -510,8 +510,8 @@ void build_tables(pbs_ctx *c, const pbs_physics &ph) {
   transfer_tables(c, ph.lambda_p1);
   // angular transfer: Gamma density of the angle between (1,u',v') and (1,u,v),
   // normalised so that sum_a P2 du dv = 1 for every incoming a'
-  c->p2.assign((size_t)G * na * na, 0.0);
-  std::vector<double> col(na);
+  // (the same [a][a'] block for every group: built once, then copied G times)
+  std::vector<double> blk((size_t)na * na), col(na);
   for (int ap = 0; ap < na; ap++) {
     const double u1 = c->u[ap % c->nu], v1 = c->v[ap / c->nu];
     double k = 0.0;
@@ -523,9 +523,11 @@ void build_tables(pbs_ctx *c, const pbs_physics &ph) {
       k += col[a];
     }
     k *= c->du * c->dv;
-    for (int g = 0; g < G; g++)
-      for (int a = 0; a < na; a++) c->p2[((size_t)g * na + a) * na + ap] = k > 0.0 ? col[a] / k : 0.0;
+    for (int a = 0; a < na; a++) blk[(size_t)a * na + ap] = k > 0.0 ? col[a] / k : 0.0;
   }
+  c->p2.clear();
+  c->p2.reserve((size_t)G * na * na);
+  for (int g = 0; g < G; g++) c->p2.insert(c->p2.end(), blk.begin(), blk.end());
 }
 
 template <typename st>
