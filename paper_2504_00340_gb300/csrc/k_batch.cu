@@ -100,6 +100,18 @@ __device__ void batch_abort(const BatchBeam *beams, int nbeams, int *abort_word,
   }
 }
 
+// The 16 x 16 angular stacks of one round as a separate function: inlined
+// into the persistent loop, their sine-table operands are hoisted out of the
+// loop into registers and the tile spills (~1 KB per thread at 128
+// registers); called, it needs no spill.  (Angle grids of at most 8 x 8 stay
+// inlined: there the call costs more than it saves.)
+template <int NU, int NV, int R>
+__device__ __noinline__ void angular_round(float *psi, const float *rho_yz, const float *ts, int nyz, int ng, float hq,
+                                           long long kgc0, long long nkgc, int bx, int x, int t, unsigned char *sm,
+                                           const ang::AngTables<float> &tb) {
+  ang::angular_f2_tiles<NU, NV, false, R>(psi, rho_yz, ts, nyz, ng, hq, kgc0, 1, nkgc, bx, x, t, sm, tb);
+}
+
 template <int NU, int NV, int SHAPE>
 __device__ __forceinline__ void run_tile(const BatchBeam &bm, const BatchTask &tk, long long tile, unsigned char *smem,
                                          const ang::AngTables<float> &tb) {
@@ -163,8 +175,12 @@ __device__ __forceinline__ void run_tile(const BatchBeam &bm, const BatchTask &t
       // the next round's rows travel to the L2 while this round computes
       if (it + 1 < kBAngRep / kPer)
         prefetch_stacks<NU, NV, kR>(bm.psi, d.nyz, k0 + kPer * (it + 1) + kR * sub, kend, bx, x, t);
-      ang::angular_f2_tiles<NU, NV, false, kR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
-                                               k0 + kPer * it + kR * sub, 1, kend, bx, x, t, sm, tb);
+      if constexpr (NT == 16)
+        angular_round<NU, NV, kR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
+                                  k0 + kPer * it + kR * sub, kend, bx, x, t, sm, tb);
+      else
+        ang::angular_f2_tiles<NU, NV, false, kR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
+                                                 k0 + kPer * it + kR * sub, 1, kend, bx, x, t, sm, tb);
       __syncthreads();  // the next stacks reuse the shared tiles
     }
   }
