@@ -247,7 +247,8 @@ def test_source_contraction(orc, precision, tol, ny, nz, nu, nv):
 
 
 @pytest.mark.parametrize("form", [0, 1, 2])
-@pytest.mark.parametrize("ny,nz,nu,nv,ng", [(24, 24, 16, 16, 40), (16, 20, 8, 16, 60), (12, 12, 16, 16, 7)])
+@pytest.mark.parametrize("ny,nz,nu,nv,ng", [(24, 24, 16, 16, 40), (16, 20, 8, 16, 60), (12, 12, 16, 16, 7),
+                                             (10, 12, 16, 16, 30)])
 def test_source_contraction_tensor_core_forms(orc, form, ny, nz, nu, nv, ng):
     """The tile-by-tile, the pipelined and the pipelined-swizzled tcgen05
     contraction (source_form 0 / 1 / 2) on many groups per CTA (P^2 reloads at group boundaries, every R stage
@@ -261,6 +262,28 @@ def test_source_contraction_tensor_core_forms(orc, form, ny, nz, nu, nv, ng):
     got = s.eval_source(0, 0)
     ref = o.source(rho[0], psi)
     assert _relerr(got, ref) < 8e-3
+    s.close()
+
+
+def test_source_contraction_pipelined_forms_equal_tile_by_tile_on_many_tiles():
+    """About ten 64-point tiles per CTA, so that every one of the pipelined
+    form's four TMEM accumulators and three R stages is reused several times
+    and each CTA crosses group boundaries (P^2 released by an MMA commit and
+    reloaded): the pipelined forms issue the same MMAs in the same K order as
+    the tile-by-tile form, so their BF16 sources equal it bit for bit."""
+    ny = nz = 24
+    ng = 160
+    grid = _grid(ny, nz, 16, 16, ng)
+    s = binding.Solver(grid, nx=1, dx=0.05, n_scatter=1, precision="mixed")
+    s.set_material(np.random.default_rng(9).uniform(0.5, 1.5, size=(1, ny, nz)))
+    s.write_psi(0, smooth_state(ny, nz, ng, 16, 16, seed=11))
+    out = {}
+    for form in (0, 1, 2):
+        s.set_tuning(source_form=form)
+        out[form] = s.eval_source(0, 0)
+    assert np.abs(out[0]).max() > 0
+    assert np.array_equal(out[1], out[0])
+    assert np.array_equal(out[2], out[0])
     s.close()
 
 
