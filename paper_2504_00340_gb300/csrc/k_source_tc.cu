@@ -275,8 +275,8 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
 // ---------------------------------------------------------------- pipelined form
 //
 // Warp-specialised and pipelined: lane 0 of warp 0 issues the TMA loads, lane
-// 0 of warp 1 the MMAs, warps 2-9 drain the accumulators.  P^2_g (all M rows, whole K) is
-// loaded once per group by one 5-D TMA copy straight into the canonical K-major
+// 0 of warp 1 the MMAs, warps 2-9 drain the accumulators.  P^2_g (all M rows,
+// whole K) is loaded once per group by one 5-D TMA copy straight into the canonical K-major
 // core-matrix layout; each R tile (whole K x 64 lateral points) by one 3-D TMA
 // copy into the canonical MN-major layout, kPipeMax stages ahead; the MMAs of a
 // tile go into one of four TMEM accumulators while the epilogue warps drain
@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(kThreads) k_source_tc(const __nv_bfloat16 *__r
 // writes its row's 32 BF16 values as two whole 32-byte sectors.  The MMAs of a
 // tile are issued from descriptors stepped by one 32-bit add each (the start
 // address field moves along K), so the issuing thread keeps the tensor pipe
-// fed; the loads wait on nothing but free stages.
+// fed; the loads wait only for free stages and, at a group change, for the
+// MMAs that read the old P^2 (an MMA commit releases it).
 // Each CTA walks a contiguous range of (group, N-tile) tiles; every wait is
 // bounded.
 
