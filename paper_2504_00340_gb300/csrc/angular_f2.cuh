@@ -22,17 +22,40 @@ __host__ __device__ constexpr int dst_off(int n) { return n <= 2 ? 0 : dst_off(n
 constexpr int kDstEntries = dst_off(kMaxAngle + 2);
 __constant__ float2 c_dst_f2[kDstEntries];
 
-// Fill this translation unit's c_dst_f2 (synchronous).
+// The same matrices hold only N/2 distinct magnitudes: with q = (m+1)(i+1)
+// mod 2(N+1) and k = q mod (N+1), entry (m, i) is zero when k = 0, else
+// sign * sqrt(2/(N+1)) sin(pi k'/(N+1)) with k' = min(k, N+1-k) <= N/2 and
+// sign = -1 exactly when q > N+1.  c_dst_mag holds those magnitudes for each
+// even N (k' = 1 .. N/2 at offset mag_off(N)).
+__host__ __device__ constexpr int mag_off(int n) { return n <= 2 ? 0 : mag_off(n - 2) + (n - 2) / 2; }
+constexpr int kMagEntries = mag_off(kMaxAngle + 2);
+__constant__ float c_dst_mag[kMagEntries];
+__host__ __device__ constexpr int dst_q(int n, int m, int i) { return ((m + 1) * (i + 1)) % (2 * (n + 1)); }
+__host__ __device__ constexpr int dst_k(int n, int m, int i) {
+  return dst_q(n, m, i) % (n + 1) <= n / 2 ? dst_q(n, m, i) % (n + 1) : (n + 1) - dst_q(n, m, i) % (n + 1);
+}
+__host__ __device__ constexpr bool dst_neg(int n, int m, int i) { return dst_q(n, m, i) > n + 1; }
+
+// Fill this translation unit's c_dst_f2 and c_dst_mag (synchronous).
 cudaError_t upload_dst_f2() {
   static float2 h[kDstEntries];
+  static float hm[kMagEntries];
   const double pi = 3.14159265358979323846;
-  for (int n = 2; n <= kMaxAngle; n += 2)
+  for (int n = 2; n <= kMaxAngle; n += 2) {
+    for (int k = 1; k <= n / 2; k++)
+      hm[mag_off(n) + k - 1] = (float)(std::sqrt(2.0 / (n + 1)) * std::sin(pi * k / (n + 1)));
+    // the pair table from the same FP32 magnitudes (exact zeros), so that both
+    // forms of the transform compute the same values
     for (int m = 0; m < n; m++)
       for (int i = 0; i < n; i++) {
-        const float v = (float)(std::sqrt(2.0 / (n + 1)) * std::sin(pi * (m + 1) * (i + 1) / (n + 1)));
+        const int k = dst_k(n, m, i);
+        const float v = k == 0 ? 0.0f : (dst_neg(n, m, i) ? -hm[mag_off(n) + k - 1] : hm[mag_off(n) + k - 1]);
         h[dst_off(n) + m * n + i] = make_float2(v, v);
       }
-  return cudaMemcpyToSymbol(c_dst_f2, h, sizeof(h));
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_dst_f2, h, sizeof(h));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_dst_mag, hm, sizeof(hm));
 }
 
 template <typename real>
@@ -106,6 +129,67 @@ __device__ __forceinline__ void dst_apply2(const float2 (&x)[N], float2 (&y)[N])
     for (int m = 0; m < N; m++) y[m] = fma2(c_dst_f2[dst_off(N) + m * N + i], (m & 1) ? o[i] : e[i], y[m]);
 }
 
+// The N/2 magnitudes of size N as duplicated pairs in registers, read
+// through an opaque move so that the compiler keeps them there: used as
+// constant-bank operands, every packed multiply-add needs its own move of the
+// pair into registers first.
+template <int N>
+struct DstMag {
+  float2 v[N / 2];
+  __device__ __forceinline__ void load() {
+#pragma unroll
+    for (int k = 0; k < N / 2; k++) {
+      float a;
+      asm volatile("mov.b32 %0, %1;" : "=f"(a) : "f"(c_dst_mag[mag_off(N) + k]));
+      v[k] = make_float2(a, a);
+    }
+  }
+};
+
+// dst_apply2 with the coefficients from registers: the magnitude and sign of
+// every entry are known at compile time (zero entries skipped).
+template <int N>
+__device__ __forceinline__ void dst_apply2r(const float2 (&x)[N], float2 (&y)[N], const DstMag<N> &c) {
+  constexpr int H = N / 2;
+  float2 e[H], o[H];
+#pragma unroll
+  for (int i = 0; i < H; i++) {
+    e[i] = add2(x[i], x[N - 1 - i]);
+    o[i] = fma2(x[N - 1 - i], make_float2(-1.f, -1.f), x[i]);
+  }
+#pragma unroll
+  for (int m = 0; m < N; m++) y[m] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < H; i++)
+#pragma unroll
+    for (int m = 0; m < N; m++) {
+      const int k = dst_k(N, m, i);
+      if (k == 0) continue;
+      const float2 w = c.v[k - 1];
+      const float2 v = (m & 1) ? o[i] : e[i];
+      y[m] = dst_neg(N, m, i) ? fma2(make_float2(-w.x, -w.y), v, y[m]) : fma2(w, v, y[m]);
+    }
+}
+
+// The v-direction magnitudes: the u set itself when the sizes agree.
+template <int A, int B>
+__device__ __forceinline__ const DstMag<B> &mag_pick(const DstMag<A> &a, const DstMag<B> &b) {
+  if constexpr (A == B)
+    return a;
+  else
+    return b;
+}
+
+// The transform of size N from the constant-bank table, or (REGC) from the
+// register magnitudes.
+template <int N, bool REGC>
+__device__ __forceinline__ void dst_apply2x(const float2 (&x)[N], float2 (&y)[N], const DstMag<N> &c) {
+  if constexpr (REGC)
+    dst_apply2r<N>(x, y, c);
+  else
+    dst_apply2<N>(x, y);
+}
+
 // As k_angular with each thread on two adjacent lateral points (one 8-byte
 // load per row) and the transforms on FP32x2 pairs; kF2X threads (2 kF2X
 // lateral points) per slab row, so that a warp covers two rows of 128 bytes
@@ -115,12 +199,19 @@ constexpr int kF2X = 16;
 // Slab stack kgc = (k * ng + g) * 2 + c, lateral block bx (2 kF2X points);
 // thread (x, t) of the kF2X x max(NU, NV) block; smem_raw holds the
 // transformed tile (NU NV kF2X float2).
-template <int NU, int NV, bool EXACT>
+template <int NU, int NV, bool EXACT, bool REGC = false>
 __device__ __forceinline__ void angular_f2_tile(float *__restrict__ psi, const float *__restrict__ rho_yz,
                                                 const float *__restrict__ ts, int nyz, int ng, float hq,
                                                 long long kgc, int bx, int x, int t, unsigned char *smem_raw,
                                                 const AngTables<float> &tb) {
   constexpr int NA = NU * NV;
+  DstMag<NU> cu;
+  DstMag<NV> cv_own;  // loaded only when NV != NU (else the u set serves both)
+  if constexpr (REGC) {
+    cu.load();
+    if constexpr (NU != NV) cv_own.load();
+  }
+  const DstMag<NV> &cv = mag_pick<NU, NV>(cu, cv_own);
   float2(*tile)[kF2X] = reinterpret_cast<float2(*)[kF2X]>(smem_raw);
   const int g = (int)((kgc / 2) % ng);
   const int yz = (bx * kF2X + x) * 2;
@@ -131,7 +222,7 @@ __device__ __forceinline__ void angular_f2_tile(float *__restrict__ psi, const f
 #pragma unroll
     for (int i = 0; i < NU; i++)
       r[i] = active ? *reinterpret_cast<const float2 *>(base + (long long)(t * NU + i) * nyz) : make_float2(0.f, 0.f);
-    dst_apply2<NU>(r, y);
+    dst_apply2x<NU, REGC>(r, y, cu);
 #pragma unroll
     for (int i = 0; i < NU; i++) tile[t * NU + i][x] = y[i];
   }
@@ -146,13 +237,13 @@ __device__ __forceinline__ void angular_f2_tile(float *__restrict__ psi, const f
     float2 c[NV], y[NV];
 #pragma unroll
     for (int j = 0; j < NV; j++) c[j] = tile[j * NU + t][x];
-    dst_apply2<NV>(c, y);
+    dst_apply2x<NV, REGC>(c, y, cv);
 #pragma unroll
     for (int n = 0; n < NV; n++) {
       const float l = tb.lam[n * NU + t];
       y[n] = scale_mode2<EXACT>(y[n], q, l);
     }
-    dst_apply2<NV>(y, c);
+    dst_apply2x<NV, REGC>(y, c, cv);
 #pragma unroll
     for (int j = 0; j < NV; j++) tile[j * NU + t][x] = c[j];
   }
@@ -161,7 +252,7 @@ __device__ __forceinline__ void angular_f2_tile(float *__restrict__ psi, const f
     float2 r[NU], y[NU];
 #pragma unroll
     for (int i = 0; i < NU; i++) r[i] = tile[t * NU + i][x];
-    dst_apply2<NU>(r, y);
+    dst_apply2x<NU, REGC>(r, y, cu);
     if (active) {
 #pragma unroll
       for (int i = 0; i < NU; i++) *reinterpret_cast<float2 *>(base + (long long)(t * NU + i) * nyz) = y[i];
@@ -174,12 +265,19 @@ __device__ __forceinline__ void angular_f2_tile(float *__restrict__ psi, const f
 // so that the loads of the R stacks are in flight together (latency hidden
 // by independent work instead of by more resident warps).  smem_raw holds R
 // tiles.
-template <int NU, int NV, bool EXACT, int R>
+template <int NU, int NV, bool EXACT, int R, bool REGC = false>
 __device__ __forceinline__ void angular_f2_tiles(float *__restrict__ psi, const float *__restrict__ rho_yz,
                                                  const float *__restrict__ ts, int nyz, int ng, float hq,
                                                  long long kgc0, long long kstride, long long nkgc, int bx, int x,
                                                  int t, unsigned char *smem_raw, const AngTables<float> &tb) {
   constexpr int NA = NU * NV;
+  DstMag<NU> cu;
+  DstMag<NV> cv_own;
+  if constexpr (REGC) {
+    cu.load();
+    if constexpr (NU != NV) cv_own.load();
+  }
+  const DstMag<NV> &cv = mag_pick<NU, NV>(cu, cv_own);
   const int yz = (bx * kF2X + x) * 2;
   float *base[R];
   bool active[R];
@@ -202,7 +300,7 @@ __device__ __forceinline__ void angular_f2_tiles(float *__restrict__ psi, const 
 #pragma unroll
     for (int r = 0; r < R; r++) {
       float2 y[NU];
-      dst_apply2<NU>(rr[r], y);
+      dst_apply2x<NU, REGC>(rr[r], y, cu);
 #pragma unroll
       for (int i = 0; i < NU; i++) tile[r][t * NU + i][x] = y[i];
     }
@@ -222,13 +320,13 @@ __device__ __forceinline__ void angular_f2_tiles(float *__restrict__ psi, const 
       float2 c[NV], y[NV];
 #pragma unroll
       for (int j = 0; j < NV; j++) c[j] = tile[r][j * NU + t][x];
-      dst_apply2<NV>(c, y);
+      dst_apply2x<NV, REGC>(c, y, cv);
 #pragma unroll
       for (int n = 0; n < NV; n++) {
         const float l = tb.lam[n * NU + t];
         y[n] = scale_mode2<EXACT>(y[n], q, l);
       }
-      dst_apply2<NV>(y, c);
+      dst_apply2x<NV, REGC>(y, c, cv);
 #pragma unroll
       for (int j = 0; j < NV; j++) tile[r][j * NU + t][x] = c[j];
     }
@@ -240,7 +338,7 @@ __device__ __forceinline__ void angular_f2_tiles(float *__restrict__ psi, const 
       float2 rr[NU], y[NU];
 #pragma unroll
       for (int i = 0; i < NU; i++) rr[i] = tile[r][t * NU + i][x];
-      dst_apply2<NU>(rr, y);
+      dst_apply2x<NU, REGC>(rr, y, cu);
       if (active[r]) {
 #pragma unroll
         for (int i = 0; i < NU; i++) *reinterpret_cast<float2 *>(base[r] + (long long)(t * NU + i) * nyz) = y[i];

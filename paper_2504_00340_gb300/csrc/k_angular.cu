@@ -142,8 +142,10 @@ __global__ void __launch_bounds__(tile_w<real>() * (NU > NV ? NU : NV), 2)
 
 // MINB > 0: registers capped so that MINB CTAs fit an SM (more warps to hide
 // the load latency).  PAIR: each CTA takes two consecutive slab stacks, the
-// second's rows asked of the L2 while the first is transformed.
-template <int NU, int NV, bool EXACT, int MINB, bool PAIR>
+// second's rows asked of the L2 while the first is transformed.  REGC: the
+// sine coefficients from registers (N/2 magnitudes per size, signs known at
+// compile time) instead of constant-bank pairs, each of which costs a move.
+template <int NU, int NV, bool EXACT, int MINB, bool PAIR, bool REGC = false>
 __global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV), MINB)
     k_angular_f2(float *__restrict__ psi, const float *__restrict__ rho_yz, const float *__restrict__ ts, int nyz,
                  int ng, float hq, long long kgc0, long long kgc_end, const __grid_constant__ AngTables<float> tb) {
@@ -165,16 +167,16 @@ __global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV), MINB)
                                      smem_raw, tb);
     }
   } else {
-    angular_f2_tile<NU, NV, EXACT>(psi, rho_yz, ts, nyz, ng, hq, kgc0 + blockIdx.y, blockIdx.x, threadIdx.x,
-                                   threadIdx.y, smem_raw, tb);
+    angular_f2_tile<NU, NV, EXACT, REGC>(psi, rho_yz, ts, nyz, ng, hq, kgc0 + blockIdx.y, blockIdx.x, threadIdx.x,
+                                         threadIdx.y, smem_raw, tb);
   }
 }
 
-template <int NU, int NV, bool EXACT, int MINB, bool PAIR>
+template <int NU, int NV, bool EXACT, int MINB, bool PAIR, bool REGC = false>
 cudaError_t go_f2_form(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
                        const AngTables<float> &tb) {
   constexpr int NT = NU > NV ? NU : NV;
-  auto kern = k_angular_f2<NU, NV, EXACT, MINB, PAIR>;
+  auto kern = k_angular_f2<NU, NV, EXACT, MINB, PAIR, REGC>;
   const size_t smem = sizeof(float2) * NU * NV * kF2X;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -193,12 +195,16 @@ cudaError_t go_f2_form(const LaunchCtx &lc, const Dims &d, float *psi, const flo
   return cudaSuccess;
 }
 
-// Packed FP32 forms (angular_form 2, 3, 4).
+// Packed FP32 forms (angular_form 2, 3, 4; 5 and 6 with the coefficients in
+// registers, as compiled and capped at 85 registers).
 template <int NU, int NV, bool EXACT>
 cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
                   const AngTables<float> &tb) {
   constexpr int NT = NU > NV ? NU : NV;
   constexpr int kMinB = 1024 / (kF2X * NT);  // 64 registers per thread
+  constexpr int kMinB3 = 768 / (kF2X * NT);  // 85 registers per thread
+  if (lc.angular_form == 5) return go_f2_form<NU, NV, EXACT, 0, false, true>(lc, d, psi, rho_yz, ts, h, tb);
+  if (lc.angular_form == 6) return go_f2_form<NU, NV, EXACT, kMinB3, false, true>(lc, d, psi, rho_yz, ts, h, tb);
   if (lc.angular_form == 3) return go_f2_form<NU, NV, EXACT, kMinB, false>(lc, d, psi, rho_yz, ts, h, tb);
   if (lc.angular_form == 4) return go_f2_form<NU, NV, EXACT, 0, true>(lc, d, psi, rho_yz, ts, h, tb);
   return go_f2_form<NU, NV, EXACT, 0, false>(lc, d, psi, rho_yz, ts, h, tb);

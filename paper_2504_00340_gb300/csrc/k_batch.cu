@@ -109,7 +109,7 @@ template <int NU, int NV, int R>
 __device__ __noinline__ void angular_round(float *psi, const float *rho_yz, const float *ts, int nyz, int ng, float hq,
                                            long long kgc0, long long nkgc, int bx, int x, int t, unsigned char *sm,
                                            const ang::AngTables<float> &tb) {
-  ang::angular_f2_tiles<NU, NV, false, R>(psi, rho_yz, ts, nyz, ng, hq, kgc0, 1, nkgc, bx, x, t, sm, tb);
+  ang::angular_f2_tiles<NU, NV, false, R, true>(psi, rho_yz, ts, nyz, ng, hq, kgc0, 1, nkgc, bx, x, t, sm, tb);
 }
 
 template <int NU, int NV, int SHAPE>
@@ -179,8 +179,8 @@ __device__ __forceinline__ void run_tile(const BatchBeam &bm, const BatchTask &t
         angular_round<NU, NV, kR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
                                   k0 + kPer * it + kR * sub, kend, bx, x, t, sm, tb);
       else
-        ang::angular_f2_tiles<NU, NV, false, kR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
-                                                 k0 + kPer * it + kR * sub, 1, kend, bx, x, t, sm, tb);
+        ang::angular_f2_tiles<NU, NV, false, kR, true>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng,
+                                                       bm.hq, k0 + kPer * it + kR * sub, 1, kend, bx, x, t, sm, tb);
       __syncthreads();  // the next stacks reuse the shared tiles
     }
   }

@@ -154,7 +154,7 @@ def test_transport_substep(orc, precision, tol, ny, nz, cols):
     s.close()
 
 
-@pytest.mark.parametrize("form", [2, 3, 4])
+@pytest.mark.parametrize("form", [2, 3, 4, 5, 6])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("nu,nv", [(8, 8), (16, 16), (4, 6)])
 def test_angular_substep(orc, precision, tol, nu, nv, form):
@@ -173,7 +173,7 @@ def test_angular_substep(orc, precision, tol, nu, nv, form):
     s.close()
 
 
-@pytest.mark.parametrize("form", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("form", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("nu,nv", [(16, 16), (8, 8)])
 def test_angular_exact_integrator(orc, precision, tol, form, nu, nv):
@@ -190,6 +190,30 @@ def test_angular_exact_integrator(orc, precision, tol, form, nu, nv):
     s.substep_angular(3.0, 1)
     for k in range(2):
         assert _relerr(s.read_psi(k), o.angular_substep(3.0, rho[1], psi[k])) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("nu,nv", [(16, 16), (8, 8), (4, 6), (10, 10)])
+def test_angular_packed_forms_agree_bit_for_bit(orc, nu, nv):
+    """The packed forms 2-6 (coefficients from the constant bank or, 5 and 6,
+    from registers: the same FP32 magnitudes, zero entries skipped) give the
+    same FP32 result, and it matches the oracle; even lateral count 12 x 16,
+    three groups."""
+    grid = _grid(12, 16, nu, nv, 3)
+    s, o, rho = _pair(orc, grid, 2, 0.05, 1, "fp32")
+    psi = [random_state((3, 2, nv, nu, 12, 16), seed=41 + k) for k in range(2)]
+    out = {}
+    for form in (2, 3, 4, 5, 6):
+        s.set_tuning(angular_form=form)
+        for k in range(2):
+            s.write_psi(k, psi[k])
+        s.substep_angular(3.0, 1)
+        out[form] = [s.read_psi(k) for k in range(2)]
+    for form in (3, 4, 5, 6):
+        for k in range(2):
+            assert np.array_equal(out[form][k], out[2][k]), (form, k)
+    for k in range(2):
+        assert _relerr(out[5][k], o.angular_substep(3.0, rho[1], psi[k])) < 5e-6
     s.close()
 
 
