@@ -17,13 +17,17 @@
 // along v; thread (x, j) transforms back along u and stores to global memory.
 // Sine and eigenvalue tables travel as kernel parameters (constant bank).
 //
-// Main form (k_angular_tma): a persistent CTA walks its tiles of
-// [all angles x 32 lateral points] of one (component, g, c); each tile comes
-// in by one 2-D TMA copy (cp.async.bulk.tensor, rows nyz apart in memory) into
-// one of three shared-memory buffers, is transformed in place (u, then v with
-// the mode factor, then u back) and leaves by one TMA store, while the next
-// two tiles load.  No per-element global address arithmetic remains; the
-// direct form (k_angular) serves grids whose row pitch breaks the TMA rules.
+// FP32 forms, chosen by the autotuner: the packed forms (k_angular_f2,
+// angular_form 2-6) transform two lateral points per thread on FP32x2 pairs;
+// form 5, the default for FP32, holds the N/2 distinct sine magnitudes in
+// registers (angular_f2.cuh).  The TMA-staged form (k_angular_tma) has a
+// persistent CTA walk its tiles of [all angles x 32 lateral points] of one
+// (component, g, c); each tile comes in by one 2-D TMA copy
+// (cp.async.bulk.tensor, rows nyz apart in memory) into one of three
+// shared-memory buffers, is transformed in place (u, then v with the mode
+// factor, then u back) and leaves by one TMA store, while the next two tiles
+// load.  The direct form (k_angular) serves FP64 and grids whose row pitch
+// breaks the TMA rules.
 #include "pbs_internal.cuh"
 #include "angular_f2.cuh"
 
