@@ -320,7 +320,7 @@ pbs_status pbs_run(pbs_ctx *ctx, int use_graph);
  * different depth and size fill the GPU together with no bucketing and no
  * empty energy groups.  Every tile is the same device code as the matching
  * block of the per-substep kernels, so each beam's psi equals its own
- * pbs_run with the tuning {energy_angles 8, energy_form 1, angular_form 2 to 6}
+ * pbs_run with the tuning {energy_angles 8, energy_form 1, angular_form 2 to 7}
  * bit for bit (the dose up to the order of its atomic FP64 sums).
  *   use_graph      nonzero: record the batch (every beam's restart from its
  *                  projection, the queue reset, the launch) into a CUDA graph
@@ -454,7 +454,8 @@ pbs_status pbs_get_options(const pbs_ctx *ctx, pbs_options *options);
  *                   coefficients held in registers (the N/2 distinct
  *                   magnitudes, signs fixed at compile time) instead of read
  *                   from the constant bank, 6 as 5 at most 85 registers per
- *                   thread; a form the grid does not allow falls back to 0
+ *                   thread, 7 as 5 with two slab stacks per CTA (as 4); a form
+ *                   the grid does not allow falls back to 0
  *   source_form     BF16 source contraction on the tensor cores (mixed
  *                   precision, n_scatter > 0): 0 tile by tile, 1 pipelined
  *                   (TMA loads, MMAs and epilogue of consecutive tiles

@@ -163,12 +163,12 @@ __global__ void __launch_bounds__(kF2X * (NU > NV ? NU : NV), MINB)
       for (int i = 0; i < NU; i++)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (long long)(threadIdx.y * NU + i) * nyz));
     }
-    angular_f2_tile<NU, NV, EXACT>(psi, rho_yz, ts, nyz, ng, hq, k, blockIdx.x, threadIdx.x, threadIdx.y, smem_raw,
-                                   tb);
+    angular_f2_tile<NU, NV, EXACT, REGC>(psi, rho_yz, ts, nyz, ng, hq, k, blockIdx.x, threadIdx.x, threadIdx.y,
+                                         smem_raw, tb);
     if (k + 1 < kgc_end) {
       __syncthreads();  // the tile is reused
-      angular_f2_tile<NU, NV, EXACT>(psi, rho_yz, ts, nyz, ng, hq, k + 1, blockIdx.x, threadIdx.x, threadIdx.y,
-                                     smem_raw, tb);
+      angular_f2_tile<NU, NV, EXACT, REGC>(psi, rho_yz, ts, nyz, ng, hq, k + 1, blockIdx.x, threadIdx.x, threadIdx.y,
+                                           smem_raw, tb);
     }
   } else {
     angular_f2_tile<NU, NV, EXACT, REGC>(psi, rho_yz, ts, nyz, ng, hq, kgc0 + blockIdx.y, blockIdx.x, threadIdx.x,
@@ -199,8 +199,8 @@ cudaError_t go_f2_form(const LaunchCtx &lc, const Dims &d, float *psi, const flo
   return cudaSuccess;
 }
 
-// Packed FP32 forms (angular_form 2, 3, 4; 5 and 6 with the coefficients in
-// registers, as compiled and capped at 85 registers).
+// Packed FP32 forms (angular_form 2, 3, 4; 5, 6 and 7 with the coefficients
+// in registers: as compiled, capped at 85 registers, two stacks per CTA).
 template <int NU, int NV, bool EXACT>
 cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *rho_yz, const float *ts, double h,
                   const AngTables<float> &tb) {
@@ -209,6 +209,7 @@ cudaError_t go_f2(const LaunchCtx &lc, const Dims &d, float *psi, const float *r
   constexpr int kMinB3 = 768 / (kF2X * NT);  // 85 registers per thread
   if (lc.angular_form == 5) return go_f2_form<NU, NV, EXACT, 0, false, true>(lc, d, psi, rho_yz, ts, h, tb);
   if (lc.angular_form == 6) return go_f2_form<NU, NV, EXACT, kMinB3, false, true>(lc, d, psi, rho_yz, ts, h, tb);
+  if (lc.angular_form == 7) return go_f2_form<NU, NV, EXACT, 0, true, true>(lc, d, psi, rho_yz, ts, h, tb);
   if (lc.angular_form == 3) return go_f2_form<NU, NV, EXACT, kMinB, false>(lc, d, psi, rho_yz, ts, h, tb);
   if (lc.angular_form == 4) return go_f2_form<NU, NV, EXACT, 0, true>(lc, d, psi, rho_yz, ts, h, tb);
   return go_f2_form<NU, NV, EXACT, 0, false>(lc, d, psi, rho_yz, ts, h, tb);

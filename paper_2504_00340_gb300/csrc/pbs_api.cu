@@ -1136,7 +1136,7 @@ pbs_status autotune_impl(pbs_ctx *c, int reps) {
   c->tune = pick;
   best = 1e30f;
   if (r == PBS_OK) {
-    for (int form : {5, 6, 2, 3, 4, 1, 0}) {
+    for (int form : {5, 7, 6, 2, 3, 4, 1, 0}) {
       c->tune.angular_form = form;
       float ms;
       r = time_best([&] { return angular_run<real>(c, c->dx, 0, c->B); }, ms);
@@ -1779,7 +1779,7 @@ pbs_status pbs_set_tuning(pbs_ctx *c, const pbs_tuning *t) {
       t->energy_form > 1 || t->transport_ctas < 0 || t->transport_ctas > 64 ||
       (t->transport_cols != 0 && t->transport_cols != 4 && t->transport_cols != 6 && t->transport_cols != 8) ||
       t->angular_form < 0 ||
-      t->angular_form > 6 || t->source_form < 0 || t->source_form > 2)
+      t->angular_form > 7 || t->source_form < 0 || t->source_form > 2)
     return fail(c, PBS_ERR_ARG, "tuning value out of range");
   c->tune = *t;
   drop_graph(c);

@@ -160,7 +160,7 @@ struct LaunchCtx {
   int energy_angles = 8;   // energy: angles per block (4, 8 or 16) x 32 lateral points
   int transport_ctas = 0;  // streaming transport: resident CTAs per SM (0 = as many as fit)
   int transport_cols = 0;  // streaming transport: columns per lane, 4 or 6 (0 = by row width)
-  int angular_form = 5;    // angular substep: 0 direct, 1 TMA-staged persistent, 2-6 packed FP32x2
+  int angular_form = 5;    // angular substep: 0 direct, 1 TMA-staged persistent, 2-7 packed FP32x2
                            // (2 as compiled, 3 at 64 registers, 4 two stacks per CTA; where the grid allows, else 0)
   int energy_form = 1;     // FP32 energy substep: 0 one lane per thread, 1 packed FP32x2
                            // (form 1 where the grid allows, else 0)

@@ -115,7 +115,7 @@ def main(argv=None):
     p.add_argument("--physics-model", type=int, choices=[0, 1],
                    help="0: Bragg-Kleeman + Highland, 1: the paper's Appendix A tables")
     p.add_argument("--energy-form", type=int, choices=[0, 1], help="FP32 energy kernel form (default: tuned)")
-    p.add_argument("--angular-form", type=int, choices=range(7), help="angular kernel form (default: tuned)")
+    p.add_argument("--angular-form", type=int, choices=range(8), help="angular kernel form (default: tuned)")
     p.add_argument("--energy-angles", type=int, choices=[4, 8, 16], help="angles per energy block")
     p.add_argument("--transport-cols", type=int, choices=[4, 6, 8], help="transport columns per lane")
     p.add_argument("--transport-ctas", type=int, help="resident transport CTAs per SM (0: as many as fit)")

@@ -156,7 +156,7 @@ def test_autotune_and_forms_keep_results():
     s.autotune(2)
     t = s.tuning
     assert t["energy_angles"] in (4, 8, 16) and t["energy_form"] in (0, 1)
-    assert t["transport_ctas"] in (0, 1, 2, 3, 4) and t["angular_form"] in (0, 1, 2, 3, 4, 5, 6)
+    assert t["transport_ctas"] in (0, 1, 2, 3, 4) and t["angular_form"] in (0, 1, 2, 3, 4, 5, 6, 7)
     assert t["transport_cols"] in (4, 6, 8)
     assert s.depth == 0
     plain = dict(energy_angles=8, energy_form=0, transport_ctas=0, angular_form=0)
@@ -181,7 +181,7 @@ def test_autotune_and_forms_keep_results():
     with pytest.raises(binding.PbsError):
         s.set_tuning(energy_angles=6)
     with pytest.raises(binding.PbsError):
-        s.set_tuning(energy_angles=8, angular_form=7)
+        s.set_tuning(energy_angles=8, angular_form=8)
     s.close()
 
 

@@ -154,7 +154,7 @@ def test_transport_substep(orc, precision, tol, ny, nz, cols):
     s.close()
 
 
-@pytest.mark.parametrize("form", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("form", [2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("nu,nv", [(8, 8), (16, 16), (4, 6)])
 def test_angular_substep(orc, precision, tol, nu, nv, form):
@@ -173,7 +173,7 @@ def test_angular_substep(orc, precision, tol, nu, nv, form):
     s.close()
 
 
-@pytest.mark.parametrize("form", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("form", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-6)])
 @pytest.mark.parametrize("nu,nv", [(16, 16), (8, 8)])
 def test_angular_exact_integrator(orc, precision, tol, form, nu, nv):
@@ -195,21 +195,21 @@ def test_angular_exact_integrator(orc, precision, tol, form, nu, nv):
 
 @pytest.mark.parametrize("nu,nv", [(16, 16), (8, 8), (4, 6), (10, 10)])
 def test_angular_packed_forms_agree_bit_for_bit(orc, nu, nv):
-    """The packed forms 2-6 (coefficients from the constant bank or, 5 and 6,
-    from registers: the same FP32 magnitudes, zero entries skipped) give the
+    """The packed forms 2-7 (coefficients from the constant bank, or from
+    registers in 5-7: the same FP32 magnitudes, zero entries skipped) give the
     same FP32 result, and it matches the oracle; even lateral count 12 x 16,
-    three groups."""
+    three groups (form 4 and 7 take two stacks per CTA: a ragged last pair)."""
     grid = _grid(12, 16, nu, nv, 3)
     s, o, rho = _pair(orc, grid, 2, 0.05, 1, "fp32")
     psi = [random_state((3, 2, nv, nu, 12, 16), seed=41 + k) for k in range(2)]
     out = {}
-    for form in (2, 3, 4, 5, 6):
+    for form in (2, 3, 4, 5, 6, 7):
         s.set_tuning(angular_form=form)
         for k in range(2):
             s.write_psi(k, psi[k])
         s.substep_angular(3.0, 1)
         out[form] = [s.read_psi(k) for k in range(2)]
-    for form in (3, 4, 5, 6):
+    for form in (3, 4, 5, 6, 7):
         for k in range(2):
             assert np.array_equal(out[form][k], out[2][k]), (form, k)
     for k in range(2):
