@@ -254,11 +254,12 @@ cudaError_t launch_kv(const LaunchCtx &lc, const Dims &d, real *psi, double tau,
     // the FP32 march needs a few registers more than some residencies leave
     // (4 columns: ~135, 8 columns: ~175): asked for 4 (4 columns) or 3 (8
     // columns) CTAs per SM, take the form whose registers are capped for it
-    if (sizeof(real) == 4 && !CN && vec && ((KV == 4 && lc.transport_ctas == 4) || (KV == 8 && lc.transport_ctas == 3))) {
-      if (KV == 4)
-        kern = fz ? k_transport_rows<real, true, true, KV, CN, 4> : k_transport_rows<real, true, false, KV, CN, 4>;
-      else
-        kern = fz ? k_transport_rows<real, true, true, KV, CN, 3> : k_transport_rows<real, true, false, KV, CN, 3>;
+    // (instantiated only for the FP32 explicit march: the other forms never
+    // take them, and each capped pair is two more kernels to compile)
+    if constexpr (sizeof(real) == 4 && !CN && (KV == 4 || KV == 8)) {
+      constexpr int kCap = KV == 4 ? 4 : 3;
+      if (vec && lc.transport_ctas == kCap)
+        kern = fz ? k_transport_rows<real, true, true, KV, CN, kCap> : k_transport_rows<real, true, false, KV, CN, kCap>;
     }
     cudaError_t e;
     if (smem > 48 * 1024 &&
