@@ -100,13 +100,13 @@ __device__ void batch_abort(const BatchBeam *beams, int nbeams, int *abort_word,
   }
 }
 
-// The 16 x 16 angular stacks of one round as a separate function: inlined
+// One sweep of 16 x 16 angular stacks as a separate function: inlined
 // into the persistent loop, their sine-table operands are hoisted out of the
 // loop into registers and the tile spills (~1 KB per thread at 128
 // registers); called, it needs no spill.  (Angle grids of at most 8 x 8 stay
 // inlined: there the call costs more than it saves.)
 template <int NU, int NV, int R>
-__device__ __noinline__ void angular_round(float *psi, const float *rho_yz, const float *ts, int nyz, int ng, float hq,
+__device__ __noinline__ void angular_sweep(float *psi, const float *rho_yz, const float *ts, int nyz, int ng, float hq,
                                            long long kgc0, long long nkgc, int bx, int x, int t, unsigned char *sm,
                                            const ang::AngTables<float> &tb) {
   ang::angular_f2_tiles<NU, NV, false, R, true>(psi, rho_yz, ts, nyz, ng, hq, kgc0, 1, nkgc, bx, x, t, sm, tb);
@@ -166,17 +166,17 @@ __device__ __forceinline__ void run_tile(const BatchBeam &bm, const BatchTask &t
     const int bx = (int)(tile % bm.a_bx);
     const long long k0 = tk.first + (tile / bm.a_bx) * kBAngRep;
     const long long kend = tk.first + tk.nstacks;  // the task's stacks end here
-    constexpr int kPer = kSub * kR;  // stacks per round of the CTA
+    constexpr int kPer = kSub * kR;  // stacks per sweep of the CTA
     const int sub = tid / (16 * NT);
     const int x = tid & 15, t = (tid >> 4) % NT;
     unsigned char *sm = smem + (size_t)sub * kR * sizeof(float2) * NU * NV * ang::kF2X;
 #pragma unroll 1
     for (int it = 0; it < kBAngRep / kPer && k0 + kPer * it < kend; it++) {
-      // the next round's rows travel to the L2 while this round computes
+      // the next sweep's rows travel to the L2 while this sweep computes
       if (it + 1 < kBAngRep / kPer)
         prefetch_stacks<NU, NV, kR>(bm.psi, d.nyz, k0 + kPer * (it + 1) + kR * sub, kend, bx, x, t);
       if constexpr (NT == 16)
-        angular_round<NU, NV, kR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
+        angular_sweep<NU, NV, kR>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng, bm.hq,
                                   k0 + kPer * it + kR * sub, kend, bx, x, t, sm, tb);
       else
         ang::angular_f2_tiles<NU, NV, false, kR, true>(bm.psi, bm.rho + (size_t)step * nyz, bm.ts, d.nyz, d.ng,
